@@ -1,0 +1,343 @@
+"""Throughput of the differentiable magneto-elastic MPM on one GB300.
+
+One bench step = one design iteration of the 2D locomotion workload: the
+forward pass over the whole horizon (cell sort, P2G, grid operation, G2P,
+objective) plus the checkpointed adjoint (recomputation and the reverse
+kernels), producing dL/dphi, dL/dB~_r and dL/dB_applied.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is particle-steps per second of
+forward+adjoint over all ranks (sum of particles x substeps / max time);
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload instead.  Several GPUs run independent replicas (a single simulation
+does not shard without a halo exchange every substep).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2503_22767_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s fwd+adjoint (and ms/design iter) vs oracle, % HBM roofline"
+UNIT = "particle-steps/s"
+CLASS_NAMES = ["forward particle (G2P+P2G)", "adjoint particle (P2G^T+G2P^T)", "grid operation",
+               "grid adjoint"]
+
+
+def workload(seed=0):
+    return W.walker_2d(seed=seed, n_steps=4000, checkpoint_every=100)
+
+
+def workload_desc(w):
+    c = w.cfg
+    return {
+        "workload": (f"walker2d_128: 2D locomotion, {c.res}^2 grid, {c.n_total} particles, "
+                     f"{c.n_steps} substeps dt={c.dt}, Coulomb floor mu={c.floor_mu}, "
+                     f"16-coefficient Fourier field per axis, checkpoint every {c.checkpoint_every}"),
+        "particles": c.n_total,
+        "substeps": c.n_steps,
+        "grid": f"{c.res}^{c.dim}",
+        "checkpoint_every": c.checkpoint_every,
+        "step": "one design iteration: forward over the horizon + checkpointed adjoint",
+    }
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2503_22767_gb300.sim import Simulator
+
+    w = workload(seed=rank)
+    cfg = w.cfg
+    sim = Simulator(cfg)
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    x0, phi, mag, field = t(w.x0), t(w.phi), t(w.mag), t(w.field)
+    dloss = torch.ones(cfg.n_instances, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def iteration():
+        loss, _ = sim.forward(x0, phi, mag, field)
+        g = sim.backward(dloss)
+        return loss, g
+
+    for _ in range(args.warmup):
+        iteration()
+    torch.cuda.synchronize()
+    sim.reset_stats()
+    sim.set_option(1, args.timing_stride)  # time every k-th launch of each kernel class
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clocks:
+        for i in range(args.steps):
+            flush.zero_()  # evict L2 between timed iterations (outside the events)
+            ev[i][0].record(stream)
+            loss, g = iteration()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    stats = sim.stats()
+    sim.set_option(1, 0)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    ps = cfg.n_total * cfg.n_steps
+    value = ps * world / (ms_per_step / 1000.0)
+    loss_val = float(loss.sum().item())
+
+    # dominant kernel class by measured time
+    per_class_ms = [stats["timed_ms"][c] for c in range(4)]
+    dom = int(np.argmax(per_class_ms))
+    peak, peak_kind = load_peaks()
+    achieved = (stats["timed_bytes"][dom] / 1e9) / (stats["timed_ms"][dom] / 1e3) if stats["timed_ms"][dom] else 0.0
+    launches_timed = stats["timed_launches"][dom]
+    roofline = {
+        "bound": "hbm",
+        "kernel": CLASS_NAMES[dom],
+        "achieved": round(achieved, 1),
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": round(achieved / peak, 4),
+        "peak_source": f"{peak_kind} hbm_gbs",
+        "traffic": None,
+        "avg_launch_us": round(1e3 * stats["timed_ms"][dom] / max(launches_timed, 1), 2),
+        "algorithmic_bytes_per_launch": round(stats["timed_bytes"][dom] / max(launches_timed, 1)),
+        "timed_launches": launches_timed,
+        "time_share_by_class": {CLASS_NAMES[c]: round(per_class_ms[c] / max(sum(per_class_ms), 1e-9), 3)
+                                for c in range(4)},
+    }
+    if args.traffic_bytes:
+        roofline["traffic"] = args.traffic_bytes
+
+    # end to end through the host-buffer entry points (pinned memory)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hx0, hphi, hmag, hfield = pin(w.x0), pin(w.phi), pin(w.mag), pin(w.field)
+    hloss = torch.empty(cfg.n_instances).pin_memory()
+    hdl = torch.ones(cfg.n_instances).pin_memory()
+    hgp = torch.empty(phi.shape).pin_memory()
+    hgm = torch.empty(mag.shape).pin_memory()
+    hgf = torch.empty(field.shape).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.forward_host(hx0, hphi, hmag, hfield, None, None, None, hloss)
+        sim.backward_host(hdl, hgp, hgm, hgf)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    h2d = 4 * (w.x0.size + w.phi.size + w.mag.size + w.field.size + cfg.n_instances)
+    d2h = 4 * (cfg.n_instances + w.phi.size + w.mag.size + w.field.size)
+    e2e = {"value": round(ps / (e2e_ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3), "steps": e2e_steps,
+           "api": "mpm_forward_host + mpm_backward_host (C ABI, pinned host buffers)"}
+    if dist:
+        t2 = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+        e2e["value"] = round(ps * world / (float(t2.item()) / 1e3), 1)
+
+    sim.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    out = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded walker body, design and field schedule; see workloads.walker_2d)",
+        "config": {**workload_desc(w), "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between timed iterations (outside the timed events)"},
+        "ms_per_design_iteration": round(ms_per_step, 3),
+        "loss": loss_val,
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(stats["launches"]),
+        "clocks": clocks.summary(),
+        "device_bytes": stats["device_bytes"],
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_steps)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# oracle arm (CPU baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def _oracle_sample(w, n_steps):
+    import oracle
+
+    ws = W.with_steps(w, n_steps)
+    t0 = time.perf_counter()
+    oracle.forward(ws)
+    oracle.backward(ws, ckpt_every=max(1, n_steps // 4))
+    dt = time.perf_counter() - t0
+    return ws.cfg.n_total * n_steps / dt, dt
+
+
+def cpu_baseline(w, n_steps):
+    v, dt = _oracle_sample(w, n_steps)
+    return {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"first {n_steps} of {w.cfg.n_steps} substeps, all {w.cfg.n_total} particles, "
+                       f"forward + adjoint (FP64 serial C oracle; {dt:.1f} s; host has {os.cpu_count()} cores)")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload()
+    n = args.cpu_sample_steps
+    for _ in range(args.warmup):
+        _oracle_sample(w, max(1, n // 4))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _oracle_sample(w, n)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = w.cfg.n_total * n / (ms / 1e3)
+    sample = (f"each step: first {n} of {w.cfg.n_steps} substeps, all {w.cfg.n_total} particles, "
+              "forward + adjoint of the FP64 serial C oracle")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {**workload_desc(w), "parallelism": "CPU, one core"},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--timing-stride", type=int, default=8,
+                    help="time every k-th launch of each kernel class with CUDA events")
+    ap.add_argument("--cpu-sample-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

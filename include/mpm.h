@@ -1,0 +1,223 @@
+/*
+ * mpm.h -- C ABI of the GB300 differentiable magneto-elastic MPM library.
+ *
+ * The library advances a batch of independent MLS-MPM simulations of
+ * hard-magnetic soft material (arxiv 2503.22767, Section 2) and computes the
+ * reverse-mode gradients of a scalar objective with respect to the design
+ * variables (Section 2.3, Section 3.1):
+ *
+ *   per substep n (Section 2.2):
+ *     sort      particles by grid cell (a performance ordering; not in the paper)
+ *     P2G       grid mass and momentum, Eq. 14-15, with the Piola stress of
+ *               Eq. 7 interpolated by SIMP, Eq. 31-33
+ *     grid op   Eq. 16-17 (damping, gravity) and Eq. 18 (walls, Coulomb floor)
+ *     G2P       Eq. 19-22 (velocity, APIC affine matrix, position, F)
+ *   objective   shape MSE (Eq. 38, summed over tasks by Eq. 35) or
+ *               locomotion (Eq. 40)
+ *
+ * Conventions shared by every entry point
+ *   - Every array argument is float32, contiguous, structure-of-arrays:
+ *     a per-particle vector quantity is [d][N], component-major, with the
+ *     particles of all instances concatenated in instance order.
+ *   - "device" pointers must be CUDA device memory of the current device;
+ *     "host" pointers are ordinary (preferably pinned) host memory.  The
+ *     caller owns every buffer it passes; the library never frees them and
+ *     keeps no reference after the call returns (inputs that the backward pass
+ *     needs are copied into library-owned storage).
+ *   - Work is enqueued on `cuda_stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  forward/backward synchronise that stream before
+ *     returning, because the status includes device-side checks.
+ *   - Every function returns an mpm_status; no C++ exception or abort
+ *     crosses the ABI.  mpm_last_error() gives a text for the last failure.
+ *   - One handle must not be used from two threads at once.
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_handle mpm_handle;
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_ERR_ARG = -1,     /* invalid argument or configuration (host check) */
+    MPM_ERR_CUDA = -2,    /* a CUDA runtime call failed */
+    MPM_ERR_OOM = -3,     /* device allocation failed in mpm_create */
+    MPM_ERR_STATE = -4,   /* backward without a preceding successful forward */
+    MPM_ERR_NUMERIC = -5, /* J <= 0 or a non-finite value appeared on the device */
+    MPM_ERR_DOMAIN = -6,  /* a particle's stencil left the grid */
+    MPM_ERR_TIMEOUT = -7  /* a bounded device-side wait gave up */
+} mpm_status;
+
+/*
+ * Problem description (copied by mpm_create; pointers need only live for the
+ * duration of that call).
+ *
+ *   dim, grid_res     2 or 3; res nodes per axis, dx = 1/res, node i at i*dx.
+ *   dt, n_steps       substep size and horizon N.
+ *   n_instances, n_particles
+ *                     independent simulations and their particle counts (host
+ *                     array [n_instances]); each instance has its own grid.
+ *   n_designs, design_of_instance
+ *                     topology phi and magnetisation B~_r are given per design;
+ *                     instance i uses design design_of_instance[i] (host array,
+ *                     NULL = identity).  Instances sharing a design must have
+ *                     equal particle counts; their gradients are summed
+ *                     (multi-task sharing, Eq. 35).
+ *   E, nu, rho0, p_vol
+ *                     Young's modulus, Poisson ratio (G = E/(2(1+nu)),
+ *                     K = E/(3(1-2nu))), density and particle volume; the
+ *                     particle mass is phi * rho0 * p_vol (Eq. 33).
+ *   simp_eps, simp_q  SIMP interpolation (Eq. 31).
+ *   damping_c, gravity
+ *                     damping rate (1/s) and body acceleration (Eq. 17).
+ *   bound, wall_mode, floor_mu
+ *                     wall band width in nodes; wall_mode 0 = every wall
+ *                     non-slip, 1 = Coulomb friction floor (axis 1, low side,
+ *                     Eq. 18 with coefficient floor_mu) and non-slip elsewhere.
+ *   loss_kind         0 = mean squared distance of final positions to the
+ *                     target (Eq. 38), 1 = -sum_{n=1..N} vbar_x(n) dt with the
+ *                     mass-averaged velocity (Eq. 40).
+ *   checkpoint_every  K: the backward pass recomputes K-substep segments from
+ *                     checkpoints; 0 = keep every substep (one segment).
+ */
+typedef struct {
+    int dim;
+    int grid_res;
+    double dt;
+    int n_steps;
+    int n_instances;
+    const int* n_particles;
+    int n_designs;
+    const int* design_of_instance;
+    double E, nu, rho0, p_vol;
+    double simp_eps;
+    int simp_q;
+    double damping_c;
+    double gravity[3];
+    int bound;
+    int wall_mode;
+    double floor_mu;
+    int loss_kind;
+    int checkpoint_every;
+} mpm_config;
+
+/*
+ * Create a handle and allocate, on the current device, every buffer the
+ * forward and backward passes need (grid, sort scratch, checkpoints, segment
+ * store, saved inputs).  No later call allocates device memory.
+ * Errors: MPM_ERR_ARG (bad config), MPM_ERR_OOM, MPM_ERR_CUDA.  On error
+ * *out is set to NULL and nothing stays allocated.
+ */
+int mpm_create(const mpm_config* cfg, mpm_handle** out);
+
+/* Release everything the handle owns (synchronises the device first). */
+int mpm_destroy(mpm_handle* h);
+
+/* Text of the last error on this handle ("" if none).  Owned by the handle. */
+const char* mpm_last_error(const mpm_handle* h);
+
+/*
+ * Run the N substeps of every instance from rest (C = 0, F = I) and
+ * evaluate the objective (Section 2.2, Eq. 14-22; Eq. 38 or Eq. 40).
+ *   x0      device [d][N]      initial positions (N = sum of n_particles)
+ *   v0      device [d][N]      initial velocities, or NULL for zero
+ *   phi_bar device [Nd]        projected topology variable per particle of
+ *                              each design (Nd = sum over designs)
+ *   mag     device [d][Nd]     residual flux density B~_r in Tesla (Eq. 26)
+ *   field   device [n_instances][n_steps][d]
+ *                              applied flux density B_applied in Tesla, held
+ *                              constant over substep n (t_n = n dt)
+ *   target  device [d][N]      target positions (loss_kind 0; NULL otherwise)
+ *   x_out   device [d][N]      final positions in input order, or NULL
+ *   loss_out device [n_instances] objective of each instance
+ * Errors: MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_NUMERIC (inverted or non-finite
+ * deformation), MPM_ERR_DOMAIN (a particle's stencil left the grid; the
+ * kernels clamp indices so memory stays in bounds).  The inputs needed by
+ * mpm_backward are copied; the caller may reuse its buffers on return.
+ */
+int mpm_forward(mpm_handle* h, const float* x0, const float* v0, const float* phi_bar,
+                const float* mag, const float* field, const float* target, float* x_out,
+                float* loss_out, void* cuda_stream);
+
+/*
+ * Reverse-mode gradients of sum_i dloss[i] * loss_i for the last successful
+ * mpm_forward on this handle, by checkpointed recomputation (Section 2.3).
+ *   dloss   device [n_instances] upstream gradient
+ *   g_phi   device [Nd]        dL/dphi_bar (overwritten)
+ *   g_mag   device [d][Nd]     dL/dB~_r   (overwritten)
+ *   g_field device [n_instances][n_steps][d] dL/dB_applied (overwritten)
+ * Any output may be NULL to skip it.  Errors: MPM_ERR_STATE (no forward),
+ * MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_NUMERIC, MPM_ERR_DOMAIN.
+ */
+int mpm_backward(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag, float* g_field,
+                 void* cuda_stream);
+
+/*
+ * Same as mpm_forward / mpm_backward but every array argument is a HOST
+ * pointer: the library copies inputs to the device and results back inside
+ * the call (cudaMemcpyAsync on cuda_stream into buffers allocated by
+ * mpm_create).  Use pinned memory for full copy bandwidth.
+ */
+int mpm_forward_host(mpm_handle* h, const float* x0, const float* v0, const float* phi_bar,
+                     const float* mag, const float* field, const float* target, float* x_out,
+                     float* loss_out, void* cuda_stream);
+int mpm_backward_host(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
+                      float* g_field, void* cuda_stream);
+
+/*
+ * Final particle state of the last forward, in input order (device
+ * pointers, each may be NULL): x, v [d][N]; C, F [d][d][N] (row-major
+ * components, component (a,b) at offset (a*d+b)*N).
+ */
+int mpm_read_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* cuda_stream);
+
+/*
+ * The particle ordering used by the substep, exposed for checking: for
+ * device positions x [d][N] (N = sum of n_particles, instances concatenated)
+ * writes the cell key of every particle and the stable order by key
+ * (perm[new] = old; ties keep input order).  Key definition: per axis
+ * base = floor(fl(fl(x * res) - 0.5)) in float32 round-to-nearest, clamped
+ * to [0, res-3]; blocks of edge 8 (2D) or 4 (3D) cells; key = instance *
+ * (blocks * cells per block) + block index * cells per block + cell index in
+ * the block, blocks and cells row-major with the last axis fastest.
+ * Not in the paper: it is the locality order of the GPU path.
+ *   keys, perm: device int32 [N].
+ */
+int mpm_sort_particles(mpm_handle* h, const float* x, int* keys, int* perm, void* cuda_stream);
+
+/* Options (mpm_set_option keys). */
+enum {
+    MPM_OPT_TIMING = 1, /* k > 0: time every k-th launch of each kernel class with CUDA
+                           events (on the call's stream); 0 (default): off */
+    MPM_OPT_BLOCK = 2   /* threads per block of the particle kernels: a multiple of 32
+                           in [32, 256] (default 128) */
+};
+/* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
+int mpm_set_option(mpm_handle* h, int key, long long value);
+
+/*
+ * Counters since creation or the last reset: kernel launches issued by the
+ * library, and, with MPM_OPT_TIMING on, the number of timed launches and
+ * total milliseconds of the named kernel class, plus the algorithmic bytes
+ * those launches moved.  kernel_class: 0 = forward particle kernel
+ * (G2P + P2G), 1 = adjoint particle kernel (P2G^T + G2P^T), 2 = grid
+ * operation, 3 = grid adjoint.
+ */
+typedef struct {
+    long long launches;
+    long long timed_launches[4];
+    double timed_ms[4];
+    double timed_bytes[4];
+    long long device_bytes;
+} mpm_stats;
+int mpm_get_stats(const mpm_handle* h, mpm_stats* out);
+int mpm_reset_stats(mpm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPM_H */

@@ -1,0 +1,101 @@
+// Host-side launchers of the substep kernels (implemented in kernels_*.cu).
+// Each returns the cudaError_t of its launch; all work goes on `st`.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mpm_device.cuh"
+
+namespace mpm {
+
+// Buffers one particle kernel touches; unused members stay null.
+struct StepArgs {
+    const float* s_in = nullptr;     // state read by the kernel (SoA, stride np)
+    float* s_out = nullptr;          // state written by G2P
+    const float* s_aux = nullptr;    // adjoint: state of the G2P^T substep (x, F)
+    const float4* V = nullptr;       // grid velocity of the G2P (or G2P^T) substep
+    float4* acc = nullptr;           // P2G accumulator
+    float4* Vbar = nullptr;          // G2P^T scatter target
+    const float4* gadj = nullptr;    // grid adjoint (mbar, mvbar) of the P2G^T substep
+    float* adj = nullptr;            // particle adjoint (SoA, stride np)
+    const float* phi = nullptr;      // current-order design (stride np)
+    const float* mag = nullptr;
+    float* gphi = nullptr;           // current-order design gradients
+    float* gmag = nullptr;
+    const float* field = nullptr;    // [inst][n_steps][D]
+    float* gfield = nullptr;
+    float* mom = nullptr;            // [n_steps][n_inst] sum_p m_p v_x after each substep
+    const float* Minst = nullptr;    // [n_inst] instance mass
+    const float* dloss = nullptr;    // [n_inst]
+    const int* inst_off = nullptr;   // [n_inst + 1]
+    int* err = nullptr;
+    int n_p2g = 0;                   // substep index of the P2G (or P2G^T) part
+    int n_g2p = 0;                   // substep index of the G2P part (momentum row)
+};
+
+// forward particle kernel: G2P of substep n_g2p and/or P2G of n_p2g.
+// write_all: also store v and C (needed at checkpoints and in the store pass).
+cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, const Params& P,
+                           const StepArgs& a, int block, cudaStream_t st);
+// adjoint particle kernel: P2G^T of substep n_p2g and/or G2P^T of n_p2g - 1
+// (or, without P2G^T, of substep n_p2g).
+cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, const Params& P, const StepArgs& a,
+                           int block, cudaStream_t st);
+// grid operation on every node of every instance: acc -> V; clears acc
+// (lean) or clears acc_next (store pass).
+cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,
+                        bool clear_acc, cudaStream_t st);
+// grid adjoint: Vbar -> gadj (clears Vbar).
+cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, float4* Vbar,
+                                float4* gadj, cudaStream_t st);
+
+// initial state from x0 / v0 (input order): C = 0, F = I, id = p.
+cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0,
+                              float* s, int* id, cudaStream_t st);
+// dst[c][p] = src[c][perm[p]] for every component, id_dst[p] = id_src[perm[p]].
+cudaError_t launch_reorder(int ncomp, const Params& P, const float* src, float* dst,
+                           const int* perm, const int* id_src, int* id_dst, cudaStream_t st);
+// adj_old[c][perm[p]] = adj_new[c][p]
+cudaError_t launch_unpermute(int ncomp, const Params& P, const float* src, float* dst,
+                             const int* perm, cudaStream_t st);
+// out[c][id[p]] = s[c][p] for components [c0, c0 + ncomp), out stride n_total
+cudaError_t launch_to_input_order(int ncomp, const Params& P, const float* s, int c0,
+                                  const int* id, float* out, cudaStream_t st);
+// current-order design from the per-design arrays
+cudaError_t launch_gather_design(int dim, const Params& P, const int* id, const int* inst_off,
+                                 const int* dbase, const float* phi_d, const float* mag_d,
+                                 long long nd, float* phi, float* mag, cudaStream_t st);
+// per-design gradients += current-order gradients
+cudaError_t launch_scatter_design_grad(int dim, const Params& P, const int* id,
+                                       const int* inst_off, const int* dbase, const float* gphi,
+                                       const float* gmag, long long nd, float* g_phi,
+                                       float* g_mag, cudaStream_t st);
+cudaError_t launch_instance_mass(const Params& P, const float* phi, const int* inst_off,
+                                 float* Minst, cudaStream_t st);
+cudaError_t launch_loss(int dim, const Params& P, const float* s, const float* target,
+                        const int* id, const int* inst_off, const float* Minst, const float* mom,
+                        float* loss_acc, float* loss_out, cudaStream_t st);
+cudaError_t launch_seed(int dim, const Params& P, const float* s, const float* target,
+                        const int* id, const int* inst_off, const float* phi, const float* Minst,
+                        const float* mom, const float* dloss, float* adj, float* gphi,
+                        cudaStream_t st);
+
+// ---- sort (kernels_sort.cu) ----
+struct SortBuffers {
+    int* keys = nullptr;       // [N]
+    int* slot = nullptr;       // [N]
+    int* counts = nullptr;     // [n_keys]
+    int* offsets = nullptr;    // [n_keys]
+    int* scan_tmp = nullptr;   // block sums of the recursive scan
+    long long scan_tmp_len = 0;
+    long long n_keys = 0;
+};
+long long sort_key_space(int dim, int res, int n_inst);
+long long sort_scan_tmp_len(long long n_keys);
+// keys, stable permutation perm[new] = old for positions x (component stride
+// xstride); flags kErrDomain for stencils outside the grid (keys clamp).
+cudaError_t launch_sort(int dim, const Params& P, const float* x, long long xstride,
+                        const int* inst_off, SortBuffers& sb, int* perm, int* err,
+                        cudaStream_t st);
+
+}  // namespace mpm

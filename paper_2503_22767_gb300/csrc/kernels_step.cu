@@ -1,0 +1,760 @@
+// Substep kernels of the magneto-elastic MLS-MPM and its reverse mode.
+//
+// Forward (arxiv 2503.22767, Section 2.2): the particle kernel fuses the G2P
+// of substep n (Eq. 19-22) with the P2G of substep n+1 (Eq. 14-15 with the
+// SIMP-scaled stress of Eq. 7/31-33), so between substeps a particle's state
+// is read once and written once; the grid kernel applies Eq. 16-18.
+// Reverse (Section 2.3): the particle kernel fuses the P2G^T of substep n with
+// the G2P^T of substep n-1; the grid kernel reverses Eq. 16-18 with the
+// forward branches replayed.
+//
+// Particle arrays are structure-of-arrays with component stride P.np:
+// x[D], v[D], C[D][D], F[D][D] (row-major), i.e. 2D + 2D^2 components.
+// Grids are float4 per node ([inst][node]): accumulators (m, mv), velocities
+// (v, 0), adjoints (mbar, mvbar).
+#include "kernels.h"
+
+namespace mpm {
+
+namespace {
+
+template <int D>
+struct Layout {
+    static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, N = 2 * D + 2 * D * D;
+};
+
+template <int D>
+__device__ __forceinline__ float4 pack4(float a, const float (&v)[D]) {
+    return make_float4(a, v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f);
+}
+
+template <int D>
+__device__ __forceinline__ void unpack3(const float4& g, float (&v)[D]) {
+    v[0] = g.x;
+    v[1 % D] = g.y;
+    if (D == 3) v[2 % D] = g.z;
+}
+
+template <int D>
+__device__ __forceinline__ void load_vec(const float* __restrict__ s, int base, long long np, int p,
+                                         float (&v)[D]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = s[(long long)(base + a) * np + p];
+}
+
+template <int D>
+__device__ __forceinline__ void load_mat(const float* __restrict__ s, int base, long long np, int p,
+                                         float (&M)[D][D]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) M[a][b] = s[(long long)(base + a * D + b) * np + p];
+}
+
+template <int D>
+__device__ __forceinline__ void store_vec(float* __restrict__ s, int base, long long np, int p,
+                                          const float (&v)[D]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) s[(long long)(base + a) * np + p] = v[a];
+}
+
+template <int D>
+__device__ __forceinline__ void store_mat(float* __restrict__ s, int base, long long np, int p,
+                                          const float (&M)[D][D]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) s[(long long)(base + a * D + b) * np + p] = M[a][b];
+}
+
+constexpr int kStencil2 = 9, kStencil3 = 27;
+template <int D>
+constexpr int stencil_size() { return D == 2 ? kStencil2 : kStencil3; }
+
+// ---------------------------------------------------------------------------
+// forward particle kernel
+// ---------------------------------------------------------------------------
+template <int D, bool G2P, bool P2G, bool WRITE_ALL>
+__global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
+    using L = Layout<D>;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = p < P.n_total;
+    const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
+    const long long np = P.np;
+    int flags = 0;
+    float x[D], v[D], C[D][D], F[D][D];
+    float phi = 0.0f, mp = 0.0f;
+    if (active) {
+        load_vec<D>(a.s_in, L::X, np, p, x);
+        load_mat<D>(a.s_in, L::F, np, p, F);
+        phi = a.phi[p];
+        mp = phi * P.rho0 * P.p_vol;  // Eq. 33
+        if (!G2P) {
+            load_vec<D>(a.s_in, L::V, np, p, v);
+            load_mat<D>(a.s_in, L::C, np, p, C);
+        }
+    }
+    if (G2P) {
+        float mom_x[1] = {0.0f};
+        if (active) {
+            Stencil<D> s;
+            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+            const float4* __restrict__ Vi = a.V + (long long)inst * P.nodes;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                v[i] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) C[i][j] = 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < stencil_size<D>(); ++k) {
+                NodeTerm<D> t;
+                node_term<D>(s, k, P, t);
+                float gv[D];
+                unpack3<D>(__ldg(Vi + t.node), gv);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    v[i] += t.w * gv[i];                          // Eq. 19
+#pragma unroll
+                    for (int j = 0; j < D; ++j) C[i][j] += t.w * gv[i] * t.dpos[j];  // Eq. 20
+                }
+            }
+            float Fn[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) C[i][j] *= P.kappa;
+                x[i] += P.dt * v[i];                              // Eq. 21
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float acc = F[i][j];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc += P.dt * C[i][k] * F[k][j];  // Eq. 22
+                    Fn[i][j] = acc;
+                }
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) F[i][j] = Fn[i][j];
+            float J = det<D>(F);
+            if (!(J > 0.0f) || !isfinite(J)) flags |= kErrNumeric;
+            store_vec<D>(a.s_out, L::X, np, p, x);
+            store_mat<D>(a.s_out, L::F, np, p, F);
+            if (WRITE_ALL) {
+                store_vec<D>(a.s_out, L::V, np, p, v);
+                store_mat<D>(a.s_out, L::C, np, p, C);
+            }
+            mom_x[0] = mp * v[0];
+        }
+        if (P.loss_kind == 1 && a.mom != nullptr)
+            warp_add_per_instance<1>(mom_x, inst, a.mom + (long long)a.n_g2p * P.n_inst, 1);
+    }
+    if (P2G && active) {
+        Stencil<D> s;
+        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        StressParts<D> S;
+        stress_parts<D>(F, phi, P, S);
+        if (!(S.J > 0.0f)) flags |= kErrNumeric;
+        float Br[D], Ba[D], Pk[D][D], A[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            Br[i] = a.mag[(long long)i * np + p];
+            Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
+        }
+        piola<D>(F, S, Br, Ba, Pk);
+        const float sc = P.dt * P.kappa * P.p_vol;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                float pft = 0.0f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
+                A[i][j] = mp * C[i][j] - sc * pft;  // affine momentum, reading R1
+            }
+        float4* __restrict__ ai = a.acc + (long long)inst * P.nodes;
+#pragma unroll
+        for (int k = 0; k < stencil_size<D>(); ++k) {
+            NodeTerm<D> t;
+            node_term<D>(s, k, P, t);
+            float mv[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float ad = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) ad += A[i][j] * t.dpos[j];
+                mv[i] = t.w * (mp * v[i] + ad);   // Eq. 15
+            }
+            atomicAdd(ai + t.node, pack4<D>(t.w * mp, mv));  // Eq. 14 in .x
+        }
+    }
+    if (flags) atomicOr(a.err, flags);
+}
+
+// ---------------------------------------------------------------------------
+// grid operation (Eq. 16-18)
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) k_grid(Params P, float4* __restrict__ acc,
+                                              float4* __restrict__ V, float4* __restrict__ acc_next,
+                                              bool clear_acc, long long total) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    float4 g = acc[i];
+    int c[D];
+    node_coords<D>(i % P.nodes, P.res, c);
+    float mv[D], v[D];
+    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+    grid_velocity<D>(P, c, g.x, mv, v);
+    V[i] = make_float4(v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f, 0.0f);
+    if (clear_acc) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (acc_next) acc_next[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __restrict__ acc,
+                                                      float4* __restrict__ Vbar,
+                                                      float4* __restrict__ gadj, long long total) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    float4 g = acc[i];
+    float4 vb4 = Vbar[i];
+    Vbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int c[D];
+    node_coords<D>(i % P.nodes, P.res, c);
+    float mv[D], vb[D], mvb[D], mb;
+    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+    unpack3<D>(vb4, vb);
+    grid_velocity_adjoint<D>(P, c, g.x, mv, vb, mb, mvb);
+    gadj[i] = pack4<D>(mb, mvb);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint particle kernel
+//   P2GT: reverse of P2G at substep n = a.n_p2g; completes the particle
+//         adjoint of state n (x, v, C, F), accumulates design gradients.
+//   G2PT: reverse of G2P at substep m (= n-1 when fused, else n): consumes
+//         the adjoint of state m+1, scatters Vbar, writes the partial
+//         adjoint (x, F) of state m.
+// ---------------------------------------------------------------------------
+template <int D, bool P2GT, bool G2PT>
+__global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
+    using L = Layout<D>;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = p < P.n_total;
+    const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
+    const long long np = P.np;
+    int flags = 0;
+    // adjoint of the state between the two halves (state n if P2GT)
+    float xb[D], vb[D], Cb[D][D], Fb[D][D];
+    float Cn[D][D];  // C of state n (= m+1), needed by G2P^T
+    float bab[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) bab[i] = 0.0f;
+    if (P2GT) {
+        if (active) {
+            const int n = a.n_p2g;
+            float x[D], v[D], F[D][D];
+            load_vec<D>(a.s_in, L::X, np, p, x);
+            load_vec<D>(a.s_in, L::V, np, p, v);
+            load_mat<D>(a.s_in, L::C, np, p, Cn);
+            load_mat<D>(a.s_in, L::F, np, p, F);
+            load_vec<D>(a.adj, L::X, np, p, xb);
+            load_mat<D>(a.adj, L::F, np, p, Fb);
+            const float phi = a.phi[p];
+            const float mp = phi * P.rho0 * P.p_vol;
+            float Br[D], Ba[D], Pk[D][D], A[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                Br[i] = a.mag[(long long)i * np + p];
+                Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + n) * D + i);
+            }
+            Stencil<D> s;
+            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+            StressParts<D> S;
+            stress_parts<D>(F, phi, P, S);
+            piola<D>(F, S, Br, Ba, Pk);
+            const float sc = P.dt * P.kappa * P.p_vol;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float pft = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
+                    A[i][j] = mp * Cn[i][j] - sc * pft;
+                }
+            float mpb = 0.0f, Ab[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                vb[i] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) Ab[i][j] = 0.0f;
+            }
+            const float4* __restrict__ gi = a.gadj + (long long)inst * P.nodes;
+#pragma unroll
+            for (int k = 0; k < stencil_size<D>(); ++k) {
+                NodeTerm<D> t;
+                node_term<D>(s, k, P, t);
+                float4 g = __ldg(gi + t.node);
+                float mvb[D];
+                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
+                // value of this node's contribution: w * (mb mp + mvb . (mp v + A dpos))
+                float inner = g.x * mp, vcd = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    float ad = 0.0f, cd = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        ad += A[i][j] * t.dpos[j];
+                        cd += Cn[i][j] * t.dpos[j];
+                    }
+                    inner += mvb[i] * (mp * v[i] + ad);
+                    vcd += mvb[i] * (v[i] + cd);
+                }
+                mpb += t.w * (g.x + vcd);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    vb[i] += t.w * mp * mvb[i];
+#pragma unroll
+                    for (int j = 0; j < D; ++j) Ab[i][j] += t.w * mvb[i] * t.dpos[j];
+                }
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    float atm = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) atm += A[i][c] * mvb[i];
+                    xb[c] += t.gw[c] * inner - t.w * atm;
+                }
+            }
+            // A = mp C - sc P F^T
+            float Pb[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) Cb[i][j] = mp * Ab[i][j];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float pb = 0.0f, fb = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        pb += Ab[i][k] * F[k][j];    // (Abar F)_ij
+                        fb += Ab[k][i] * Pk[k][j];   // (Abar^T P)_ij
+                    }
+                    Pb[i][j] = -sc * pb;
+                    Fb[i][j] -= sc * fb;
+                }
+            float phib = 0.0f, brb[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) brb[i] = 0.0f;
+            piola_adjoint<D>(F, phi, S, Br, Ba, Pb, P, Fb, phib, brb, bab);
+            float gph = phib + mpb * P.rho0 * P.p_vol;
+            // locomotion seed on state n (n >= 1), Eq. 40
+            if (P.loss_kind == 1 && n >= 1) {
+                const float M = a.Minst[inst];
+                if (M > 0.0f) {
+                    const float dl = a.dloss[inst];
+                    const float rM = 1.0f / M;
+                    const float vbar = a.mom[(long long)(n - 1) * P.n_inst + inst] * rM;
+                    vb[0] -= P.dt * mp * rM * dl;
+                    gph -= P.dt * (v[0] - vbar) * rM * dl * P.rho0 * P.p_vol;
+                }
+            }
+            a.gphi[p] += gph;
+#pragma unroll
+            for (int i = 0; i < D; ++i) a.gmag[(long long)i * np + p] += brb[i];
+        }
+        warp_add_per_instance<D>(bab, inst, a.gfield + (long long)a.n_p2g * D,
+                                 (long long)P.n_steps * D);
+        if (!G2PT && active) {
+            store_vec<D>(a.adj, L::X, np, p, xb);
+            store_vec<D>(a.adj, L::V, np, p, vb);
+            store_mat<D>(a.adj, L::C, np, p, Cb);
+            store_mat<D>(a.adj, L::F, np, p, Fb);
+        }
+    }
+    if (G2PT && active) {
+        if (!P2GT) {
+            // adjoint of state m+1 and C_{m+1} from memory
+            load_vec<D>(a.adj, L::X, np, p, xb);
+            load_vec<D>(a.adj, L::V, np, p, vb);
+            load_mat<D>(a.adj, L::C, np, p, Cb);
+            load_mat<D>(a.adj, L::F, np, p, Fb);
+            load_mat<D>(a.s_in, L::C, np, p, Cn);
+        }
+        float x[D], F[D][D];
+        load_vec<D>(a.s_aux, L::X, np, p, x);
+        load_mat<D>(a.s_aux, L::F, np, p, F);
+        Stencil<D> s;
+        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
+        float vt[D], Ct[D][D], Fo[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) vt[i] = vb[i] + P.dt * xb[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                float fft = 0.0f, ctf = Fb[i][j];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    fft += Fb[i][k] * F[j][k];          // (Fbar F^T)_ij
+                    ctf += P.dt * Cn[k][i] * Fb[k][j];  // ((I + dt C')^T Fbar)_ij
+                }
+                Ct[i][j] = Cb[i][j] + P.dt * fft;
+                Fo[i][j] = ctf;
+            }
+        const float4* __restrict__ Vi = a.V + (long long)inst * P.nodes;
+        float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
+#pragma unroll
+        for (int k = 0; k < stencil_size<D>(); ++k) {
+            NodeTerm<D> t;
+            node_term<D>(s, k, P, t);
+            float gv[D];
+            unpack3<D>(__ldg(Vi + t.node), gv);
+            // Eq. 19-20 reversed: v' = sum w V, C' = kappa sum w V dpos^T
+            float vdot = 0.0f, vcd = 0.0f, cd[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                cd[i] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) cd[i] += Ct[i][j] * t.dpos[j];
+                vdot += gv[i] * vt[i];
+                vcd += gv[i] * cd[i];
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                float ctv = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) ctv += Ct[i][c] * gv[i];
+                xb[c] += t.gw[c] * (vdot + P.kappa * vcd) - P.kappa * t.w * ctv;
+            }
+            float sv[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) sv[i] = t.w * (vt[i] + P.kappa * cd[i]);
+            float4 c4 = make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f);
+            atomicAdd(Vbi + t.node, c4);
+        }
+        store_vec<D>(a.adj, L::X, np, p, xb);
+        store_mat<D>(a.adj, L::F, np, p, Fo);
+    }
+    if (flags) atomicOr(a.err, flags);
+}
+
+// ---------------------------------------------------------------------------
+// helpers: init, permutations, design, loss and seeds
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_init_state(Params P, const float* __restrict__ x0, const float* __restrict__ v0,
+                             float* __restrict__ s, int* __restrict__ id) {
+    using L = Layout<D>;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_total) return;
+    const long long np = P.np, n = P.n_total;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        s[(L::X + i) * np + p] = x0[i * n + p];
+        s[(L::V + i) * np + p] = v0 ? v0[i * n + p] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            s[(L::C + i * D + j) * np + p] = 0.0f;
+            s[(L::F + i * D + j) * np + p] = (i == j) ? 1.0f : 0.0f;
+        }
+    }
+    id[p] = p;
+}
+
+__global__ void k_reorder(Params P, int ncomp, const float* __restrict__ src, float* __restrict__ dst,
+                          const int* __restrict__ perm, const int* __restrict__ id_src,
+                          int* __restrict__ id_dst) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_total) return;
+    int q = perm[p];
+    for (int c = 0; c < ncomp; ++c) dst[c * P.np + p] = src[c * P.np + q];
+    if (id_dst) id_dst[p] = id_src[q];
+}
+
+__global__ void k_unpermute(Params P, int ncomp, const float* __restrict__ src,
+                            float* __restrict__ dst, const int* __restrict__ perm) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_total) return;
+    int q = perm[p];
+    for (int c = 0; c < ncomp; ++c) dst[c * P.np + q] = src[c * P.np + p];
+}
+
+__global__ void k_to_input_order(Params P, int ncomp, const float* __restrict__ s, int c0,
+                                 const int* __restrict__ id, float* __restrict__ out) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_total) return;
+    int q = id[p];
+    for (int c = 0; c < ncomp; ++c) out[(long long)c * P.n_total + q] = s[(c0 + c) * P.np + p];
+}
+
+__device__ __forceinline__ long long design_index(int g, const int* __restrict__ inst_off,
+                                                  const int* __restrict__ dbase, int n_inst) {
+    int inst = find_instance(inst_off, n_inst, g);
+    return (long long)dbase[inst] + (g - inst_off[inst]);
+}
+
+template <int D>
+__global__ void k_gather_design(Params P, const int* __restrict__ id, const int* __restrict__ inst_off,
+                                const int* __restrict__ dbase, const float* __restrict__ phi_d,
+                                const float* __restrict__ mag_d, long long nd,
+                                float* __restrict__ phi, float* __restrict__ mag) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_total) return;
+    long long di = design_index(id[p], inst_off, dbase, P.n_inst);
+    phi[p] = phi_d[di];
+#pragma unroll
+    for (int i = 0; i < D; ++i) mag[i * P.np + p] = mag_d[i * nd + di];
+}
+
+template <int D>
+__global__ void k_scatter_design_grad(Params P, const int* __restrict__ id,
+                                      const int* __restrict__ inst_off,
+                                      const int* __restrict__ dbase, const float* __restrict__ gphi,
+                                      const float* __restrict__ gmag, long long nd,
+                                      float* __restrict__ g_phi, float* __restrict__ g_mag) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_total) return;
+    long long di = design_index(id[p], inst_off, dbase, P.n_inst);
+    if (g_phi) atomicAdd(g_phi + di, gphi[p]);
+    if (g_mag) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) atomicAdd(g_mag + i * nd + di, gmag[i * P.np + p]);
+    }
+}
+
+__global__ void k_instance_mass(Params P, const float* __restrict__ phi,
+                                const int* __restrict__ inst_off, float* __restrict__ Minst) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = p < P.n_total;
+    int inst = active ? find_instance(inst_off, P.n_inst, p) : -1;
+    float m[1] = {active ? phi[p] * P.rho0 * P.p_vol : 0.0f};
+    warp_add_per_instance<1>(m, inst, Minst, 1);
+}
+
+template <int D>
+__global__ void k_loss_mse(Params P, const float* __restrict__ s, const float* __restrict__ target,
+                           const int* __restrict__ id, const int* __restrict__ inst_off,
+                           float* __restrict__ loss_acc) {
+    using L = Layout<D>;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = p < P.n_total;
+    int inst = active ? find_instance(inst_off, P.n_inst, p) : -1;
+    float e2[1] = {0.0f};
+    if (active) {
+        int q = id[p];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float e = s[(L::X + i) * P.np + p] - target[(long long)i * P.n_total + q];
+            e2[0] += e * e;
+        }
+    }
+    warp_add_per_instance<1>(e2, inst, loss_acc, 1);
+}
+
+__global__ void k_loss_finalize(Params P, const int* __restrict__ inst_off,
+                                const float* __restrict__ Minst, const float* __restrict__ mom,
+                                const float* __restrict__ loss_acc, float* __restrict__ loss_out) {
+    int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= P.n_inst) return;
+    if (P.loss_kind == 1) {
+        float M = Minst[inst];
+        double acc = 0.0;
+        for (int n = 0; n < P.n_steps; ++n) acc += mom[(long long)n * P.n_inst + inst];
+        loss_out[inst] = M > 0.0f ? (float)(-(double)P.dt * acc / M) : 0.0f;
+    } else {
+        int cnt = inst_off[inst + 1] - inst_off[inst];
+        loss_out[inst] = cnt > 0 ? loss_acc[inst] / (float)cnt : 0.0f;
+    }
+}
+
+template <int D>
+__global__ void k_seed(Params P, const float* __restrict__ s, const float* __restrict__ target,
+                       const int* __restrict__ id, const int* __restrict__ inst_off,
+                       const float* __restrict__ phi, const float* __restrict__ Minst,
+                       const float* __restrict__ mom, const float* __restrict__ dloss,
+                       float* __restrict__ adj, float* __restrict__ gphi) {
+    using L = Layout<D>;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_total) return;
+    int inst = find_instance(inst_off, P.n_inst, p);
+    const long long np = P.np;
+    for (int c = 0; c < L::N; ++c) adj[c * np + p] = 0.0f;
+    float dl = dloss[inst];
+    if (P.loss_kind == 1) {
+        float M = Minst[inst];
+        if (M > 0.0f && P.n_steps > 0) {
+            float rM = 1.0f / M;
+            float mp = phi[p] * P.rho0 * P.p_vol;
+            float vx = s[L::V * np + p];
+            float vbar = mom[(long long)(P.n_steps - 1) * P.n_inst + inst] * rM;
+            adj[L::V * np + p] = -P.dt * mp * rM * dl;
+            gphi[p] -= P.dt * (vx - vbar) * rM * dl * P.rho0 * P.p_vol;
+        }
+    } else {
+        int cnt = inst_off[inst + 1] - inst_off[inst];
+        int q = id[p];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float e = s[(L::X + i) * np + p] - target[(long long)i * P.n_total + q];
+            adj[(L::X + i) * np + p] = 2.0f * e / (float)cnt * dl;
+        }
+    }
+}
+
+inline int blocks_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int D>
+static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, const StepArgs& a,
+                             int block, cudaStream_t st) {
+    dim3 grid(blocks_for(P.n_total, block));
+    if (P.n_total == 0) return cudaSuccess;
+    if (g2p && p2g) {
+        if (all) k_forward<D, true, true, true><<<grid, block, 0, st>>>(P, a);
+        else k_forward<D, true, true, false><<<grid, block, 0, st>>>(P, a);
+    } else if (g2p) {
+        if (all) k_forward<D, true, false, true><<<grid, block, 0, st>>>(P, a);
+        else k_forward<D, true, false, false><<<grid, block, 0, st>>>(P, a);
+    } else {
+        k_forward<D, false, true, false><<<grid, block, 0, st>>>(P, a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, const Params& P,
+                           const StepArgs& a, int block, cudaStream_t st) {
+    return dim == 2 ? forward_d<2>(g2p, p2g, write_all, P, a, block, st)
+                    : forward_d<3>(g2p, p2g, write_all, P, a, block, st);
+}
+
+template <int D>
+static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepArgs& a, int block,
+                             cudaStream_t st) {
+    dim3 grid(blocks_for(P.n_total, block));
+    if (P.n_total == 0) return cudaSuccess;
+    if (p2gt && g2pt) k_adjoint<D, true, true><<<grid, block, 0, st>>>(P, a);
+    else if (p2gt) k_adjoint<D, true, false><<<grid, block, 0, st>>>(P, a);
+    else k_adjoint<D, false, true><<<grid, block, 0, st>>>(P, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, const Params& P, const StepArgs& a,
+                           int block, cudaStream_t st) {
+    return dim == 2 ? adjoint_d<2>(p2gt, g2pt, P, a, block, st)
+                    : adjoint_d<3>(p2gt, g2pt, P, a, block, st);
+}
+
+cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,
+                        bool clear_acc, cudaStream_t st) {
+    long long total = P.nodes * P.n_inst;
+    dim3 grid(blocks_for(total, 256));
+    if (dim == 2) k_grid<2><<<grid, 256, 0, st>>>(P, acc, V, acc_next, clear_acc, total);
+    else k_grid<3><<<grid, 256, 0, st>>>(P, acc, V, acc_next, clear_acc, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, float4* Vbar,
+                                float4* gadj, cudaStream_t st) {
+    long long total = P.nodes * P.n_inst;
+    dim3 grid(blocks_for(total, 256));
+    if (dim == 2) k_grid_adjoint<2><<<grid, 256, 0, st>>>(P, acc, Vbar, gadj, total);
+    else k_grid_adjoint<3><<<grid, 256, 0, st>>>(P, acc, Vbar, gadj, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0, float* s,
+                              int* id, cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    dim3 grid(blocks_for(P.n_total, 256));
+    if (dim == 2) k_init_state<2><<<grid, 256, 0, st>>>(P, x0, v0, s, id);
+    else k_init_state<3><<<grid, 256, 0, st>>>(P, x0, v0, s, id);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(int ncomp, const Params& P, const float* src, float* dst,
+                           const int* perm, const int* id_src, int* id_dst, cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    k_reorder<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, ncomp, src, dst, perm, id_src, id_dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(int ncomp, const Params& P, const float* src, float* dst,
+                             const int* perm, cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    k_unpermute<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, ncomp, src, dst, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_input_order(int ncomp, const Params& P, const float* s, int c0,
+                                  const int* id, float* out, cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    k_to_input_order<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, ncomp, s, c0, id, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_design(int dim, const Params& P, const int* id, const int* inst_off,
+                                 const int* dbase, const float* phi_d, const float* mag_d,
+                                 long long nd, float* phi, float* mag, cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    dim3 grid(blocks_for(P.n_total, 256));
+    if (dim == 2) k_gather_design<2><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, phi_d, mag_d, nd, phi, mag);
+    else k_gather_design<3><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, phi_d, mag_d, nd, phi, mag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_design_grad(int dim, const Params& P, const int* id,
+                                       const int* inst_off, const int* dbase, const float* gphi,
+                                       const float* gmag, long long nd, float* g_phi,
+                                       float* g_mag, cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    dim3 grid(blocks_for(P.n_total, 256));
+    if (dim == 2)
+        k_scatter_design_grad<2><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, gphi, gmag, nd, g_phi, g_mag);
+    else
+        k_scatter_design_grad<3><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, gphi, gmag, nd, g_phi, g_mag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_instance_mass(const Params& P, const float* phi, const int* inst_off,
+                                 float* Minst, cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    k_instance_mass<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, phi, inst_off, Minst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(int dim, const Params& P, const float* s, const float* target,
+                        const int* id, const int* inst_off, const float* Minst, const float* mom,
+                        float* loss_acc, float* loss_out, cudaStream_t st) {
+    if (P.loss_kind == 0 && P.n_total > 0) {
+        dim3 grid(blocks_for(P.n_total, 256));
+        if (dim == 2) k_loss_mse<2><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, loss_acc);
+        else k_loss_mse<3><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, loss_acc);
+    }
+    k_loss_finalize<<<blocks_for(P.n_inst, 64), 64, 0, st>>>(P, inst_off, Minst, mom, loss_acc, loss_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed(int dim, const Params& P, const float* s, const float* target,
+                        const int* id, const int* inst_off, const float* phi, const float* Minst,
+                        const float* mom, const float* dloss, float* adj, float* gphi,
+                        cudaStream_t st) {
+    if (P.n_total == 0) return cudaSuccess;
+    dim3 grid(blocks_for(P.n_total, 256));
+    if (dim == 2) k_seed<2><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, phi, Minst, mom, dloss, adj, gphi);
+    else k_seed<3><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, phi, Minst, mom, dloss, adj, gphi);
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

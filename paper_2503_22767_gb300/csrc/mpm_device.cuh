@@ -1,0 +1,444 @@
+// Device building blocks of the magneto-elastic MLS-MPM substep (sm_103a).
+//
+// Templated on the spatial dimension D (2 or 3).  Everything here is
+// single-precision and register-resident; the kernels that use it live in
+// kernels_step.cu.  Equations refer to arxiv 2503.22767.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpm {
+
+constexpr float kMu0 = 1.25663706143591729e-6f;  // vacuum permeability 4 pi 1e-7
+
+enum ErrBits : int { kErrNumeric = 1, kErrDomain = 2, kErrTimeout = 4 };
+
+// Scalar parameters every kernel receives by value.
+struct Params {
+    int res;         // nodes per axis
+    int bound;       // wall band width in nodes
+    int wall_mode;   // 0 all non-slip, 1 Coulomb floor on axis 1 (low side)
+    int loss_kind;   // 0 shape MSE (Eq. 38), 1 locomotion (Eq. 40)
+    int simp_q;      // SIMP exponent (Eq. 31)
+    int n_inst;      // instances
+    int n_steps;     // horizon N
+    int n_total;     // particles (all instances)
+    long long np;    // stride between SoA components of particle arrays
+    long long nodes; // nodes per instance grid (res^D)
+    float dx, inv_dx, dt, kappa;  // kappa = 4/dx^2 (inverse B-spline inertia)
+    float p_vol, rho0, G, K, eps, damping, mu;
+    float gravity[3];
+};
+
+// Index of the instance owning particle p (instance ranges are contiguous
+// and survive the cell sort, whose key starts with the instance).
+__device__ __forceinline__ int find_instance(const int* __restrict__ inst_off, int n_inst, int p) {
+    int lo = 0, hi = n_inst;  // inst_off[lo] <= p < inst_off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(inst_off + mid) <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// quadratic B-spline stencil (Section 2.2 step 1): base = floor(x/dx - 0.5)
+// ---------------------------------------------------------------------------
+template <int D>
+struct Stencil {
+    int base[D];
+    float r[D];       // x/dx - base, in [0.5, 1.5) for a particle inside the grid
+    float w[D][3];    // 1D weights per axis
+    float dw[D][3];   // their derivatives with respect to x/dx
+};
+
+// Returns false (and clamps the base so every node index stays in range) when
+// the particle's stencil leaves the grid or its position is not finite.
+template <int D>
+__device__ __forceinline__ bool make_stencil(const float (&x)[D], const Params& P, Stencil<D>& s) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        float fx = __fmul_rn(x[a], P.inv_dx);
+        float fb = floorf(__fsub_rn(fx, 0.5f));
+        int b;
+        if (fb >= 0.0f && fb <= (float)(P.res - 3)) {
+            b = (int)fb;
+        } else {
+            ok = false;
+            b = (fb > 0.0f) ? P.res - 3 : 0;  // NaN lands here too
+        }
+        float r = fx - (float)b;
+        s.base[a] = b;
+        s.r[a] = r;
+        float u0 = 1.5f - r, u1 = r - 1.0f, u2 = r - 0.5f;
+        s.w[a][0] = 0.5f * u0 * u0;
+        s.w[a][1] = 0.75f - u1 * u1;
+        s.w[a][2] = 0.5f * u2 * u2;
+        s.dw[a][0] = -u0;
+        s.dw[a][1] = -2.0f * u1;
+        s.dw[a][2] = u2;
+    }
+    return ok;
+}
+
+template <int D>
+struct NodeTerm {
+    long long node;  // node index within the instance grid
+    float w;         // weight N(x_p - x_i)
+    float gw[D];     // d w / d x_p
+    float dpos[D];   // x_i - x_p
+};
+
+template <int D>
+__device__ __forceinline__ void node_term(const Stencil<D>& s, int k, const Params& P, NodeTerm<D>& t) {
+    int o[D];
+    if (D == 2) {
+        o[0] = k / 3;
+        o[D - 1] = k % 3;
+    } else {
+        o[0] = k / 9;
+        o[1 % D] = (k / 3) % 3;
+        o[D - 1] = k % 3;
+    }
+    float w = 1.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) w *= s.w[a][o[a]];
+    t.w = w;
+    long long idx = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        float g = s.dw[c][o[c]] * P.inv_dx;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (a != c) g *= s.w[a][o[a]];
+        t.gw[c] = g;
+        t.dpos[c] = ((float)o[c] - s.r[c]) * P.dx;
+        idx = idx * P.res + (s.base[c] + o[c]);
+    }
+    t.node = idx;
+}
+
+// ---------------------------------------------------------------------------
+// small dense algebra
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ float det(const float (&F)[D][D]) {
+    if (D == 2) return F[0][0] * F[1 % D][1 % D] - F[0][1 % D] * F[1 % D][0];
+    return F[0][0] * (F[1][1] * F[2 % D][2 % D] - F[1][2 % D] * F[2 % D][1]) -
+           F[0][1] * (F[1][0] * F[2 % D][2 % D] - F[1][2 % D] * F[2 % D][0]) +
+           F[0][2 % D] * (F[1][0] * F[2 % D][1] - F[1][1] * F[2 % D][0]);
+}
+
+// H = F^{-T} = cofactor(F) / J
+template <int D>
+__device__ __forceinline__ void inv_transpose(const float (&F)[D][D], float J, float (&H)[D][D]) {
+    float rJ = 1.0f / J;
+    if (D == 2) {
+        H[0][0] = F[1 % D][1 % D] * rJ;
+        H[0][1 % D] = -F[1 % D][0] * rJ;
+        H[1 % D][0] = -F[0][1 % D] * rJ;
+        H[1 % D][1 % D] = F[0][0] * rJ;
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                int i1 = (i + 1) % D, i2 = (i + 2) % D, j1 = (j + 1) % D, j2 = (j + 2) % D;
+                H[i][j] = (F[i1][j1] * F[i2][j2] - F[i1][j2] * F[i2][j1]) * rJ;
+            }
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float frob(const float (&A)[D][D], const float (&B)[D][D]) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) s += A[i][j] * B[i][j];
+    return s;
+}
+
+__device__ __forceinline__ float int_pow(float x, int q) {
+    float r = 1.0f;
+    for (int i = 0; i < q; ++i) r *= x;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// constitutive model: Piola stress of Eq. 7 under the SIMP weights of Eq. 31
+// 2D is plane strain: F3 = diag(F, 1), I1 = |F|^2 + 1, J = det F.
+// ---------------------------------------------------------------------------
+template <int D>
+struct StressParts {
+    float J, I1, a, b;   // a = G J^{-2/3}, b = K J (J - 1)
+    float H[D][D];       // F^{-T}
+    float s, sE;         // phi^q and eps + (1 - eps) phi^q
+};
+
+template <int D>
+__device__ __forceinline__ void stress_parts(const float (&F)[D][D], float phi, const Params& P,
+                                             StressParts<D>& S) {
+    S.J = det<D>(F);
+    inv_transpose<D>(F, S.J, S.H);
+    S.I1 = frob<D>(F, F) + (D == 2 ? 1.0f : 0.0f);
+    float r13 = rcbrtf(S.J);
+    S.a = P.G * r13 * r13;
+    S.b = P.K * S.J * (S.J - 1.0f);
+    S.s = int_pow(phi, P.simp_q);
+    S.sE = P.eps + (1.0f - P.eps) * S.s;
+}
+
+template <int D>
+__device__ __forceinline__ void piola(const float (&F)[D][D], const StressParts<D>& S,
+                                      const float (&Br)[D], const float (&Ba)[D],
+                                      float (&Pk)[D][D]) {
+    float third = S.I1 * (1.0f / 3.0f);
+    float sm = S.s * (1.0f / kMu0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float pe = S.a * (F[i][j] - third * S.H[i][j]) + S.b * S.H[i][j];
+            Pk[i][j] = S.sE * pe - sm * Ba[i] * Br[j];
+        }
+}
+
+// Reverse of piola(): given Pbar, accumulate into Fbar and return the
+// phi, B~_r and B_applied cotangents (added to phib, brb, bab).
+//   dJ = J H:dF, dI1 = 2F:dF, d(F^{-T}) = -H dF^T H, d a = -(2/3) a H:dF,
+//   d b = K (2J - 1) J H:dF.
+template <int D>
+__device__ __forceinline__ void piola_adjoint(const float (&F)[D][D], float phi,
+                                              const StressParts<D>& S, const float (&Br)[D],
+                                              const float (&Ba)[D], const float (&Pbar)[D][D],
+                                              const Params& P, float (&Fbar)[D][D], float& phib,
+                                              float (&brb)[D], float (&bab)[D]) {
+    float third = S.I1 * (1.0f / 3.0f);
+    // phi: d s / d phi = q phi^(q-1)
+    float ds = P.simp_q > 0 ? (float)P.simp_q * int_pow(phi, P.simp_q - 1) : 0.0f;
+    float pe_dot = 0.0f, pm_dot = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float pe = S.a * (F[i][j] - third * S.H[i][j]) + S.b * S.H[i][j];
+            pe_dot += Pbar[i][j] * pe;
+            pm_dot -= Pbar[i][j] * Ba[i] * Br[j];
+        }
+    phib += ds * ((1.0f - P.eps) * pe_dot + pm_dot * (1.0f / kMu0));
+    // magnetic part  -(s/mu0) Ba (x) Br
+    float sm = S.s * (1.0f / kMu0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            bab[i] -= sm * Pbar[i][j] * Br[j];
+            brb[j] -= sm * Pbar[i][j] * Ba[i];
+        }
+    // elastic part scaled by sE
+    float Pb[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) Pb[i][j] = S.sE * Pbar[i][j];
+    float PbF = frob<D>(Pb, F);
+    float PbH = frob<D>(Pb, S.H);
+    // X = H Pb^T H
+    float HPt[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < D; ++l) acc += S.H[i][l] * Pb[k][l];  // (H Pb^T)_ik
+            HPt[i][k] = acc;
+        }
+    float cH = -(2.0f / 3.0f) * S.a * (PbF - third * PbH) + P.K * (2.0f * S.J - 1.0f) * S.J * PbH;
+    float cF = -(2.0f / 3.0f) * S.a * PbH;
+    float cX = S.a * third - S.b;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float X = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) X += HPt[i][k] * S.H[k][j];
+            Fbar[i][j] += S.a * Pb[i][j] + cH * S.H[i][j] + cF * F[i][j] + cX * X;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// grid operation on one node (Eq. 16-18).  Bands are applied axis by axis,
+// low side before high side; a band whose wall the velocity points into
+// projects it: Coulomb friction on the floor in wall mode 1, otherwise v = 0.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void node_coords(long long local, int res, int (&c)[D]) {
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+        c[a] = (int)(local % res);
+        local /= res;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void grid_velocity(const Params& P, const int (&c)[D], float m,
+                                              const float (&mv)[D], float (&v)[D]) {
+    if (!(m > 0.0f)) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] = 0.0f;
+        return;
+    }
+    float rm = 1.0f / m;
+    float keep = 1.0f - P.dt * P.damping;
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = keep * (mv[i] * rm) + P.dt * P.gravity[i];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            bool band = side == 0 ? (c[a] < P.bound) : (c[a] >= P.res - P.bound);
+            float vn = side == 0 ? v[a] : -v[a];
+            if (!band || !(vn < 0.0f)) continue;
+            if (P.wall_mode == 1 && a == 1 && side == 0) {
+                float t2 = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    if (i != a) t2 += v[i] * v[i];
+                float u = sqrtf(t2);
+                float sp = u + P.mu * vn;
+                float f = (u > 0.0f && sp > 0.0f) ? sp / u : 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[i] = (i == a) ? 0.0f : v[i] * f;
+            } else {
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[i] = 0.0f;
+            }
+        }
+    }
+}
+
+// Reverse of grid_velocity: Vbar -> (mbar, mvbar).  The forward branches are
+// replayed from (m, mv); overwritten components pass no gradient.
+template <int D>
+__device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int (&c)[D], float m,
+                                                      const float (&mv)[D], const float (&Vbar)[D],
+                                                      float& mbar, float (&mvbar)[D]) {
+    mbar = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) mvbar[i] = 0.0f;
+    if (!(m > 0.0f)) return;
+    float rm = 1.0f / m;
+    float keep = 1.0f - P.dt * P.damping;
+    float v0[D], v[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        v0[i] = mv[i] * rm;
+        v[i] = keep * v0[i] + P.dt * P.gravity[i];
+    }
+    // replay, remembering the input of every projection that fired
+    float vin[2 * D][D];
+    int kind[2 * D];
+    int nops = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            bool band = side == 0 ? (c[a] < P.bound) : (c[a] >= P.res - P.bound);
+            float vn = side == 0 ? v[a] : -v[a];
+            int op = 2 * a + side;
+            kind[op] = 0;
+            if (!band || !(vn < 0.0f)) continue;
+#pragma unroll
+            for (int i = 0; i < D; ++i) vin[op][i] = v[i];
+            ++nops;
+            if (P.wall_mode == 1 && a == 1 && side == 0) {
+                kind[op] = 2;
+                float t2 = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    if (i != a) t2 += v[i] * v[i];
+                float u = sqrtf(t2);
+                float sp = u + P.mu * vn;
+                float f = (u > 0.0f && sp > 0.0f) ? sp / u : 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[i] = (i == a) ? 0.0f : v[i] * f;
+            } else {
+                kind[op] = 1;
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[i] = 0.0f;
+            }
+        }
+    }
+    float vb[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) vb[i] = Vbar[i];
+    if (nops > 0) {
+#pragma unroll
+        for (int op = 2 * D - 1; op >= 0; --op) {
+            if (kind[op] == 1) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) vb[i] = 0.0f;
+            } else if (kind[op] == 2) {
+                const int a = op >> 1;
+                float vn = vin[op][a];
+                float t2 = 0.0f, tdot = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    if (i != a) {
+                        t2 += vin[op][i] * vin[op][i];
+                        tdot += vb[i] * vin[op][i];
+                    }
+                float u = sqrtf(t2);
+                float sp = u + P.mu * vn;
+                if (u > 0.0f && sp > 0.0f) {
+                    float ru = 1.0f / u;
+                    float f = 1.0f + P.mu * vn * ru;
+                    float g = P.mu * vn * tdot * ru * ru * ru;
+                    float out_n = P.mu * tdot * ru;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) vb[i] = (i == a) ? out_n : vb[i] * f - g * vin[op][i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) vb[i] = 0.0f;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float v0b = keep * vb[i];
+        mvbar[i] = v0b * rm;
+        mbar -= v0b * v0[i] * rm;
+    }
+}
+
+// Warp-aggregated add of per-lane values into dst[inst * stride + c]: lanes
+// of one instance are summed with shuffles first (the common case), mixed
+// warps fall back to per-lane atomics.  Every lane of the warp must call it.
+template <int NC>
+__device__ __forceinline__ void warp_add_per_instance(const float (&val)[NC], int inst,
+                                                      float* __restrict__ dst, long long stride) {
+    const unsigned full = 0xffffffffu;
+    int inst0 = __shfl_sync(full, inst, 0);
+    bool uniform = __all_sync(full, inst == inst0 || inst < 0) && inst0 >= 0;
+    if (uniform) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            float s = val[c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(full, s, off);
+            if ((threadIdx.x & 31) == 0 && s != 0.0f) atomicAdd(dst + (long long)inst0 * stride + c, s);
+        }
+    } else if (inst >= 0) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (val[c] != 0.0f) atomicAdd(dst + (long long)inst * stride + c, val[c]);
+    }
+}
+
+}  // namespace mpm

@@ -1,0 +1,833 @@
+// Runtime behind the C ABI of include/mpm.h.
+//
+// One handle owns every device buffer of a batch of simulations (allocated
+// once in mpm_create) and drives the kernels of kernels_step.cu and
+// kernels_sort.cu:
+//
+//   forward   for each segment of K substeps: sort the particles by cell and
+//             reorder the state, save a checkpoint (state, ids, permutation),
+//             then per substep: grid operation, fused G2P(n) + P2G(n+1).
+//             Between substeps only x and F are stored ("lean" pass).
+//   backward  for each segment in reverse: restore its checkpoint, recompute
+//             the K substeps storing every state and grid, then per substep in
+//             reverse: grid adjoint, fused P2G^T(n) + G2P^T(n-1); the particle
+//             adjoint crosses segment boundaries through the saved
+//             permutation; design gradients go back to input order.
+//
+// The paper (arxiv 2503.22767, Section 2.3) differentiates with Taichi's tape;
+// the checkpointed recomputation here is what lets contact-rich horizons of
+// thousands of substeps fit in HBM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mpm.h"
+
+using mpm::Params;
+using mpm::StepArgs;
+
+namespace {
+
+enum KernelClass { kFwdParticle = 0, kAdjParticle = 1, kGrid = 2, kGridAdj = 3, kNumClasses = 4 };
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    double bytes = 0.0;
+};
+
+}  // namespace
+
+struct mpm_handle {
+    // --- configuration ---
+    int dim = 0, res = 0, T = 0, n_inst = 0, K = 0, n_seg = 0, ncomp = 0;
+    long long N = 0, np = 0, Nd = 0, nodes = 0, total_nodes = 0;
+    std::vector<int> counts, inst_off, design_of, dcount, dbase;
+    Params P{};
+    int block = 128;
+    int timing_stride = 0;  // 0 = off; k = time every k-th launch of a class
+    std::string err;
+
+    // --- device buffers ---
+    std::vector<void*> allocs;
+    long long device_bytes = 0;
+    int* d_inst_off = nullptr;
+    int* d_dbase = nullptr;
+    float* stA = nullptr;
+    float* stB = nullptr;
+    int* idA = nullptr;
+    int* idB = nullptr;
+    float* ck_state = nullptr;
+    int* ck_id = nullptr;
+    int* ck_perm = nullptr;
+    float* seg_state = nullptr;
+    float4* seg_acc = nullptr;
+    float4* seg_V = nullptr;
+    float4* acc = nullptr;
+    float4* V = nullptr;
+    float4* Vbar = nullptr;
+    float4* gadj = nullptr;
+    float* adj = nullptr;
+    float* adj2 = nullptr;
+    float* phi_cur = nullptr;
+    float* mag_cur = nullptr;
+    float* gphi_cur = nullptr;
+    float* gmag_cur = nullptr;
+    float* phi_d = nullptr;
+    float* mag_d = nullptr;
+    float* field = nullptr;
+    float* target = nullptr;
+    float* mom = nullptr;
+    float* Minst = nullptr;
+    float* loss_acc = nullptr;
+    float* dloss = nullptr;
+    float* gphi_d = nullptr;
+    float* gmag_d = nullptr;
+    float* gfield_d = nullptr;
+    float* st_x0 = nullptr;
+    float* st_v0 = nullptr;
+    float* st_xout = nullptr;
+    float* st_loss = nullptr;
+    int* d_err = nullptr;
+    int* perm = nullptr;
+    mpm::SortBuffers sb;
+
+    // --- run state ---
+    bool forward_done = false;
+    float* cur = nullptr;  // final state of the last forward
+    int* id_cur = nullptr;
+
+    // --- counters ---
+    long long launches = 0;
+    std::vector<EventPair> events[kNumClasses];
+    size_t ev_used[kNumClasses] = {0, 0, 0, 0};
+    long long class_launch[kNumClasses] = {0, 0, 0, 0};
+    long long timed_launches[kNumClasses] = {0, 0, 0, 0};
+    double timed_ms[kNumClasses] = {0, 0, 0, 0};
+    double timed_bytes[kNumClasses] = {0, 0, 0, 0};
+};
+
+namespace {
+
+#define MPM_CUDA(h, call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return MPM_ERR_CUDA;                                                            \
+        }                                                                                   \
+    } while (0)
+
+int fail(mpm_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+template <typename T>
+int dalloc(mpm_handle* h, T** p, long long count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    size_t bytes = sizeof(T) * (size_t)count;
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA;
+    }
+    h->allocs.push_back(ptr);
+    h->device_bytes += (long long)bytes;
+    *p = (T*)ptr;
+    return MPM_OK;
+}
+
+void free_all(mpm_handle* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    for (int c = 0; c < kNumClasses; ++c) {
+        for (auto& e : h->events[c]) {
+            if (e.a) cudaEventDestroy(e.a);
+            if (e.b) cudaEventDestroy(e.b);
+        }
+        h->events[c].clear();
+    }
+}
+
+// algorithmic bytes of one launch (what the method itself must move; see the
+// repository's design notes for the derivation)
+enum Variant { kFused = 0, kFusedStore = 1, kFirstP2G = 2, kLastG2PT = 3, kFirstP2GT = 4 };
+
+double particle_bytes(int d, int cls, int variant) {
+    const double xf = d + d * d, full = 2 * d + 2 * d * d, design = 1 + d;
+    if (cls == kFwdParticle) {
+        if (variant == kFirstP2G) return 4.0 * (full + design);             // P2G alone
+        return 4.0 * (xf + (variant == kFusedStore ? full : xf) + design);  // G2P(+P2G)
+    }
+    if (variant == kLastG2PT) return 4.0 * (full + d * d + xf + xf);        // G2P^T alone
+    if (variant == kFirstP2GT) return 4.0 * (full + xf + full + 3 * design); // P2G^T alone
+    // fused adjoint: state n (full) + state n-1 (x, F) + partial adjoint
+    // in and out (x, F) + design + design-gradient read-modify-write
+    return 4.0 * (full + xf + 2 * xf + design + 2 * design);
+}
+
+// Launch wrapper: counts launches and, when timing is on, brackets every
+// timing_stride-th launch of the class with CUDA events.
+template <typename F>
+int timed(mpm_handle* h, int cls, double bytes, cudaStream_t st, F&& launch) {
+    bool time_it = h->timing_stride > 0 && (h->class_launch[cls] % h->timing_stride) == 0;
+    h->class_launch[cls]++;
+    h->launches++;
+    EventPair* ev = nullptr;
+    if (time_it) {
+        auto& pool = h->events[cls];
+        if (h->ev_used[cls] == pool.size()) {
+            EventPair e;
+            MPM_CUDA(h, cudaEventCreate(&e.a));
+            MPM_CUDA(h, cudaEventCreate(&e.b));
+            pool.push_back(e);
+        }
+        ev = &pool[h->ev_used[cls]++];
+        ev->bytes = bytes;
+        MPM_CUDA(h, cudaEventRecord(ev->a, st));
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess) {
+        h->err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
+        return MPM_ERR_CUDA;
+    }
+    if (ev) MPM_CUDA(h, cudaEventRecord(ev->b, st));
+    return MPM_OK;
+}
+
+// after a stream sync: fold recorded event pairs into the totals
+int collect_timing(mpm_handle* h) {
+    for (int c = 0; c < kNumClasses; ++c) {
+        for (size_t i = 0; i < h->ev_used[c]; ++i) {
+            float ms = 0.0f;
+            MPM_CUDA(h, cudaEventElapsedTime(&ms, h->events[c][i].a, h->events[c][i].b));
+            h->timed_ms[c] += ms;
+            h->timed_bytes[c] += h->events[c][i].bytes;
+            h->timed_launches[c]++;
+        }
+        h->ev_used[c] = 0;
+    }
+    return MPM_OK;
+}
+
+int check_device_flags(mpm_handle* h, cudaStream_t st) {
+    int flags = 0;
+    MPM_CUDA(h, cudaMemcpyAsync(&flags, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(h, cudaStreamSynchronize(st));
+    int rc = collect_timing(h);
+    if (rc != MPM_OK) return rc;
+    if (flags & mpm::kErrDomain) return fail(h, MPM_ERR_DOMAIN, "a particle stencil left the grid");
+    if (flags & mpm::kErrNumeric)
+        return fail(h, MPM_ERR_NUMERIC, "inverted or non-finite deformation gradient");
+    if (flags & mpm::kErrTimeout) return fail(h, MPM_ERR_TIMEOUT, "device wait timed out");
+    return MPM_OK;
+}
+
+int validate(const mpm_config* c, std::string& why) {
+    if (!c) { why = "config is NULL"; return MPM_ERR_ARG; }
+    if (c->dim != 2 && c->dim != 3) { why = "dim must be 2 or 3"; return MPM_ERR_ARG; }
+    if (c->bound < 0 || c->grid_res < 2 * c->bound + 3 || c->grid_res < 4) {
+        why = "grid_res must be >= max(4, 2*bound + 3)";
+        return MPM_ERR_ARG;
+    }
+    if (!(c->dt > 0.0) || !std::isfinite(c->dt)) { why = "dt must be > 0"; return MPM_ERR_ARG; }
+    if (c->n_steps < 1) { why = "n_steps must be >= 1"; return MPM_ERR_ARG; }
+    if (c->n_instances < 1 || !c->n_particles) { why = "need n_instances >= 1 and n_particles"; return MPM_ERR_ARG; }
+    if (!(c->E > 0.0) || !(c->nu >= 0.0 && c->nu < 0.5) || !(c->rho0 > 0.0) || !(c->p_vol > 0.0)) {
+        why = "need E > 0, 0 <= nu < 0.5, rho0 > 0, p_vol > 0";
+        return MPM_ERR_ARG;
+    }
+    if (!(c->simp_eps >= 0.0 && c->simp_eps <= 1.0) || c->simp_q < 0 || c->simp_q > 16) {
+        why = "need 0 <= simp_eps <= 1 and 0 <= simp_q <= 16";
+        return MPM_ERR_ARG;
+    }
+    if (c->wall_mode != 0 && c->wall_mode != 1) { why = "wall_mode must be 0 or 1"; return MPM_ERR_ARG; }
+    if (c->wall_mode == 1 && c->grid_res < 2 * c->bound + 3) { why = "grid too small"; return MPM_ERR_ARG; }
+    if (!(c->floor_mu >= 0.0) || !(c->damping_c >= 0.0)) { why = "need floor_mu >= 0, damping_c >= 0"; return MPM_ERR_ARG; }
+    if (c->loss_kind != 0 && c->loss_kind != 1) { why = "loss_kind must be 0 or 1"; return MPM_ERR_ARG; }
+    if (c->checkpoint_every < 0) { why = "checkpoint_every must be >= 0"; return MPM_ERR_ARG; }
+    long long n = 0;
+    for (int i = 0; i < c->n_instances; ++i) {
+        if (c->n_particles[i] < 0) { why = "negative particle count"; return MPM_ERR_ARG; }
+        n += c->n_particles[i];
+    }
+    if (n > (1LL << 30)) { why = "too many particles"; return MPM_ERR_ARG; }
+    if (mpm::sort_key_space(c->dim, c->grid_res, c->n_instances) >= (1LL << 31)) {
+        why = "grid_res^dim * n_instances too large for 32-bit cell keys";
+        return MPM_ERR_ARG;
+    }
+    int nd = c->design_of_instance ? c->n_designs : c->n_instances;
+    if (nd < 1 || nd > c->n_instances) { why = "n_designs must be in [1, n_instances]"; return MPM_ERR_ARG; }
+    if (c->design_of_instance) {
+        std::vector<int> cnt(nd, -1);
+        for (int i = 0; i < c->n_instances; ++i) {
+            int dz = c->design_of_instance[i];
+            if (dz < 0 || dz >= nd) { why = "design_of_instance out of range"; return MPM_ERR_ARG; }
+            if (cnt[dz] >= 0 && cnt[dz] != c->n_particles[i]) {
+                why = "instances sharing a design must have equal particle counts";
+                return MPM_ERR_ARG;
+            }
+            cnt[dz] = c->n_particles[i];
+        }
+        for (int dz = 0; dz < nd; ++dz)
+            if (cnt[dz] < 0) { why = "every design must be used by an instance"; return MPM_ERR_ARG; }
+    }
+    return MPM_OK;
+}
+
+int create_impl(const mpm_config* c, mpm_handle* h) {
+    h->dim = c->dim;
+    h->res = c->grid_res;
+    h->T = c->n_steps;
+    h->n_inst = c->n_instances;
+    h->K = (c->checkpoint_every <= 0 || c->checkpoint_every > h->T) ? h->T : c->checkpoint_every;
+    h->n_seg = (h->T + h->K - 1) / h->K;
+    h->ncomp = 2 * h->dim + 2 * h->dim * h->dim;
+    h->counts.assign(c->n_particles, c->n_particles + h->n_inst);
+    h->inst_off.assign(h->n_inst + 1, 0);
+    for (int i = 0; i < h->n_inst; ++i) h->inst_off[i + 1] = h->inst_off[i] + h->counts[i];
+    h->N = h->inst_off[h->n_inst];
+    h->np = std::max<long long>(32, (h->N + 31) / 32 * 32);
+    int nd = c->design_of_instance ? c->n_designs : h->n_inst;
+    h->design_of.resize(h->n_inst);
+    for (int i = 0; i < h->n_inst; ++i) h->design_of[i] = c->design_of_instance ? c->design_of_instance[i] : i;
+    h->dcount.assign(nd, 0);
+    for (int i = 0; i < h->n_inst; ++i) h->dcount[h->design_of[i]] = h->counts[i];
+    std::vector<int> doff(nd + 1, 0);
+    for (int z = 0; z < nd; ++z) doff[z + 1] = doff[z] + h->dcount[z];
+    h->Nd = doff[nd];
+    h->dbase.resize(h->n_inst);
+    for (int i = 0; i < h->n_inst; ++i) h->dbase[i] = doff[h->design_of[i]];
+    h->nodes = 1;
+    for (int a = 0; a < h->dim; ++a) h->nodes *= h->res;
+    h->total_nodes = h->nodes * h->n_inst;
+
+    Params& P = h->P;
+    P.res = h->res;
+    P.bound = c->bound;
+    P.wall_mode = c->wall_mode;
+    P.loss_kind = c->loss_kind;
+    P.simp_q = c->simp_q;
+    P.n_inst = h->n_inst;
+    P.n_steps = h->T;
+    P.n_total = (int)h->N;
+    P.np = h->np;
+    P.nodes = h->nodes;
+    P.dx = (float)(1.0 / h->res);
+    P.inv_dx = (float)h->res;
+    P.dt = (float)c->dt;
+    P.kappa = (float)(4.0 * h->res * (double)h->res);
+    P.p_vol = (float)c->p_vol;
+    P.rho0 = (float)c->rho0;
+    P.G = (float)(c->E / (2.0 * (1.0 + c->nu)));
+    P.K = (float)(c->E / (3.0 * (1.0 - 2.0 * c->nu)));
+    P.eps = (float)c->simp_eps;
+    P.damping = (float)c->damping_c;
+    P.mu = (float)c->floor_mu;
+    for (int i = 0; i < 3; ++i) P.gravity[i] = (float)c->gravity[i];
+
+    const long long S = (long long)h->ncomp * h->np;
+    const int d = h->dim;
+    int rc;
+#define ALLOC(ptr, n) if ((rc = dalloc(h, &(ptr), (n))) != MPM_OK) return rc
+    ALLOC(h->d_inst_off, h->n_inst + 1);
+    ALLOC(h->d_dbase, h->n_inst);
+    ALLOC(h->stA, S);
+    ALLOC(h->stB, S);
+    ALLOC(h->idA, h->np);
+    ALLOC(h->idB, h->np);
+    ALLOC(h->ck_state, S * h->n_seg);
+    ALLOC(h->ck_id, h->np * h->n_seg);
+    ALLOC(h->ck_perm, h->np * h->n_seg);
+    ALLOC(h->seg_state, S * (h->K + 1));
+    ALLOC(h->seg_acc, h->total_nodes * h->K);
+    ALLOC(h->seg_V, h->total_nodes * h->K);
+    ALLOC(h->acc, h->total_nodes);
+    ALLOC(h->V, h->total_nodes);
+    ALLOC(h->Vbar, h->total_nodes);
+    ALLOC(h->gadj, h->total_nodes);
+    ALLOC(h->adj, S);
+    ALLOC(h->adj2, S);
+    ALLOC(h->phi_cur, h->np);
+    ALLOC(h->mag_cur, d * h->np);
+    ALLOC(h->gphi_cur, h->np);
+    ALLOC(h->gmag_cur, d * h->np);
+    ALLOC(h->phi_d, h->Nd);
+    ALLOC(h->mag_d, d * h->Nd);
+    ALLOC(h->field, (long long)h->n_inst * h->T * d);
+    ALLOC(h->target, d * h->N);
+    ALLOC(h->mom, (long long)h->T * h->n_inst);
+    ALLOC(h->Minst, h->n_inst);
+    ALLOC(h->loss_acc, h->n_inst);
+    ALLOC(h->dloss, h->n_inst);
+    ALLOC(h->gphi_d, h->Nd);
+    ALLOC(h->gmag_d, d * h->Nd);
+    ALLOC(h->gfield_d, (long long)h->n_inst * h->T * d);
+    ALLOC(h->st_x0, d * h->N);
+    ALLOC(h->st_v0, d * h->N);
+    ALLOC(h->st_xout, d * h->N);
+    ALLOC(h->st_loss, h->n_inst);
+    ALLOC(h->d_err, 1);
+    ALLOC(h->perm, h->np);
+    h->sb.n_keys = mpm::sort_key_space(d, h->res, h->n_inst);
+    h->sb.scan_tmp_len = mpm::sort_scan_tmp_len(h->sb.n_keys);
+    ALLOC(h->sb.keys, h->np);
+    ALLOC(h->sb.slot, h->np);
+    ALLOC(h->sb.counts, h->sb.n_keys);
+    ALLOC(h->sb.offsets, h->sb.n_keys);
+    ALLOC(h->sb.scan_tmp, h->sb.scan_tmp_len);
+#undef ALLOC
+    MPM_CUDA(h, cudaMemcpy(h->d_inst_off, h->inst_off.data(), sizeof(int) * (h->n_inst + 1),
+                           cudaMemcpyHostToDevice));
+    MPM_CUDA(h, cudaMemcpy(h->d_dbase, h->dbase.data(), sizeof(int) * h->n_inst,
+                           cudaMemcpyHostToDevice));
+    // padding lanes of the state buffers stay finite
+    MPM_CUDA(h, cudaMemset(h->stA, 0, sizeof(float) * S));
+    MPM_CUDA(h, cudaMemset(h->stB, 0, sizeof(float) * S));
+    return MPM_OK;
+}
+
+StepArgs base_args(mpm_handle* h) {
+    StepArgs a;
+    a.phi = h->phi_cur;
+    a.mag = h->mag_cur;
+    a.field = h->field;
+    a.inst_off = h->d_inst_off;
+    a.err = h->d_err;
+    a.Minst = h->Minst;
+    a.dloss = h->dloss;
+    a.gphi = h->gphi_cur;
+    a.gmag = h->gmag_cur;
+    a.gfield = h->gfield_d;
+    return a;
+}
+
+// copy src -> dst (device) unless they are the same buffer
+int dcopy(mpm_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (dst == src || bytes == 0) return MPM_OK;
+    MPM_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return MPM_OK;
+}
+
+int forward_impl(mpm_handle* h, const float* x0, const float* v0, const float* phi,
+                 const float* mag, const float* field, const float* target, float* x_out,
+                 float* loss_out, cudaStream_t st) {
+    const int d = h->dim;
+    const Params& P = h->P;
+    if (!loss_out) return fail(h, MPM_ERR_ARG, "loss_out is NULL");
+    if (h->N > 0 && (!x0 || !phi || !mag)) return fail(h, MPM_ERR_ARG, "x0, phi_bar and mag are required");
+    if (!field) return fail(h, MPM_ERR_ARG, "field is required");
+    if (h->N > 0 && P.loss_kind == 0 && !target) return fail(h, MPM_ERR_ARG, "target is required for loss_kind 0");
+    h->forward_done = false;
+    int rc;
+    if ((rc = dcopy(h, h->phi_d, phi, sizeof(float) * h->Nd, st))) return rc;
+    if ((rc = dcopy(h, h->mag_d, mag, sizeof(float) * d * h->Nd, st))) return rc;
+    if ((rc = dcopy(h, h->field, field, sizeof(float) * h->n_inst * h->T * d, st))) return rc;
+    if (target && (rc = dcopy(h, h->target, target, sizeof(float) * d * h->N, st))) return rc;
+    MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    MPM_CUDA(h, cudaMemsetAsync(h->mom, 0, sizeof(float) * h->T * h->n_inst, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->Minst, 0, sizeof(float) * h->n_inst, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->loss_acc, 0, sizeof(float) * h->n_inst, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(float4) * h->total_nodes, st));
+    const long long S = (long long)h->ncomp * h->np;
+
+    float* cur = h->stA;
+    float* nxt = h->stB;
+    int* id_cur = h->idA;
+    int* id_nxt = h->idB;
+    h->launches++;
+    MPM_CUDA(h, mpm::launch_init_state(d, P, x0, v0, cur, id_cur, st));
+    for (int seg = 0; seg < h->n_seg; ++seg) {
+        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T);
+        // cell sort and reorder of the full state
+        h->launches += 4;
+        MPM_CUDA(h, mpm::launch_sort(d, P, cur, h->np, h->d_inst_off, h->sb, h->perm, h->d_err, st));
+        h->launches++;
+        MPM_CUDA(h, mpm::launch_reorder(h->ncomp, P, cur, nxt, h->perm, id_cur, id_nxt, st));
+        std::swap(cur, nxt);
+        std::swap(id_cur, id_nxt);
+        h->launches++;
+        MPM_CUDA(h, mpm::launch_gather_design(d, P, id_cur, h->d_inst_off, h->d_dbase, h->phi_d,
+                                              h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st));
+        MPM_CUDA(h, cudaMemcpyAsync(h->ck_state + S * seg, cur, sizeof(float) * S,
+                                    cudaMemcpyDeviceToDevice, st));
+        MPM_CUDA(h, cudaMemcpyAsync(h->ck_id + h->np * seg, id_cur, sizeof(int) * h->np,
+                                    cudaMemcpyDeviceToDevice, st));
+        MPM_CUDA(h, cudaMemcpyAsync(h->ck_perm + h->np * seg, h->perm, sizeof(int) * h->np,
+                                    cudaMemcpyDeviceToDevice, st));
+        StepArgs a = base_args(h);
+        a.mom = h->mom;
+        if (seg == 0) {
+            h->launches++;
+            MPM_CUDA(h, mpm::launch_instance_mass(P, h->phi_cur, h->d_inst_off, h->Minst, st));
+            a.s_in = cur;
+            a.acc = h->acc;
+            a.n_p2g = 0;
+            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
+                     return mpm::launch_forward(d, false, true, false, P, a, h->block, st);
+                 })))
+                return rc;
+        }
+        for (int n = s0; n < s1; ++n) {
+            if ((rc = timed(h, kGrid, 48.0 * h->total_nodes, st, [&] {
+                     return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, st);
+                 })))
+                return rc;
+            const bool p2g = n + 1 < h->T;
+            const bool all = n + 1 == s1;
+            a.s_in = cur;
+            a.s_out = nxt;
+            a.V = h->V;
+            a.acc = h->acc;
+            a.n_g2p = n;
+            a.n_p2g = n + 1;
+            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, all ? kFusedStore : kFused), st, [&] {
+                     return mpm::launch_forward(d, true, p2g, all, P, a, h->block, st);
+                 })))
+                return rc;
+            std::swap(cur, nxt);
+        }
+    }
+    h->launches++;
+    MPM_CUDA(h, mpm::launch_loss(d, P, cur, h->target, id_cur, h->d_inst_off, h->Minst, h->mom,
+                                 h->loss_acc, loss_out, st));
+    if (x_out) {
+        h->launches++;
+        MPM_CUDA(h, mpm::launch_to_input_order(d, P, cur, 0, id_cur, x_out, st));
+    }
+    rc = check_device_flags(h, st);
+    if (rc != MPM_OK) return rc;
+    h->cur = cur;
+    h->id_cur = id_cur;
+    h->forward_done = true;
+    return MPM_OK;
+}
+
+int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag, float* g_field,
+                  cudaStream_t st) {
+    if (!h->forward_done) return fail(h, MPM_ERR_STATE, "mpm_backward needs a successful mpm_forward first");
+    if (!dloss) return fail(h, MPM_ERR_ARG, "dloss is NULL");
+    const int d = h->dim;
+    const Params& P = h->P;
+    const long long S = (long long)h->ncomp * h->np;
+    int rc;
+    if ((rc = dcopy(h, h->dloss, dloss, sizeof(float) * h->n_inst, st))) return rc;
+    MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    MPM_CUDA(h, cudaMemsetAsync(h->gphi_d, 0, sizeof(float) * h->Nd, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->gmag_d, 0, sizeof(float) * d * h->Nd, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->gfield_d, 0, sizeof(float) * h->n_inst * h->T * d, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->Vbar, 0, sizeof(float4) * h->total_nodes, st));
+    float* adj = h->adj;
+    float* adj_next = h->adj2;
+    for (int seg = h->n_seg - 1; seg >= 0; --seg) {
+        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T), Ks = s1 - s0;
+        const int* id_seg = h->ck_id + h->np * seg;
+        auto state = [&](int k) { return h->seg_state + S * k; };
+        auto gacc = [&](int k) { return h->seg_acc + h->total_nodes * k; };
+        auto gV = [&](int k) { return h->seg_V + h->total_nodes * k; };
+        MPM_CUDA(h, cudaMemcpyAsync(state(0), h->ck_state + S * seg, sizeof(float) * S,
+                                    cudaMemcpyDeviceToDevice, st));
+        h->launches++;
+        MPM_CUDA(h, mpm::launch_gather_design(d, P, id_seg, h->d_inst_off, h->d_dbase, h->phi_d,
+                                              h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->gphi_cur, 0, sizeof(float) * h->np, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->gmag_cur, 0, sizeof(float) * d * h->np, st));
+        // --- recompute the segment, storing states and grids ---
+        MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * h->total_nodes, st));
+        StepArgs a = base_args(h);
+        a.s_in = state(0);
+        a.acc = gacc(0);
+        a.n_p2g = s0;
+        if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
+                 return mpm::launch_forward(d, false, true, false, P, a, h->block, st);
+             })))
+            return rc;
+        for (int k = 0; k < Ks; ++k) {
+            const int n = s0 + k;
+            float4* next_acc = k + 1 < Ks ? gacc(k + 1) : nullptr;
+            if ((rc = timed(h, kGrid, 48.0 * h->total_nodes, st, [&] {
+                     return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, st);
+                 })))
+                return rc;
+            a = base_args(h);
+            a.s_in = state(k);
+            a.s_out = state(k + 1);
+            a.V = gV(k);
+            a.acc = next_acc;
+            a.n_g2p = n;
+            a.n_p2g = n + 1;
+            const bool p2g = k + 1 < Ks;
+            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
+                     return mpm::launch_forward(d, true, p2g, true, P, a, h->block, st);
+                 })))
+                return rc;
+        }
+        // --- adjoint of the state at the segment end ---
+        if (s1 == h->T) {
+            h->launches++;
+            MPM_CUDA(h, mpm::launch_seed(d, P, state(Ks), h->target, id_seg, h->d_inst_off, h->phi_cur,
+                                         h->Minst, h->mom, h->dloss, adj, h->gphi_cur, st));
+        } else {
+            h->launches++;
+            MPM_CUDA(h, mpm::launch_unpermute(h->ncomp, P, adj_next, adj, h->ck_perm + h->np * (seg + 1), st));
+        }
+        // G2P^T of the last substep of the segment
+        a = base_args(h);
+        a.s_in = state(Ks);
+        a.s_aux = state(Ks - 1);
+        a.V = gV(Ks - 1);
+        a.Vbar = h->Vbar;
+        a.adj = adj;
+        a.mom = h->mom;
+        a.n_p2g = s1;
+        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kLastG2PT), st, [&] {
+                 return mpm::launch_adjoint(d, false, true, P, a, h->block, st);
+             })))
+            return rc;
+        for (int k = Ks - 1; k >= 1; --k) {
+            const int n = s0 + k;
+            if ((rc = timed(h, kGridAdj, 64.0 * h->total_nodes, st, [&] {
+                     return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, st);
+                 })))
+                return rc;
+            a = base_args(h);
+            a.s_in = state(k);
+            a.s_aux = state(k - 1);
+            a.V = gV(k - 1);
+            a.Vbar = h->Vbar;
+            a.gadj = h->gadj;
+            a.adj = adj;
+            a.mom = h->mom;
+            a.n_p2g = n;
+            if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
+                     return mpm::launch_adjoint(d, true, true, P, a, h->block, st);
+                 })))
+                return rc;
+        }
+        if ((rc = timed(h, kGridAdj, 64.0 * h->total_nodes, st, [&] {
+                 return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, st);
+             })))
+            return rc;
+        a = base_args(h);
+        a.s_in = state(0);
+        a.gadj = h->gadj;
+        a.adj = adj;
+        a.mom = h->mom;
+        a.n_p2g = s0;
+        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFirstP2GT), st, [&] {
+                 return mpm::launch_adjoint(d, true, false, P, a, h->block, st);
+             })))
+            return rc;
+        h->launches++;
+        MPM_CUDA(h, mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase,
+                                                    h->gphi_cur, h->gmag_cur, h->Nd, h->gphi_d,
+                                                    h->gmag_d, st));
+        std::swap(adj, adj_next);
+    }
+    if (g_phi && (rc = dcopy(h, g_phi, h->gphi_d, sizeof(float) * h->Nd, st))) return rc;
+    if (g_mag && (rc = dcopy(h, g_mag, h->gmag_d, sizeof(float) * d * h->Nd, st))) return rc;
+    if (g_field && (rc = dcopy(h, g_field, h->gfield_d, sizeof(float) * h->n_inst * h->T * d, st)))
+        return rc;
+    return check_device_flags(h, st);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int mpm_create(const mpm_config* cfg, mpm_handle** out) {
+    if (!out) return MPM_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    int rc = validate(cfg, why);
+    if (rc != MPM_OK) {
+        std::fprintf(stderr, "mpm_create: %s\n", why.c_str());
+        return rc;
+    }
+    mpm_handle* h = new (std::nothrow) mpm_handle();
+    if (!h) return MPM_ERR_OOM;
+    try {
+        rc = create_impl(cfg, h);
+    } catch (...) {
+        rc = MPM_ERR_OOM;
+    }
+    if (rc != MPM_OK) {
+        std::fprintf(stderr, "mpm_create: %s\n", h->err.c_str());
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return MPM_OK;
+}
+
+int mpm_destroy(mpm_handle* h) {
+    if (!h) return MPM_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return MPM_OK;
+}
+
+const char* mpm_last_error(const mpm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int mpm_forward(mpm_handle* h, const float* x0, const float* v0, const float* phi_bar,
+                const float* mag, const float* field, const float* target, float* x_out,
+                float* loss_out, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    try {
+        return forward_impl(h, x0, v0, phi_bar, mag, field, target, x_out, loss_out,
+                            (cudaStream_t)cuda_stream);
+    } catch (...) {
+        return fail(h, MPM_ERR_CUDA, "unexpected exception in mpm_forward");
+    }
+}
+
+int mpm_backward(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag, float* g_field,
+                 void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    try {
+        return backward_impl(h, dloss, g_phi, g_mag, g_field, (cudaStream_t)cuda_stream);
+    } catch (...) {
+        return fail(h, MPM_ERR_CUDA, "unexpected exception in mpm_backward");
+    }
+}
+
+int mpm_forward_host(mpm_handle* h, const float* x0, const float* v0, const float* phi_bar,
+                     const float* mag, const float* field, const float* target, float* x_out,
+                     float* loss_out, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int d = h->dim;
+    if (!loss_out || !field || (h->N > 0 && (!x0 || !phi_bar || !mag)))
+        return fail(h, MPM_ERR_ARG, "missing input");
+    if (h->N > 0 && h->P.loss_kind == 0 && !target) return fail(h, MPM_ERR_ARG, "target is required for loss_kind 0");
+    auto h2d = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    MPM_CUDA(h, h2d(h->st_x0, x0, sizeof(float) * d * h->N));
+    if (v0) MPM_CUDA(h, h2d(h->st_v0, v0, sizeof(float) * d * h->N));
+    MPM_CUDA(h, h2d(h->phi_d, phi_bar, sizeof(float) * h->Nd));
+    MPM_CUDA(h, h2d(h->mag_d, mag, sizeof(float) * d * h->Nd));
+    MPM_CUDA(h, h2d(h->field, field, sizeof(float) * h->n_inst * h->T * d));
+    if (target) MPM_CUDA(h, h2d(h->target, target, sizeof(float) * d * h->N));
+    int rc;
+    try {
+        rc = forward_impl(h, h->st_x0, v0 ? h->st_v0 : nullptr, h->phi_d, h->mag_d, h->field,
+                          target ? h->target : nullptr, x_out ? h->st_xout : nullptr, h->st_loss, st);
+    } catch (...) {
+        return fail(h, MPM_ERR_CUDA, "unexpected exception in mpm_forward_host");
+    }
+    if (rc != MPM_OK) return rc;
+    MPM_CUDA(h, cudaMemcpyAsync(loss_out, h->st_loss, sizeof(float) * h->n_inst, cudaMemcpyDeviceToHost, st));
+    if (x_out && h->N > 0)
+        MPM_CUDA(h, cudaMemcpyAsync(x_out, h->st_xout, sizeof(float) * d * h->N, cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(h, cudaStreamSynchronize(st));
+    return MPM_OK;
+}
+
+int mpm_backward_host(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
+                      float* g_field, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    if (!dloss) return fail(h, MPM_ERR_ARG, "dloss is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int d = h->dim;
+    MPM_CUDA(h, cudaMemcpyAsync(h->dloss, dloss, sizeof(float) * h->n_inst, cudaMemcpyHostToDevice, st));
+    int rc;
+    try {
+        rc = backward_impl(h, h->dloss, nullptr, nullptr, nullptr, st);
+    } catch (...) {
+        return fail(h, MPM_ERR_CUDA, "unexpected exception in mpm_backward_host");
+    }
+    if (rc != MPM_OK) return rc;
+    if (g_phi && h->Nd)
+        MPM_CUDA(h, cudaMemcpyAsync(g_phi, h->gphi_d, sizeof(float) * h->Nd, cudaMemcpyDeviceToHost, st));
+    if (g_mag && h->Nd)
+        MPM_CUDA(h, cudaMemcpyAsync(g_mag, h->gmag_d, sizeof(float) * d * h->Nd, cudaMemcpyDeviceToHost, st));
+    if (g_field)
+        MPM_CUDA(h, cudaMemcpyAsync(g_field, h->gfield_d, sizeof(float) * h->n_inst * h->T * d,
+                                    cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(h, cudaStreamSynchronize(st));
+    return MPM_OK;
+}
+
+int mpm_read_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    if (!h->forward_done) return fail(h, MPM_ERR_STATE, "no forward result to read");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int d = h->dim;
+    const Params& P = h->P;
+    if (x) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, x, st));
+    if (v) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, d, h->id_cur, v, st));
+    if (C) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d, h->id_cur, C, st));
+    if (F) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d + d * d, h->id_cur, F, st));
+    MPM_CUDA(h, cudaStreamSynchronize(st));
+    return MPM_OK;
+}
+
+int mpm_sort_particles(mpm_handle* h, const float* x, int* keys, int* perm, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    if (h->N > 0 && (!x || !keys || !perm)) return fail(h, MPM_ERR_ARG, "x, keys and perm are required");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    MPM_CUDA(h, mpm::launch_sort(h->dim, h->P, x, h->N, h->d_inst_off, h->sb, perm, h->d_err, st));
+    if (h->N > 0)
+        MPM_CUDA(h, cudaMemcpyAsync(keys, h->sb.keys, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, st));
+    MPM_CUDA(h, cudaStreamSynchronize(st));
+    return MPM_OK;
+}
+
+int mpm_set_option(mpm_handle* h, int key, long long value) {
+    if (!h) return MPM_ERR_ARG;
+    switch (key) {
+        case MPM_OPT_TIMING:
+            if (value < 0) return fail(h, MPM_ERR_ARG, "timing stride must be >= 0");
+            h->timing_stride = (int)value;
+            return MPM_OK;
+        case MPM_OPT_BLOCK:
+            if (value < 32 || value > 256 || value % 32) return fail(h, MPM_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
+            h->block = (int)value;
+            return MPM_OK;
+        default:
+            return fail(h, MPM_ERR_ARG, "unknown option");
+    }
+}
+
+int mpm_get_stats(const mpm_handle* h, mpm_stats* out) {
+    if (!h || !out) return MPM_ERR_ARG;
+    out->launches = h->launches;
+    for (int c = 0; c < 4; ++c) {
+        out->timed_launches[c] = h->timed_launches[c];
+        out->timed_ms[c] = h->timed_ms[c];
+        out->timed_bytes[c] = h->timed_bytes[c];
+    }
+    out->device_bytes = h->device_bytes;
+    return MPM_OK;
+}
+
+int mpm_reset_stats(mpm_handle* h) {
+    if (!h) return MPM_ERR_ARG;
+    h->launches = 0;
+    for (int c = 0; c < 4; ++c) {
+        h->timed_launches[c] = 0;
+        h->timed_ms[c] = 0.0;
+        h->timed_bytes[c] = 0.0;
+        h->class_launch[c] = 0;
+    }
+    return MPM_OK;
+}
+
+}  // extern "C"

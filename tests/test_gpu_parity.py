@@ -1,0 +1,309 @@
+"""GPU (FP32, CUDA kernels through the C ABI) against the FP64 oracle.
+
+Tolerances (from the method's precision targets): particle state relative L2
+<= 1e-4 (positions, velocities, deformation gradients) over the stated
+horizons; gradients per design block: cosine >= 0.999 and relative L2 error
+<= 1e-3; the cell sort and its permutation bit-exact.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from paper_2503_22767_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2503_22767_gb300.sim import Simulator  # noqa: E402
+from paper_2503_22767_gb300 import binding as B  # noqa: E402
+
+STATE_TOL = 1e-4
+GRAD_COS = 0.999
+GRAD_REL = 1e-3
+
+
+def _t(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def run_gpu(w, backward=True, block=None):
+    sim = Simulator(w.cfg, block=block)
+    loss, x = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), target=_t(w.target),
+                          v0=_t(w.v0), want_x=True)
+    xs, v, C, F = sim.read_state()
+    out = dict(loss=loss.cpu().numpy().astype(np.float64), x=x.cpu().numpy(), x_state=xs.cpu().numpy(),
+               v=v.cpu().numpy(), C=C.cpu().numpy(), F=F.cpu().numpy())
+    if backward:
+        g_phi, g_mag, g_field = sim.backward(torch.ones(w.cfg.n_instances, device="cuda"))
+        out.update(g_phi=g_phi.cpu().numpy(), g_mag=g_mag.cpu().numpy(), g_field=g_field.cpu().numpy())
+    out["stats"] = sim.stats()
+    sim.close()
+    return out
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def cosine(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    na, nb = np.linalg.norm(a), np.linalg.norm(b)
+    if na == 0 and nb == 0:
+        return 1.0
+    return float(a @ b / (na * nb))
+
+
+def assert_state(g, o, w, tol=STATE_TOL):
+    d = w.cfg.dim
+    x0 = w.x0.astype(np.float64)
+    errs = {
+        "x": rel_l2(g["x"], o["x"]),
+        "u": rel_l2(g["x"] - x0, o["x"] - x0),
+        "v": rel_l2(g["v"], o["v"]),
+        "F": rel_l2(g["F"], o["F"]),
+        "F-I": rel_l2(g["F"] - np.eye(d)[:, :, None], o["F"] - np.eye(d)[:, :, None]),
+    }
+    print(w.name, {k: f"{v:.2e}" for k, v in errs.items()})
+    np.testing.assert_array_equal(g["x"], g["x_state"])
+    assert errs["x"] <= tol and errs["v"] <= tol and errs["F"] <= tol, errs
+    return errs
+
+
+def assert_grads(g, o, w, cos=GRAD_COS, rel=GRAD_REL):
+    res = {}
+    for k in ("g_phi", "g_mag", "g_field"):
+        res[k] = (cosine(g[k], o[k]), rel_l2(g[k], o[k]))
+    print(w.name, {k: f"cos {c:.6f} rel {r:.2e}" for k, (c, r) in res.items()})
+    for k, (c, r) in res.items():
+        assert c >= cos and r <= rel, (k, c, r)
+    return res
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(key):
+    import oracle
+
+    w = CASES[key]()
+    return w, oracle.forward(w), oracle.backward(w, ckpt_every=50)
+
+
+# workloads sized so the oracle finishes in seconds but spanning many CTAs,
+# ragged tails and both dimensions
+CASES = {
+    "beam2d_64_4x4": lambda: W.beam_2d(seed=0, per_axis=4),
+    "beam2d_64_2x2": lambda: W.beam_2d(seed=1, per_axis=2),
+    "walker2d_128_s0.5_300": lambda: W.walker_2d(seed=2, n_steps=300, scale=0.5, checkpoint_every=100),
+    "walker2d_128_full_body_200": lambda: W.walker_2d(seed=0, n_steps=200, checkpoint_every=100),
+    "plate3d_32_3tasks_60": lambda: W.plate_3d(seed=3, n_steps=60, res=32, cells=(20, 5, 20)),
+    "walker3d_48_s0.25_60": lambda: W.walker_3d(seed=4, n_steps=60, res=48, scale=0.25,
+                                                checkpoint_every=25),
+    "tiny2d_floor": lambda: W.tiny_2d(seed=11, n_steps=40, res=16, per_axis=2, cells=(5, 3),
+                                      bound=3, lift=3, loss_kind=1, wall_mode=1, phi_lo=0.3,
+                                      gravity=-9.81, field_scale=0.2, mag_scale=1.0, v_scale=0.2),
+    "tiny3d_free": lambda: W.tiny_3d(seed=9, n_steps=30, res=12, per_axis=2, loss_kind=0,
+                                     phi_lo=0.3, v_scale=0.05, bound=1, gravity=-9.81,
+                                     field_scale=0.2, mag_scale=1.0),
+}
+
+
+@pytest.mark.parametrize("key", list(CASES))
+def test_forward_parity(key):
+    w, of, _ = _oracle(key)
+    g = run_gpu(w, backward=False)
+    assert_state(g, of, w)
+    np.testing.assert_allclose(g["loss"], of["loss"], rtol=1e-3, atol=1e-7 * np.abs(of["loss"]).max())
+
+
+@pytest.mark.parametrize("key", list(CASES))
+def test_gradient_parity(key):
+    w, _, ob = _oracle(key)
+    g = run_gpu(w)
+    assert_grads(g, ob, w)
+
+
+# ---------------------------------------------------------------------------
+# sort: bit-exact against the oracle's key definition and stable order
+# ---------------------------------------------------------------------------
+
+def _sort_case(w, xf):
+    import oracle
+
+    sim = Simulator(w.cfg)
+    keys, perm = sim.sort(_t(xf))
+    sim.close()
+    bs = 8 if w.cfg.dim == 2 else 4
+    ok = oracle.cell_keys(w.cfg.dim, w.cfg.res, bs, w.cfg.counts, xf)
+    op = oracle.sort_perm(ok)
+    np.testing.assert_array_equal(keys.cpu().numpy(), ok)
+    np.testing.assert_array_equal(perm.cpu().numpy(), op)
+
+
+@pytest.mark.parametrize("key", ["beam2d_64_4x4", "walker2d_128_s0.5_300", "plate3d_32_3tasks_60",
+                                 "walker3d_48_s0.25_60"])
+def test_sort_bitexact(key):
+    w = CASES[key]()
+    _sort_case(w, w.x0)
+
+
+def test_sort_bitexact_faces_and_batches():
+    """Positions exactly on cell faces, shuffled order, several instances."""
+    w = W.walker_batch_2d(seed=5, n_instances=4, n_steps=10, n_lo=800, n_hi=3000)
+    rng = np.random.default_rng(0)
+    xf = w.x0.copy()
+    res = w.cfg.res
+    k = xf.shape[1] // 3
+    xf[:, :k] = (np.floor(xf[:, :k] * res) + 0.5) / res  # base switches exactly here
+    xf[:, k:2 * k] = np.floor(xf[:, k:2 * k] * res) / res
+    # shuffle inside each instance (instances stay contiguous)
+    off = np.concatenate([[0], np.cumsum(w.cfg.counts)])
+    for i in range(len(w.cfg.counts)):
+        idx = rng.permutation(np.arange(off[i], off[i + 1]))
+        xf[:, off[i]:off[i + 1]] = xf[:, idx]
+    _sort_case(w, xf.astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# checkpointing, batching, shared designs
+# ---------------------------------------------------------------------------
+
+def test_checkpoint_interval_invariance():
+    base = W.walker_2d(seed=6, n_steps=150, scale=0.4)
+    grads = {}
+    for K in (1, 7, 50, 0):
+        w = W.with_steps(base, 150, checkpoint_every=K)
+        grads[K] = run_gpu(w)
+    for K in (1, 7, 50):
+        for k in ("g_phi", "g_mag", "g_field"):
+            assert cosine(grads[K][k], grads[0][k]) >= GRAD_COS
+            assert rel_l2(grads[K][k], grads[0][k]) <= GRAD_REL
+    import oracle
+    ob = oracle.backward(base)
+    assert_grads(grads[7], ob, base)
+
+
+def _subset(w, i):
+    off = np.concatenate([[0], np.cumsum(w.cfg.counts)])
+    sl = slice(off[i], off[i + 1])
+    cfg = W.MpmConfig(**{**w.cfg.as_dict(), "counts": [w.cfg.counts[i]], "design_of_instance": None})
+    return W.Workload(f"{w.name}[{i}]", cfg, w.x0[:, sl], None, w.phi[sl], w.mag[:, sl],
+                      w.field[i:i + 1], None if w.target is None else w.target[:, sl])
+
+
+def test_batch_equals_instances_alone():
+    w = W.walker_batch_2d(seed=7, n_instances=5, n_steps=120, n_lo=1500, n_hi=6000)
+    gb = run_gpu(w)
+    off = np.concatenate([[0], np.cumsum(w.cfg.counts)])
+    for i in range(w.cfg.n_instances):
+        wi = _subset(w, i)
+        gi = run_gpu(wi)
+        sl = slice(off[i], off[i + 1])
+        assert abs(gb["loss"][i] - gi["loss"][0]) <= 1e-4 * abs(gi["loss"][0]) + 1e-9
+        assert rel_l2(gb["x"][:, sl], gi["x"]) <= 1e-6
+        for k, bsl in (("g_phi", sl), ("g_mag", (slice(None), sl))):
+            assert cosine(gb[k][bsl], gi[k]) >= GRAD_COS and rel_l2(gb[k][bsl], gi[k]) <= GRAD_REL
+        assert rel_l2(gb["g_field"][i], gi["g_field"][0]) <= GRAD_REL
+
+
+def test_shared_design_gradient_is_sum_over_tasks():
+    """Multi-task (Eq. 35): one design, three field schedules and targets."""
+    key = "plate3d_32_3tasks_60"
+    w, _, ob = _oracle(key)
+    assert w.cfg.design_of_instance == [0, 0, 0]
+    g = run_gpu(w)
+    assert g["g_phi"].shape == ob["g_phi"].shape == (w.cfg.counts[0],)
+    assert_grads(g, ob, w)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and error statuses
+# ---------------------------------------------------------------------------
+
+def test_empty_and_ragged_instances():
+    w = W.walker_batch_2d(seed=8, n_instances=3, n_steps=40, n_lo=300, n_hi=900)
+    # insert an empty instance in the middle
+    counts = [w.cfg.counts[0], 0, w.cfg.counts[1], w.cfg.counts[2]]
+    cfg = W.MpmConfig(**{**w.cfg.as_dict(), "counts": counts})
+    field = np.concatenate([w.field[:1], w.field[:1] * 0.5, w.field[1:]], axis=0)
+    we = W.Workload("empty-mid", cfg, w.x0, None, w.phi, w.mag, field, None)
+    import oracle
+    g = run_gpu(we)
+    of = oracle.forward(we)
+    ob = oracle.backward(we)
+    assert g["loss"][1] == 0.0 and np.all(g["g_field"][1] == 0.0)
+    assert_state(g, of, we)
+    assert_grads(g, ob, we)
+
+
+def test_single_particle_and_no_particles():
+    import oracle
+    w = W.tiny_2d(seed=1, n_steps=10, res=16, per_axis=1, cells=(1, 1), bound=1, lift=6)
+    assert w.cfg.n_total == 1
+    g = run_gpu(w)
+    assert_state(g, oracle.forward(w), w)
+    cfg = W.MpmConfig(**{**w.cfg.as_dict(), "counts": [0]})
+    we = W.Workload("none", cfg, np.zeros((2, 0), np.float32), None, np.zeros(0, np.float32),
+                    np.zeros((2, 0), np.float32), w.field, np.zeros((2, 0), np.float32))
+    g = run_gpu(we)
+    assert g["loss"][0] == 0.0 and np.all(g["g_field"] == 0.0)
+
+
+def test_domain_error_is_a_status_not_a_fault():
+    w = W.tiny_2d(seed=2, n_steps=5, res=16)
+    x0 = w.x0.copy()
+    x0[0, 0] = 1.5  # outside the grid
+    wb = W.Workload("bad", w.cfg, x0, None, w.phi, w.mag, w.field, w.target)
+    sim = Simulator(wb.cfg)
+    with pytest.raises(B.MpmError) as ei:
+        sim.forward(_t(wb.x0), _t(wb.phi), _t(wb.mag), _t(wb.field), target=_t(wb.target))
+    assert ei.value.status == B.MPM_ERR_DOMAIN
+    with pytest.raises(B.MpmError) as ei:
+        sim.backward(torch.ones(1, device="cuda"))
+    assert ei.value.status == B.MPM_ERR_STATE
+    # the handle stays usable
+    loss, _ = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), target=_t(w.target))
+    assert np.isfinite(loss.cpu().numpy()).all()
+    sim.close()
+
+
+def test_nan_input_is_reported():
+    w = W.tiny_2d(seed=3, n_steps=5, res=16, bound=1, lift=6)
+    mag = w.mag.copy()
+    mag[0, 0] = np.nan
+    sim = Simulator(w.cfg)
+    with pytest.raises(B.MpmError) as ei:
+        sim.forward(_t(w.x0), _t(w.phi), _t(mag), _t(w.field), target=_t(w.target))
+    assert ei.value.status in (B.MPM_ERR_NUMERIC, B.MPM_ERR_DOMAIN)
+    sim.close()
+
+
+def test_host_entry_points_match_device_ones():
+    w = CASES["walker2d_128_s0.5_300"]()
+    g = run_gpu(w)
+    sim = Simulator(w.cfg)
+    cfg = w.cfg
+    loss = np.zeros(cfg.n_instances, np.float32)
+    x = np.zeros((cfg.dim, cfg.n_total), np.float32)
+    sim.forward_host(w.x0, w.phi, w.mag, w.field, None, None, x, loss)
+    gp = np.zeros_like(w.phi)
+    gm = np.zeros_like(w.mag)
+    gf = np.zeros_like(w.field)
+    sim.backward_host(np.ones(cfg.n_instances, np.float32), gp, gm, gf)
+    sim.close()
+    assert rel_l2(x, g["x"]) <= 1e-6
+    assert cosine(gp, g["g_phi"]) >= 0.99999 and cosine(gf, g["g_field"]) >= 0.99999
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_block_size_does_not_change_results(block):
+    w, of, ob = _oracle("walker2d_128_s0.5_300")
+    g = run_gpu(w, block=block)
+    assert_state(g, of, w)
+    assert_grads(g, ob, w)
