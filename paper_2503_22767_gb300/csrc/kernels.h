@@ -58,9 +58,10 @@ cudaError_t launch_reorder(int ncomp, const Params& P, const float* src, float* 
 // adj_old[c][perm[p]] = adj_new[c][p]
 cudaError_t launch_unpermute(int ncomp, const Params& P, const float* src, float* dst,
                              const int* perm, cudaStream_t st);
-// out[c][id[p]] = s[c][p] for components [c0, c0 + ncomp), out stride n_total
+// out[c][id[p]] = s[c][p] for components [c0, c0 + ncomp), out stride n_total;
+// diag > 0 marks a diag x diag block stored as E = F - I (F is written).
 cudaError_t launch_to_input_order(int ncomp, const Params& P, const float* s, int c0,
-                                  const int* id, float* out, cudaStream_t st);
+                                  const int* id, float* out, cudaStream_t st, int diag = 0);
 // current-order design from the per-design arrays
 cudaError_t launch_gather_design(int dim, const Params& P, const int* id, const int* inst_off,
                                  const int* dbase, const float* phi_d, const float* mag_d,

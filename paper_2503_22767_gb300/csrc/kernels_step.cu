@@ -9,7 +9,9 @@
 // forward branches replayed.
 //
 // Particle arrays are structure-of-arrays with component stride P.np:
-// x[D], v[D], C[D][D], F[D][D] (row-major), i.e. 2D + 2D^2 components.
+// x[D], v[D], C[D][D], E[D][D] (row-major), i.e. 2D + 2D^2 components, where
+// E = F - I is the strain form of the deformation gradient (see
+// mpm_device.cuh: it keeps small strains exact to float32 precision).
 // Grids are float4 per node ([inst][node]): accumulators (m, mv), velocities
 // (v, 0), adjoints (mbar, mvbar).
 #include "kernels.h"
@@ -20,6 +22,7 @@ namespace {
 
 template <int D>
 struct Layout {
+    // F slot holds E = F - I
     static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, N = 2 * D + 2 * D * D;
 };
 
@@ -126,21 +129,22 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
                 for (int j = 0; j < D; ++j) C[i][j] *= P.kappa;
                 x[i] += P.dt * v[i];                              // Eq. 21
             }
+            // Eq. 22 in strain form: E' = E + dt C (I + E)
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    float acc = F[i][j];
+                    float acc = C[i][j];
 #pragma unroll
-                    for (int k = 0; k < D; ++k) acc += P.dt * C[i][k] * F[k][j];  // Eq. 22
-                    Fn[i][j] = acc;
+                    for (int k = 0; k < D; ++k) acc += C[i][k] * F[k][j];
+                    Fn[i][j] = F[i][j] + P.dt * acc;
                 }
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
                 for (int j = 0; j < D; ++j) F[i][j] = Fn[i][j];
-            float J = det<D>(F);
-            if (!(J > 0.0f) || !isfinite(J)) flags |= kErrNumeric;
+            float Jm1 = det_minus_one<D>(F);
+            if (!(Jm1 > -1.0f) || !isfinite(Jm1)) flags |= kErrNumeric;
             store_vec<D>(a.s_out, L::X, np, p, x);
             store_mat<D>(a.s_out, L::F, np, p, F);
             if (WRITE_ALL) {
@@ -164,16 +168,18 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
             Br[i] = a.mag[(long long)i * np + p];
             Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
         }
-        piola<D>(F, S, Br, Ba, Pk);
+        piola<D>(S, Br, Ba, Pk);
         const float sc = P.dt * P.kappa * P.p_vol;
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                float pft = 0.0f;
+                float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
 #pragma unroll
                 for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
-                A[i][j] = mp * C[i][j] - sc * pft;  // affine momentum, reading R1
+                // MLS-MPM affine momentum (Eq. 15 with the time step and the
+                // x_i - x_p offset of the MLS-MPM form): m C - dt (4/dx^2) V P F^T
+                A[i][j] = mp * C[i][j] - sc * pft;
             }
         float4* __restrict__ ai = a.acc + (long long)inst * P.nodes;
 #pragma unroll
@@ -276,13 +282,13 @@ __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
             if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
             StressParts<D> S;
             stress_parts<D>(F, phi, P, S);
-            piola<D>(F, S, Br, Ba, Pk);
+            piola<D>(S, Br, Ba, Pk);
             const float sc = P.dt * P.kappa * P.p_vol;
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    float pft = 0.0f;
+                    float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
 #pragma unroll
                     for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
                     A[i][j] = mp * Cn[i][j] - sc * pft;
@@ -340,10 +346,10 @@ __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
             for (int i = 0; i < D; ++i)
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    float pb = 0.0f, fb = 0.0f;
+                    float pb = Ab[i][j], fb = 0.0f;  // (Abar F)_ij with F = I + E
 #pragma unroll
                     for (int k = 0; k < D; ++k) {
-                        pb += Ab[i][k] * F[k][j];    // (Abar F)_ij
+                        pb += Ab[i][k] * F[k][j];
                         fb += Ab[k][i] * Pk[k][j];   // (Abar^T P)_ij
                     }
                     Pb[i][j] = -sc * pb;
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                float fft = 0.0f, ctf = Fb[i][j];
+                float fft = Fb[i][j], ctf = Fb[i][j];  // F = I + E
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     fft += Fb[i][k] * F[j][k];          // (Fbar F^T)_ij
@@ -463,7 +469,7 @@ __global__ void k_init_state(Params P, const float* __restrict__ x0, const float
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             s[(L::C + i * D + j) * np + p] = 0.0f;
-            s[(L::F + i * D + j) * np + p] = (i == j) ? 1.0f : 0.0f;
+            s[(L::F + i * D + j) * np + p] = 0.0f;  // E = F - I = 0 at rest
         }
     }
     id[p] = p;
@@ -487,12 +493,18 @@ __global__ void k_unpermute(Params P, int ncomp, const float* __restrict__ src,
     for (int c = 0; c < ncomp; ++c) dst[c * P.np + q] = src[c * P.np + p];
 }
 
+// diag > 0: the components are a diag x diag block stored as E = F - I;
+// write F (add the identity on the diagonal).
 __global__ void k_to_input_order(Params P, int ncomp, const float* __restrict__ s, int c0,
-                                 const int* __restrict__ id, float* __restrict__ out) {
+                                 const int* __restrict__ id, float* __restrict__ out, int diag) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P.n_total) return;
     int q = id[p];
-    for (int c = 0; c < ncomp; ++c) out[(long long)c * P.n_total + q] = s[(c0 + c) * P.np + p];
+    for (int c = 0; c < ncomp; ++c) {
+        float val = s[(c0 + c) * P.np + p];
+        if (diag > 0 && c % (diag + 1) == 0) val += 1.0f;
+        out[(long long)c * P.n_total + q] = val;
+    }
 }
 
 __device__ __forceinline__ long long design_index(int g, const int* __restrict__ inst_off,
@@ -698,9 +710,9 @@ cudaError_t launch_unpermute(int ncomp, const Params& P, const float* src, float
 }
 
 cudaError_t launch_to_input_order(int ncomp, const Params& P, const float* s, int c0,
-                                  const int* id, float* out, cudaStream_t st) {
+                                  const int* id, float* out, cudaStream_t st, int diag) {
     if (P.n_total == 0) return cudaSuccess;
-    k_to_input_order<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, ncomp, s, c0, id, out);
+    k_to_input_order<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, ncomp, s, c0, id, out, diag);
     return cudaGetLastError();
 }
 

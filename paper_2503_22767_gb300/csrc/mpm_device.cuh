@@ -124,17 +124,44 @@ __device__ __forceinline__ void node_term(const Stencil<D>& s, int k, const Para
 // small dense algebra
 // ---------------------------------------------------------------------------
 template <int D>
-__device__ __forceinline__ float det(const float (&F)[D][D]) {
-    if (D == 2) return F[0][0] * F[1 % D][1 % D] - F[0][1 % D] * F[1 % D][0];
-    return F[0][0] * (F[1][1] * F[2 % D][2 % D] - F[1][2 % D] * F[2 % D][1]) -
-           F[0][1] * (F[1][0] * F[2 % D][2 % D] - F[1][2 % D] * F[2 % D][0]) +
-           F[0][2 % D] * (F[1][0] * F[2 % D][1] - F[1][1] * F[2 % D][0]);
+__device__ __forceinline__ float frob(const float (&A)[D][D], const float (&B)[D][D]) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) s += A[i][j] * B[i][j];
+    return s;
 }
 
-// H = F^{-T} = cofactor(F) / J
+__device__ __forceinline__ float int_pow(float x, int q) {
+    float r = 1.0f;
+    for (int i = 0; i < q; ++i) r *= x;
+    return r;
+}
+
+// det(I + E) - 1, expanded so that small strains keep their digits:
+// tr E + (sum of principal 2x2 minors of E) + det E.
 template <int D>
-__device__ __forceinline__ void inv_transpose(const float (&F)[D][D], float J, float (&H)[D][D]) {
-    float rJ = 1.0f / J;
+__device__ __forceinline__ float det_minus_one(const float (&E)[D][D]) {
+    if (D == 2) return E[0][0] + E[1 % D][1 % D] + (E[0][0] * E[1 % D][1 % D] - E[0][1 % D] * E[1 % D][0]);
+    const float m2 = (E[0][0] * E[1][1] - E[0][1] * E[1][0]) +
+                     (E[0][0] * E[2 % D][2 % D] - E[0][2 % D] * E[2 % D][0]) +
+                     (E[1][1] * E[2 % D][2 % D] - E[1][2 % D] * E[2 % D][1]);
+    const float d3 = E[0][0] * (E[1][1] * E[2 % D][2 % D] - E[1][2 % D] * E[2 % D][1]) -
+                     E[0][1] * (E[1][0] * E[2 % D][2 % D] - E[1][2 % D] * E[2 % D][0]) +
+                     E[0][2 % D] * (E[1][0] * E[2 % D][1] - E[1][1] * E[2 % D][0]);
+    return E[0][0] + E[1][1] + E[2 % D][2 % D] + m2 + d3;
+}
+
+// H = F^{-T} = cofactor(I + E) / J
+template <int D>
+__device__ __forceinline__ void inv_transpose_of(const float (&E)[D][D], float J, float (&H)[D][D]) {
+    float F[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) F[i][j] = E[i][j] + (i == j ? 1.0f : 0.0f);
+    const float rJ = 1.0f / J;
     if (D == 2) {
         H[0][0] = F[1 % D][1 % D] * rJ;
         H[0][1 % D] = -F[1 % D][0] * rJ;
@@ -151,86 +178,90 @@ __device__ __forceinline__ void inv_transpose(const float (&F)[D][D], float J, f
     }
 }
 
-template <int D>
-__device__ __forceinline__ float frob(const float (&A)[D][D], const float (&B)[D][D]) {
-    float s = 0.0f;
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) s += A[i][j] * B[i][j];
-    return s;
-}
-
-__device__ __forceinline__ float int_pow(float x, int q) {
-    float r = 1.0f;
-    for (int i = 0; i < q; ++i) r *= x;
-    return r;
-}
-
 // ---------------------------------------------------------------------------
-// constitutive model: Piola stress of Eq. 7 under the SIMP weights of Eq. 31
-// 2D is plane strain: F3 = diag(F, 1), I1 = |F|^2 + 1, J = det F.
+// constitutive model: Piola stress of Eq. 7 under the SIMP weights of Eq. 31.
+//
+// The kernels keep the deformation gradient as its strain E = F - I.  In
+// float32, F itself near I holds a strain of 1e-4 with three significant
+// digits; J - 1, I1 - 3 and the deviatoric term F - (I1/3) F^{-T} computed
+// from F lose the rest.  From E they are formed without cancellation:
+//   J - 1                = det_minus_one(E)
+//   I1 - 3               = 2 tr E + |E|^2      (2D plane strain: the same,
+//                                               F3 = diag(F, 1), I1 = |F|^2 + 1)
+//   F - (I1/3) F^{-T}    = H E^T + E - ((I1 - 3)/3) H,   since I - H = H E^T.
 // ---------------------------------------------------------------------------
 template <int D>
 struct StressParts {
-    float J, I1, a, b;   // a = G J^{-2/3}, b = K J (J - 1)
-    float H[D][D];       // F^{-T}
-    float s, sE;         // phi^q and eps + (1 - eps) phi^q
+    float J, Jm1, I1, a, b;  // a = G J^{-2/3}, b = K J (J - 1)
+    float H[D][D];           // F^{-T}
+    float dev[D][D];         // F - (I1/3) F^{-T}
+    float s, sE;             // phi^q and eps + (1 - eps) phi^q
 };
 
 template <int D>
-__device__ __forceinline__ void stress_parts(const float (&F)[D][D], float phi, const Params& P,
+__device__ __forceinline__ void stress_parts(const float (&E)[D][D], float phi, const Params& P,
                                              StressParts<D>& S) {
-    S.J = det<D>(F);
-    inv_transpose<D>(F, S.J, S.H);
-    S.I1 = frob<D>(F, F) + (D == 2 ? 1.0f : 0.0f);
-    float r13 = rcbrtf(S.J);
+    S.Jm1 = det_minus_one<D>(E);
+    S.J = 1.0f + S.Jm1;
+    inv_transpose_of<D>(E, S.J, S.H);
+    float trE = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) trE += E[i][i];
+    const float q3 = (2.0f * trE + frob<D>(E, E)) * (1.0f / 3.0f);  // (I1 - 3)/3
+    S.I1 = 3.0f + 3.0f * q3;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float hEt = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) hEt += S.H[i][k] * E[j][k];
+            S.dev[i][j] = hEt + E[i][j] - q3 * S.H[i][j];
+        }
+    const float r13 = rcbrtf(S.J);
     S.a = P.G * r13 * r13;
-    S.b = P.K * S.J * (S.J - 1.0f);
+    S.b = P.K * S.J * S.Jm1;
     S.s = int_pow(phi, P.simp_q);
     S.sE = P.eps + (1.0f - P.eps) * S.s;
 }
 
 template <int D>
-__device__ __forceinline__ void piola(const float (&F)[D][D], const StressParts<D>& S,
-                                      const float (&Br)[D], const float (&Ba)[D],
-                                      float (&Pk)[D][D]) {
-    float third = S.I1 * (1.0f / 3.0f);
-    float sm = S.s * (1.0f / kMu0);
+__device__ __forceinline__ void piola(const StressParts<D>& S, const float (&Br)[D],
+                                      const float (&Ba)[D], float (&Pk)[D][D]) {
+    const float sm = S.s * (1.0f / kMu0);
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            float pe = S.a * (F[i][j] - third * S.H[i][j]) + S.b * S.H[i][j];
+            const float pe = S.a * S.dev[i][j] + S.b * S.H[i][j];
             Pk[i][j] = S.sE * pe - sm * Ba[i] * Br[j];
         }
 }
 
-// Reverse of piola(): given Pbar, accumulate into Fbar and return the
-// phi, B~_r and B_applied cotangents (added to phib, brb, bab).
+// Reverse of piola(): given Pbar, accumulate dL/dF (= dL/dE) into Fbar and
+// the phi, B~_r and B_applied cotangents into phib, brb, bab.
 //   dJ = J H:dF, dI1 = 2F:dF, d(F^{-T}) = -H dF^T H, d a = -(2/3) a H:dF,
 //   d b = K (2J - 1) J H:dF.
 template <int D>
-__device__ __forceinline__ void piola_adjoint(const float (&F)[D][D], float phi,
+__device__ __forceinline__ void piola_adjoint(const float (&E)[D][D], float phi,
                                               const StressParts<D>& S, const float (&Br)[D],
                                               const float (&Ba)[D], const float (&Pbar)[D][D],
                                               const Params& P, float (&Fbar)[D][D], float& phib,
                                               float (&brb)[D], float (&bab)[D]) {
-    float third = S.I1 * (1.0f / 3.0f);
+    const float third = S.I1 * (1.0f / 3.0f);
     // phi: d s / d phi = q phi^(q-1)
-    float ds = P.simp_q > 0 ? (float)P.simp_q * int_pow(phi, P.simp_q - 1) : 0.0f;
+    const float ds = P.simp_q > 0 ? (float)P.simp_q * int_pow(phi, P.simp_q - 1) : 0.0f;
     float pe_dot = 0.0f, pm_dot = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            float pe = S.a * (F[i][j] - third * S.H[i][j]) + S.b * S.H[i][j];
-            pe_dot += Pbar[i][j] * pe;
+            pe_dot += Pbar[i][j] * (S.a * S.dev[i][j] + S.b * S.H[i][j]);
             pm_dot -= Pbar[i][j] * Ba[i] * Br[j];
         }
     phib += ds * ((1.0f - P.eps) * pe_dot + pm_dot * (1.0f / kMu0));
     // magnetic part  -(s/mu0) Ba (x) Br
-    float sm = S.s * (1.0f / kMu0);
+    const float sm = S.s * (1.0f / kMu0);
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -244,30 +275,30 @@ __device__ __forceinline__ void piola_adjoint(const float (&F)[D][D], float phi,
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) Pb[i][j] = S.sE * Pbar[i][j];
-    float PbF = frob<D>(Pb, F);
-    float PbH = frob<D>(Pb, S.H);
-    // X = H Pb^T H
-    float HPt[D][D];
+    const float PbDev = frob<D>(Pb, S.dev);  // Pb : (F - (I1/3) H), without cancellation
+    const float PbH = frob<D>(Pb, S.H);
+    float HPt[D][D];  // H Pb^T
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             float acc = 0.0f;
 #pragma unroll
-            for (int l = 0; l < D; ++l) acc += S.H[i][l] * Pb[k][l];  // (H Pb^T)_ik
+            for (int l = 0; l < D; ++l) acc += S.H[i][l] * Pb[k][l];
             HPt[i][k] = acc;
         }
-    float cH = -(2.0f / 3.0f) * S.a * (PbF - third * PbH) + P.K * (2.0f * S.J - 1.0f) * S.J * PbH;
-    float cF = -(2.0f / 3.0f) * S.a * PbH;
-    float cX = S.a * third - S.b;
+    const float cH = -(2.0f / 3.0f) * S.a * PbDev + P.K * (2.0f * S.J - 1.0f) * S.J * PbH;
+    const float cF = -(2.0f / 3.0f) * S.a * PbH;
+    const float cX = S.a * third - S.b;
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            float X = 0.0f;
+            float X = 0.0f;  // (H Pb^T H)_ij
 #pragma unroll
             for (int k = 0; k < D; ++k) X += HPt[i][k] * S.H[k][j];
-            Fbar[i][j] += S.a * Pb[i][j] + cH * S.H[i][j] + cF * F[i][j] + cX * X;
+            const float Fij = E[i][j] + (i == j ? 1.0f : 0.0f);
+            Fbar[i][j] += S.a * Pb[i][j] + cH * S.H[i][j] + cF * Fij + cX * X;
         }
 }
 

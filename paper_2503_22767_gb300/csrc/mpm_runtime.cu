@@ -773,7 +773,7 @@ int mpm_read_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* 
     if (x) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, x, st));
     if (v) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, d, h->id_cur, v, st));
     if (C) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d, h->id_cur, C, st));
-    if (F) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d + d * d, h->id_cur, F, st));
+    if (F) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d + d * d, h->id_cur, F, st, d));
     MPM_CUDA(h, cudaStreamSynchronize(st));
     return MPM_OK;
 }

@@ -244,7 +244,8 @@ def test_empty_and_ragged_instances():
 
 def test_single_particle_and_no_particles():
     import oracle
-    w = W.tiny_2d(seed=1, n_steps=10, res=16, per_axis=1, cells=(1, 1), bound=1, lift=6)
+    w = W.tiny_2d(seed=1, n_steps=10, res=16, per_axis=1, cells=(1, 1), bound=1, lift=6,
+                  v_scale=0.3)
     assert w.cfg.n_total == 1
     g = run_gpu(w)
     assert_state(g, oracle.forward(w), w)
