@@ -37,8 +37,10 @@ CLASS_NAMES = ["forward particle (G2P+P2G)", "adjoint particle (P2G^T+G2P^T)", "
                "grid adjoint"]
 
 
-def workload(seed=0):
-    return W.walker_2d(seed=seed, n_steps=4000, checkpoint_every=100)
+def workload(seed=0, substeps=4000):
+    """The 2D locomotion workload (walker_2d: 30,000 particles, 128^2 grid);
+    ``substeps`` below 4,000 only for short profiling runs."""
+    return W.walker_2d(seed=seed, n_steps=substeps, checkpoint_every=100)
 
 
 def workload_desc(w):
@@ -139,7 +141,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_2503_22767_gb300.sim import Simulator
 
-    w = workload(seed=rank)
+    w = workload(seed=rank, substeps=args.substeps)
     cfg = w.cfg
     sim = Simulator(cfg)
     t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -205,6 +207,8 @@ def run_ours(args):
         "timed_launches": launches_timed,
         "time_share_by_class": {CLASS_NAMES[c]: round(per_class_ms[c] / max(sum(per_class_ms), 1e-9), 3)
                                 for c in range(4)},
+        "avg_launch_us_by_class": {CLASS_NAMES[c]: round(1e3 * per_class_ms[c] / max(stats["timed_launches"][c], 1), 2)
+                                   for c in range(4)},
     }
     if args.traffic_bytes:
         roofline["traffic"] = args.traffic_bytes
@@ -217,7 +221,7 @@ def run_ours(args):
     hgp = torch.empty(phi.shape).pin_memory()
     hgm = torch.empty(mag.shape).pin_memory()
     hgf = torch.empty(field.shape).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.e2e_steps if args.e2e_steps else max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -330,6 +334,9 @@ def main(argv=None):
                     help="time every k-th launch of each kernel class with CUDA events")
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--substeps", type=int, default=4000,
+                    help="horizon of the timed workload (4000 = the full configuration)")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end iterations (default min(steps, 3))")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args(argv)
