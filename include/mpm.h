@@ -216,6 +216,42 @@ typedef struct {
 int mpm_get_stats(const mpm_handle* h, mpm_stats* out);
 int mpm_reset_stats(mpm_handle* h);
 
+/*
+ * One substep of ONE instance that allocates no device memory.
+ *
+ * This entry point has no counterpart in the paper: it is an interface for
+ * callers that must not call cudaMalloc.  Examples are a host framework whose
+ * pool allocator owns the whole device-memory budget, and a latency-critical
+ * loop where an allocation could block or fail.  Instead of a handle it keeps
+ * its grid scratch in a fixed array compiled into the library: every GPU that
+ * loads the library holds MPM_NOALLOC_MAX_NODES x 2 float4 (8 MiB) of it
+ * until the process exits.  The caller passes all inputs and outputs.
+ *
+ * It runs P2G (Eq. 14-15), the grid operation (Eq. 16-18) and G2P
+ * (Eq. 19-22) for substep `substep` of the configuration `cfg`:
+ *   cfg        n_instances must be 1; grid_res^dim <= MPM_NOALLOC_MAX_NODES
+ *              (512^2 in 2D, 64^3 in 3D); n_steps sizes `field`; loss_kind,
+ *              checkpoint_every and the design fields are not used
+ *   substep    index into field, 0 <= substep < n_steps
+ *   state_in   device [2d + 2d^2][N] float32 SoA: x[d], v[d], C[d][d],
+ *              E[d][d] with E = F - I (F = I and C = 0 at rest)
+ *   phi_bar    device [N]; mag device [d][N] (B~_r, Tesla)
+ *   field      device [n_steps][d] (B_applied, Tesla)
+ *   state_out  device [2d + 2d^2][N], same layout; may be state_in itself
+ * Blocks until the substep finishes on cuda_stream.  Errors: MPM_ERR_ARG (bad
+ * config, sizes beyond the scratch maximum, missing pointers; reason on
+ * stderr), MPM_ERR_CUDA, MPM_ERR_DOMAIN, MPM_ERR_NUMERIC.
+ * The first call on a device looks up the scratch array's address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; each
+ * call clears what must start at zero, but calls that overlap on the GPU
+ * (other streams, threads or processes on the same device) race on it.
+ */
+#define MPM_NOALLOC_MAX_NODES 262144
+int mpm_substep_noalloc(const mpm_config* cfg, int substep, const float* state_in,
+                        const float* phi_bar, const float* mag, const float* field,
+                        float* state_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

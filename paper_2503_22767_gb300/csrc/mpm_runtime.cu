@@ -29,6 +29,7 @@
 
 #include "kernels.h"
 #include "mpm.h"
+#include "runtime_internal.h"
 
 using mpm::Params;
 using mpm::StepArgs;
@@ -642,6 +643,10 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
 }
 
 }  // namespace
+
+namespace mpm {
+int check_config(const mpm_config* cfg, std::string* why) { return validate(cfg, *why); }
+}  // namespace mpm
 
 // ---------------------------------------------------------------------------
 // C ABI
