@@ -192,8 +192,13 @@ int mpm_sort_particles(mpm_handle* h, const float* x, int* keys, int* perm, void
 enum {
     MPM_OPT_TIMING = 1, /* k > 0: time every k-th launch of each kernel class with CUDA
                            events (on the call's stream); 0 (default): off */
-    MPM_OPT_BLOCK = 2   /* threads per block of the particle kernels: a multiple of 32
+    MPM_OPT_BLOCK = 2,  /* threads per block of the particle kernels: a multiple of 32
                            in [32, 256] (default 128) */
+    MPM_OPT_FUSE_GRID = 3, /* 1 (default): the particle kernels apply the grid operation
+                              (Eq. 16-18) and its reverse per stencil node, one kernel per
+                              substep; 0: separate grid kernels */
+    MPM_OPT_GRAPHS = 4  /* 1 (default): each pass is captured once as a CUDA graph on an
+                           internal stream and replayed on cuda_stream; 0: direct launches */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);

@@ -31,16 +31,26 @@ struct StepArgs {
     int* err = nullptr;
     int n_p2g = 0;                   // substep index of the P2G (or P2G^T) part
     int n_g2p = 0;                   // substep index of the G2P part (momentum row)
+    // fused grid operation: the particle kernels evaluate Eq. 16-18 (and its
+    // reverse) per stencil node from the accumulators instead of reading V /
+    // gadj written by a separate grid kernel
+    const float4* accG = nullptr;    // accumulator of the G2P (or G2P^T) substep
+    const float4* accP = nullptr;    // accumulator of the P2G^T substep
+    const float4* VbarIn = nullptr;  // Vbar of the P2G^T substep
+    float4* zero4 = nullptr;         // buffer the kernel clears for a later substep
+    long long zero_n = 0;            // its length in float4
 };
 
 // forward particle kernel: G2P of substep n_g2p and/or P2G of n_p2g.
 // write_all: also store v and C (needed at checkpoints and in the store pass).
-cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, const Params& P,
-                           const StepArgs& a, int block, cudaStream_t st);
+// fuse: take the grid velocity from a.accG through the grid operation.
+cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, bool fuse,
+                           const Params& P, const StepArgs& a, int block, cudaStream_t st);
 // adjoint particle kernel: P2G^T of substep n_p2g and/or G2P^T of n_p2g - 1
 // (or, without P2G^T, of substep n_p2g).
-cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, const Params& P, const StepArgs& a,
-                           int block, cudaStream_t st);
+// fuse: grid adjoint from (a.accP, a.VbarIn) and grid velocity from a.accG.
+cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, const Params& P,
+                           const StepArgs& a, int block, cudaStream_t st);
 // grid operation on every node of every instance: acc -> V; clears acc
 // (lean) or clears acc_next (store pass).
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,

@@ -77,9 +77,33 @@ constexpr int stencil_size() { return D == 2 ? kStencil2 : kStencil3; }
 // ---------------------------------------------------------------------------
 // forward particle kernel
 // ---------------------------------------------------------------------------
-template <int D, bool G2P, bool P2G, bool WRITE_ALL>
+// Clears a.zero4 (grid-stride over the whole launch); fused mode only.
+__device__ __forceinline__ void clear_buffer(const StepArgs& a) {
+    if (a.zero4 == nullptr) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.zero_n; i += stride)
+        a.zero4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Grid velocity at a stencil node: read V (separate grid kernel) or apply
+// the grid operation (Eq. 16-18) to the node's accumulator (fused).
+template <int D, bool FUSE>
+__device__ __forceinline__ void node_velocity(const float4* __restrict__ grid, const NodeTerm<D>& t,
+                                              const Params& P, float (&gv)[D]) {
+    const float4 g = __ldg(grid + t.node);
+    if (FUSE) {
+        float mv[D];
+        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+        grid_velocity<D>(P, t.c, g.x, mv, gv);
+    } else {
+        unpack3<D>(g, gv);
+    }
+}
+
+template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE>
 __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
+    if (FUSE) clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
@@ -102,7 +126,7 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
         if (active) {
             Stencil<D> s;
             if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
-            const float4* __restrict__ Vi = a.V + (long long)inst * P.nodes;
+            const float4* __restrict__ Vi = (FUSE ? a.accG : a.V) + (long long)inst * P.nodes;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 v[i] = 0.0f;
@@ -114,7 +138,7 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
                 NodeTerm<D> t;
                 node_term<D>(s, k, P, t);
                 float gv[D];
-                unpack3<D>(__ldg(Vi + t.node), gv);
+                node_velocity<D, FUSE>(Vi, t, P, gv);
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
                     v[i] += t.w * gv[i];                          // Eq. 19
@@ -246,9 +270,10 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
 //         the adjoint of state m+1, scatters Vbar, writes the partial
 //         adjoint (x, F) of state m.
 // ---------------------------------------------------------------------------
-template <int D, bool P2GT, bool G2PT>
+template <int D, bool P2GT, bool G2PT, bool FUSE>
 __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
     using L = Layout<D>;
+    if (FUSE) clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
@@ -300,14 +325,24 @@ __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
 #pragma unroll
                 for (int j = 0; j < D; ++j) Ab[i][j] = 0.0f;
             }
-            const float4* __restrict__ gi = a.gadj + (long long)inst * P.nodes;
+            const float4* __restrict__ gi = (FUSE ? a.accP : a.gadj) + (long long)inst * P.nodes;
+            const float4* __restrict__ vbi = FUSE ? a.VbarIn + (long long)inst * P.nodes : nullptr;
 #pragma unroll
             for (int k = 0; k < stencil_size<D>(); ++k) {
                 NodeTerm<D> t;
                 node_term<D>(s, k, P, t);
                 float4 g = __ldg(gi + t.node);
                 float mvb[D];
-                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
+                if (FUSE) {
+                    // grid adjoint (reverse of Eq. 16-18) of this node, on the fly
+                    float mv[D], vbv[D], mbv;
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                    unpack3<D>(__ldg(vbi + t.node), vbv);
+                    grid_velocity_adjoint<D>(P, t.c, g.x, mv, vbv, mbv, mvb);
+                    g.x = mbv;
+                } else {
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
+                }
                 // value of this node's contribution: w * (mb mp + mvb . (mp v + A dpos))
                 float inner = g.x * mp, vcd = 0.0f;
 #pragma unroll
@@ -415,14 +450,14 @@ __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
                 Ct[i][j] = Cb[i][j] + P.dt * fft;
                 Fo[i][j] = ctf;
             }
-        const float4* __restrict__ Vi = a.V + (long long)inst * P.nodes;
+        const float4* __restrict__ Vi = (FUSE ? a.accG : a.V) + (long long)inst * P.nodes;
         float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
             NodeTerm<D> t;
             node_term<D>(s, k, P, t);
             float gv[D];
-            unpack3<D>(__ldg(Vi + t.node), gv);
+            node_velocity<D, FUSE>(Vi, t, P, gv);
             // Eq. 19-20 reversed: v' = sum w V, C' = kappa sum w V dpos^T
             float vdot = 0.0f, vcd = 0.0f, cd[D];
 #pragma unroll
@@ -628,44 +663,53 @@ inline int blocks_for(long long n, int block) { return (int)((n + block - 1) / b
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, bool FUSE>
 static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, const StepArgs& a,
                              int block, cudaStream_t st) {
-    dim3 grid(blocks_for(P.n_total, block));
-    if (P.n_total == 0) return cudaSuccess;
+    // a fused launch also clears a.zero4, so it runs even without particles
+    if (P.n_total == 0 && !(FUSE && a.zero4)) return cudaSuccess;
+    long long threads = P.n_total > 0 ? P.n_total : block;
+    dim3 grid(blocks_for(threads, block));
     if (g2p && p2g) {
-        if (all) k_forward<D, true, true, true><<<grid, block, 0, st>>>(P, a);
-        else k_forward<D, true, true, false><<<grid, block, 0, st>>>(P, a);
+        if (all) k_forward<D, true, true, true, FUSE><<<grid, block, 0, st>>>(P, a);
+        else k_forward<D, true, true, false, FUSE><<<grid, block, 0, st>>>(P, a);
     } else if (g2p) {
-        if (all) k_forward<D, true, false, true><<<grid, block, 0, st>>>(P, a);
-        else k_forward<D, true, false, false><<<grid, block, 0, st>>>(P, a);
+        if (all) k_forward<D, true, false, true, FUSE><<<grid, block, 0, st>>>(P, a);
+        else k_forward<D, true, false, false, FUSE><<<grid, block, 0, st>>>(P, a);
     } else {
-        k_forward<D, false, true, false><<<grid, block, 0, st>>>(P, a);
+        k_forward<D, false, true, false, FUSE><<<grid, block, 0, st>>>(P, a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, const Params& P,
-                           const StepArgs& a, int block, cudaStream_t st) {
-    return dim == 2 ? forward_d<2>(g2p, p2g, write_all, P, a, block, st)
-                    : forward_d<3>(g2p, p2g, write_all, P, a, block, st);
+cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, bool fuse,
+                           const Params& P, const StepArgs& a, int block, cudaStream_t st) {
+    if (dim == 2)
+        return fuse ? forward_d<2, true>(g2p, p2g, write_all, P, a, block, st)
+                    : forward_d<2, false>(g2p, p2g, write_all, P, a, block, st);
+    return fuse ? forward_d<3, true>(g2p, p2g, write_all, P, a, block, st)
+                : forward_d<3, false>(g2p, p2g, write_all, P, a, block, st);
 }
 
-template <int D>
+template <int D, bool FUSE>
 static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepArgs& a, int block,
                              cudaStream_t st) {
-    dim3 grid(blocks_for(P.n_total, block));
-    if (P.n_total == 0) return cudaSuccess;
-    if (p2gt && g2pt) k_adjoint<D, true, true><<<grid, block, 0, st>>>(P, a);
-    else if (p2gt) k_adjoint<D, true, false><<<grid, block, 0, st>>>(P, a);
-    else k_adjoint<D, false, true><<<grid, block, 0, st>>>(P, a);
+    if (P.n_total == 0 && !(FUSE && a.zero4)) return cudaSuccess;
+    long long threads = P.n_total > 0 ? P.n_total : block;
+    dim3 grid(blocks_for(threads, block));
+    if (p2gt && g2pt) k_adjoint<D, true, true, FUSE><<<grid, block, 0, st>>>(P, a);
+    else if (p2gt) k_adjoint<D, true, false, FUSE><<<grid, block, 0, st>>>(P, a);
+    else k_adjoint<D, false, true, FUSE><<<grid, block, 0, st>>>(P, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, const Params& P, const StepArgs& a,
-                           int block, cudaStream_t st) {
-    return dim == 2 ? adjoint_d<2>(p2gt, g2pt, P, a, block, st)
-                    : adjoint_d<3>(p2gt, g2pt, P, a, block, st);
+cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, const Params& P,
+                           const StepArgs& a, int block, cudaStream_t st) {
+    if (dim == 2)
+        return fuse ? adjoint_d<2, true>(p2gt, g2pt, P, a, block, st)
+                    : adjoint_d<2, false>(p2gt, g2pt, P, a, block, st);
+    return fuse ? adjoint_d<3, true>(p2gt, g2pt, P, a, block, st)
+                : adjoint_d<3, false>(p2gt, g2pt, P, a, block, st);
 }
 
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,

@@ -86,6 +86,7 @@ __device__ __forceinline__ bool make_stencil(const float (&x)[D], const Params& 
 template <int D>
 struct NodeTerm {
     long long node;  // node index within the instance grid
+    int c[D];        // node coordinates
     float w;         // weight N(x_p - x_i)
     float gw[D];     // d w / d x_p
     float dpos[D];   // x_i - x_p
@@ -115,7 +116,8 @@ __device__ __forceinline__ void node_term(const Stencil<D>& s, int k, const Para
             if (a != c) g *= s.w[a][o[a]];
         t.gw[c] = g;
         t.dpos[c] = ((float)o[c] - s.r[c]) * P.dx;
-        idx = idx * P.res + (s.base[c] + o[c]);
+        t.c[c] = s.base[c] + o[c];
+        idx = idx * P.res + t.c[c];
     }
     t.node = idx;
 }

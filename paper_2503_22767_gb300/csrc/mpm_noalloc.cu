@@ -156,7 +156,7 @@ extern "C" int mpm_substep_noalloc(const mpm_config* cfg, int substep, const flo
     a.err = err;
     a.acc = acc;
     a.n_p2g = substep;
-    if ((e = mpm::launch_forward(d, false, true, false, P, a, 128, st)) != cudaSuccess)
+    if ((e = mpm::launch_forward(d, false, true, false, false, P, a, 128, st)) != cudaSuccess)
         return report(MPM_ERR_CUDA, cudaGetErrorString(e));
     if ((e = mpm::launch_grid(d, P, acc, V, nullptr, false, st)) != cudaSuccess)
         return report(MPM_ERR_CUDA, cudaGetErrorString(e));
@@ -165,7 +165,7 @@ extern "C" int mpm_substep_noalloc(const mpm_config* cfg, int substep, const flo
     g.s_out = state_out;
     g.V = V;
     g.n_g2p = substep;
-    if ((e = mpm::launch_forward(d, true, false, true, P, g, 128, st)) != cudaSuccess)
+    if ((e = mpm::launch_forward(d, true, false, true, false, P, g, 128, st)) != cudaSuccess)
         return report(MPM_ERR_CUDA, cudaGetErrorString(e));
 
     int flags = 0;

@@ -43,6 +43,14 @@ struct EventPair {
     double bytes = 0.0;
 };
 
+// One sampled launch inside a captured graph: its event pair stays owned by
+// the graph and is read after every replay.
+struct TimedLaunch {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes;
+};
+
 }  // namespace
 
 struct mpm_handle {
@@ -99,6 +107,23 @@ struct mpm_handle {
     int* perm = nullptr;
     mpm::SortBuffers sb;
 
+    float4* acc3 = nullptr;   // fused mode: three rotating P2G accumulators
+    float4* Vbar3 = nullptr;  // fused mode: three rotating G2P^T scatter targets
+
+    // --- options ---
+    bool fuse = true;     // grid operation folded into the particle kernels
+    bool graphs = true;   // replay the forward / backward passes as CUDA graphs
+    bool v0_given = false;
+
+    // --- CUDA graphs of the two passes (captured on first use) ---
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    std::vector<TimedLaunch> graph_timing[2];
+    bool capturing = false;
+    int capture_pass = 0;
+    long long graph_launches[2] = {0, 0};  // kernels inside each captured graph
+    bool ran_graph[2] = {false, false};
+
     // --- run state ---
     bool forward_done = false;
     float* cur = nullptr;  // final state of the last forward
@@ -148,7 +173,22 @@ int dalloc(mpm_handle* h, T** p, long long count) {
     return MPM_OK;
 }
 
+void drop_graphs(mpm_handle* h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->exec[i]) cudaGraphExecDestroy(h->exec[i]);
+        h->exec[i] = nullptr;
+        for (auto& t : h->graph_timing[i]) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        h->graph_timing[i].clear();
+    }
+}
+
 void free_all(mpm_handle* h) {
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     for (int c = 0; c < kNumClasses; ++c) {
@@ -184,8 +224,13 @@ int timed(mpm_handle* h, int cls, double bytes, cudaStream_t st, F&& launch) {
     bool time_it = h->timing_stride > 0 && (h->class_launch[cls] % h->timing_stride) == 0;
     h->class_launch[cls]++;
     h->launches++;
-    EventPair* ev = nullptr;
-    if (time_it) {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (time_it && h->capturing) {
+        // event-record nodes of the graph being captured
+        MPM_CUDA(h, cudaEventCreate(&ea));
+        MPM_CUDA(h, cudaEventCreate(&eb));
+        h->graph_timing[h->capture_pass].push_back(TimedLaunch{cls, ea, eb, bytes});
+    } else if (time_it) {
         auto& pool = h->events[cls];
         if (h->ev_used[cls] == pool.size()) {
             EventPair e;
@@ -193,16 +238,42 @@ int timed(mpm_handle* h, int cls, double bytes, cudaStream_t st, F&& launch) {
             MPM_CUDA(h, cudaEventCreate(&e.b));
             pool.push_back(e);
         }
-        ev = &pool[h->ev_used[cls]++];
+        EventPair* ev = &pool[h->ev_used[cls]++];
         ev->bytes = bytes;
-        MPM_CUDA(h, cudaEventRecord(ev->a, st));
+        ea = ev->a;
+        eb = ev->b;
     }
+    if (ea) MPM_CUDA(h, cudaEventRecord(ea, st));
     cudaError_t e = launch();
     if (e != cudaSuccess) {
         h->err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
         return MPM_ERR_CUDA;
     }
-    if (ev) MPM_CUDA(h, cudaEventRecord(ev->b, st));
+    if (eb) MPM_CUDA(h, cudaEventRecord(eb, st));
+    return MPM_OK;
+}
+
+// plain launches that are not timed (sort, design gathers, seeds...)
+template <typename F>
+int counted(mpm_handle* h, int n, F&& launch) {
+    h->launches += n;
+    cudaError_t e = launch();
+    if (e != cudaSuccess) {
+        h->err = std::string("launch failed: ") + cudaGetErrorString(e);
+        return MPM_ERR_CUDA;
+    }
+    return MPM_OK;
+}
+
+// after a stream sync: fold the sampled launches of a replayed graph
+int collect_graph_timing(mpm_handle* h, int pass) {
+    for (auto& t : h->graph_timing[pass]) {
+        float ms = 0.0f;
+        MPM_CUDA(h, cudaEventElapsedTime(&ms, t.a, t.b));
+        h->timed_ms[t.cls] += ms;
+        h->timed_bytes[t.cls] += t.bytes;
+        h->timed_launches[t.cls]++;
+    }
     return MPM_OK;
 }
 
@@ -357,6 +428,8 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->V, h->total_nodes);
     ALLOC(h->Vbar, h->total_nodes);
     ALLOC(h->gadj, h->total_nodes);
+    ALLOC(h->acc3, 3 * h->total_nodes);
+    ALLOC(h->Vbar3, 3 * h->total_nodes);
     ALLOC(h->adj, S);
     ALLOC(h->adj2, S);
     ALLOC(h->phi_cur, h->np);
@@ -395,6 +468,7 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     // padding lanes of the state buffers stay finite
     MPM_CUDA(h, cudaMemset(h->stA, 0, sizeof(float) * S));
     MPM_CUDA(h, cudaMemset(h->stB, 0, sizeof(float) * S));
+    MPM_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     return MPM_OK;
 }
 
@@ -420,6 +494,310 @@ int dcopy(mpm_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t 
     return MPM_OK;
 }
 
+// --- the forward pass: library-owned buffers only, so it can be captured ---
+int forward_pass(mpm_handle* h, cudaStream_t st) {
+    const int d = h->dim;
+    const Params& P = h->P;
+    const long long S = (long long)h->ncomp * h->np;
+    const long long G = h->total_nodes;
+    const bool fuse = h->fuse;
+    auto acc3 = [&](int i) { return h->acc3 + G * (i % 3); };
+    int rc;
+    MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    MPM_CUDA(h, cudaMemsetAsync(h->mom, 0, sizeof(float) * h->T * h->n_inst, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->Minst, 0, sizeof(float) * h->n_inst, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->loss_acc, 0, sizeof(float) * h->n_inst, st));
+    if (fuse) MPM_CUDA(h, cudaMemsetAsync(h->acc3, 0, sizeof(float4) * 2 * G, st));
+    else MPM_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(float4) * G, st));
+
+    float* cur = h->stA;
+    float* nxt = h->stB;
+    int* id_cur = h->idA;
+    int* id_nxt = h->idB;
+    if ((rc = counted(h, 1, [&] { return mpm::launch_init_state(d, P, h->st_x0, h->st_v0, cur, id_cur, st); })))
+        return rc;
+    for (int seg = 0; seg < h->n_seg; ++seg) {
+        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T);
+        // cell sort and reorder of the full state
+        if ((rc = counted(h, 5, [&] {
+                 return mpm::launch_sort(d, P, cur, h->np, h->d_inst_off, h->sb, h->perm, h->d_err, st);
+             })))
+            return rc;
+        if ((rc = counted(h, 1, [&] {
+                 return mpm::launch_reorder(h->ncomp, P, cur, nxt, h->perm, id_cur, id_nxt, st);
+             })))
+            return rc;
+        std::swap(cur, nxt);
+        std::swap(id_cur, id_nxt);
+        if ((rc = counted(h, 1, [&] {
+                 return mpm::launch_gather_design(d, P, id_cur, h->d_inst_off, h->d_dbase, h->phi_d,
+                                                  h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st);
+             })))
+            return rc;
+        MPM_CUDA(h, cudaMemcpyAsync(h->ck_state + S * seg, cur, sizeof(float) * S,
+                                    cudaMemcpyDeviceToDevice, st));
+        MPM_CUDA(h, cudaMemcpyAsync(h->ck_id + h->np * seg, id_cur, sizeof(int) * h->np,
+                                    cudaMemcpyDeviceToDevice, st));
+        MPM_CUDA(h, cudaMemcpyAsync(h->ck_perm + h->np * seg, h->perm, sizeof(int) * h->np,
+                                    cudaMemcpyDeviceToDevice, st));
+        StepArgs a = base_args(h);
+        a.mom = h->mom;
+        if (seg == 0) {
+            if ((rc = counted(h, 1, [&] {
+                     return mpm::launch_instance_mass(P, h->phi_cur, h->d_inst_off, h->Minst, st);
+                 })))
+                return rc;
+            a.s_in = cur;
+            a.acc = fuse ? acc3(0) : h->acc;
+            a.n_p2g = 0;
+            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
+                     return mpm::launch_forward(d, false, true, false, fuse, P, a, h->block, st);
+                 })))
+                return rc;
+        }
+        for (int n = s0; n < s1; ++n) {
+            if (!fuse && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
+                              return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, st);
+                          })))
+                return rc;
+            const bool p2g = n + 1 < h->T;
+            const bool all = n + 1 == s1;
+            a.s_in = cur;
+            a.s_out = nxt;
+            a.n_g2p = n;
+            a.n_p2g = n + 1;
+            if (fuse) {
+                a.accG = acc3(n);
+                a.acc = acc3(n + 1);
+                a.zero4 = acc3(n + 2);
+                a.zero_n = G;
+            } else {
+                a.V = h->V;
+                a.acc = h->acc;
+            }
+            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, all ? kFusedStore : kFused), st, [&] {
+                     return mpm::launch_forward(d, true, p2g, all, fuse, P, a, h->block, st);
+                 })))
+                return rc;
+            std::swap(cur, nxt);
+        }
+    }
+    if ((rc = counted(h, 2, [&] {
+             return mpm::launch_loss(d, P, cur, h->target, id_cur, h->d_inst_off, h->Minst, h->mom,
+                                     h->loss_acc, h->st_loss, st);
+         })))
+        return rc;
+    h->cur = cur;
+    h->id_cur = id_cur;
+    return MPM_OK;
+}
+
+// --- the backward pass: from h->dloss to gphi_d / gmag_d / gfield_d ---
+int backward_pass(mpm_handle* h, cudaStream_t st) {
+    const int d = h->dim;
+    const Params& P = h->P;
+    const long long S = (long long)h->ncomp * h->np;
+    const long long G = h->total_nodes;
+    const bool fuse = h->fuse;
+    int rc;
+    MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    MPM_CUDA(h, cudaMemsetAsync(h->gphi_d, 0, sizeof(float) * h->Nd, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->gmag_d, 0, sizeof(float) * d * h->Nd, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->gfield_d, 0, sizeof(float) * h->n_inst * h->T * d, st));
+    if (fuse) MPM_CUDA(h, cudaMemsetAsync(h->Vbar3, 0, sizeof(float4) * 3 * G, st));
+    else MPM_CUDA(h, cudaMemsetAsync(h->Vbar, 0, sizeof(float4) * G, st));
+    auto vb3 = [&](int i) { return h->Vbar3 + G * (((i % 3) + 3) % 3); };
+    float* adj = h->adj;
+    float* adj_next = h->adj2;
+    for (int seg = h->n_seg - 1; seg >= 0; --seg) {
+        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T), Ks = s1 - s0;
+        const int* id_seg = h->ck_id + h->np * seg;
+        auto state = [&](int k) { return h->seg_state + S * k; };
+        auto gacc = [&](int k) { return h->seg_acc + G * k; };
+        auto gV = [&](int k) { return h->seg_V + G * k; };
+        MPM_CUDA(h, cudaMemcpyAsync(state(0), h->ck_state + S * seg, sizeof(float) * S,
+                                    cudaMemcpyDeviceToDevice, st));
+        if ((rc = counted(h, 1, [&] {
+                 return mpm::launch_gather_design(d, P, id_seg, h->d_inst_off, h->d_dbase, h->phi_d,
+                                                  h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st);
+             })))
+            return rc;
+        MPM_CUDA(h, cudaMemsetAsync(h->gphi_cur, 0, sizeof(float) * h->np, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->gmag_cur, 0, sizeof(float) * d * h->np, st));
+        // --- recompute the segment, storing states and accumulators ---
+        MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * G * ((fuse && Ks >= 2) ? 2 : 1), st));
+        StepArgs a = base_args(h);
+        a.s_in = state(0);
+        a.acc = gacc(0);
+        a.n_p2g = s0;
+        if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
+                 return mpm::launch_forward(d, false, true, false, fuse, P, a, h->block, st);
+             })))
+            return rc;
+        for (int k = 0; k < Ks; ++k) {
+            const int n = s0 + k;
+            const bool p2g = k + 1 < Ks;
+            float4* next_acc = p2g ? gacc(k + 1) : nullptr;
+            if (!fuse && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
+                              return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, st);
+                          })))
+                return rc;
+            a = base_args(h);
+            a.s_in = state(k);
+            a.s_out = state(k + 1);
+            a.acc = next_acc;
+            a.n_g2p = n;
+            a.n_p2g = n + 1;
+            if (fuse) {
+                a.accG = gacc(k);
+                a.zero4 = k + 2 < Ks ? gacc(k + 2) : nullptr;
+                a.zero_n = G;
+            } else {
+                a.V = gV(k);
+            }
+            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
+                     return mpm::launch_forward(d, true, p2g, true, fuse, P, a, h->block, st);
+                 })))
+                return rc;
+        }
+        // --- adjoint of the state at the segment end ---
+        if (s1 == h->T) {
+            if ((rc = counted(h, 1, [&] {
+                     return mpm::launch_seed(d, P, state(Ks), h->target, id_seg, h->d_inst_off, h->phi_cur,
+                                             h->Minst, h->mom, h->dloss, adj, h->gphi_cur, st);
+                 })))
+                return rc;
+        } else {
+            if ((rc = counted(h, 1, [&] {
+                     return mpm::launch_unpermute(h->ncomp, P, adj_next, adj, h->ck_perm + h->np * (seg + 1), st);
+                 })))
+                return rc;
+        }
+        // G2P^T of the last substep of the segment
+        a = base_args(h);
+        a.s_in = state(Ks);
+        a.s_aux = state(Ks - 1);
+        a.adj = adj;
+        a.mom = h->mom;
+        a.n_p2g = s1;
+        if (fuse) {
+            a.accG = gacc(Ks - 1);
+            a.Vbar = vb3(s1 - 1);
+            a.zero4 = vb3(s1 + 1);
+            a.zero_n = G;
+        } else {
+            a.V = gV(Ks - 1);
+            a.Vbar = h->Vbar;
+        }
+        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kLastG2PT), st, [&] {
+                 return mpm::launch_adjoint(d, false, true, fuse, P, a, h->block, st);
+             })))
+            return rc;
+        for (int k = Ks - 1; k >= 1; --k) {
+            const int n = s0 + k;
+            if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
+                              return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, st);
+                          })))
+                return rc;
+            a = base_args(h);
+            a.s_in = state(k);
+            a.s_aux = state(k - 1);
+            a.adj = adj;
+            a.mom = h->mom;
+            a.n_p2g = n;
+            if (fuse) {
+                a.accP = gacc(k);
+                a.VbarIn = vb3(n);
+                a.accG = gacc(k - 1);
+                a.Vbar = vb3(n - 1);
+                a.zero4 = vb3(n + 1);
+                a.zero_n = G;
+            } else {
+                a.V = gV(k - 1);
+                a.Vbar = h->Vbar;
+                a.gadj = h->gadj;
+            }
+            if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
+                     return mpm::launch_adjoint(d, true, true, fuse, P, a, h->block, st);
+                 })))
+                return rc;
+        }
+        if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
+                          return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, st);
+                      })))
+            return rc;
+        a = base_args(h);
+        a.s_in = state(0);
+        a.adj = adj;
+        a.mom = h->mom;
+        a.n_p2g = s0;
+        if (fuse) {
+            a.accP = gacc(0);
+            a.VbarIn = vb3(s0);
+            a.zero4 = vb3(s0 + 2);
+            a.zero_n = G;
+        } else {
+            a.gadj = h->gadj;
+        }
+        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFirstP2GT), st, [&] {
+                 return mpm::launch_adjoint(d, true, false, fuse, P, a, h->block, st);
+             })))
+            return rc;
+        if ((rc = counted(h, 1, [&] {
+                 return mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase,
+                                                        h->gphi_cur, h->gmag_cur, h->Nd, h->gphi_d,
+                                                        h->gmag_d, st);
+             })))
+            return rc;
+        std::swap(adj, adj_next);
+    }
+    return MPM_OK;
+}
+
+// Run pass 0 (forward) or 1 (backward) on `st`: directly, or by replaying
+// its CUDA graph (captured on an internal stream on first use).
+int run_pass(mpm_handle* h, int pass, cudaStream_t st) {
+    auto body = [&](cudaStream_t s) { return pass == 0 ? forward_pass(h, s) : backward_pass(h, s); };
+    if (!h->graphs) return body(st);
+    if (!h->exec[pass]) {
+        long long launches_before = h->launches;
+        MPM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
+        h->capture_pass = pass;
+        int rc = body(h->cap_stream);
+        h->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (rc != MPM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(h, MPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->exec[pass], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->exec[pass] = nullptr;
+            return fail(h, MPM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        h->graph_launches[pass] = h->launches - launches_before;
+        h->launches = launches_before;
+    }
+    MPM_CUDA(h, cudaGraphLaunch(h->exec[pass], st));
+    h->launches += h->graph_launches[pass];
+    h->ran_graph[pass] = true;
+    return MPM_OK;
+}
+
+int finish(mpm_handle* h, int pass, cudaStream_t st) {
+    int rc = check_device_flags(h, st);
+    if (h->ran_graph[pass]) {
+        h->ran_graph[pass] = false;
+        int r2 = collect_graph_timing(h, pass);
+        if (rc == MPM_OK) rc = r2;
+    }
+    return rc;
+}
+
 int forward_impl(mpm_handle* h, const float* x0, const float* v0, const float* phi,
                  const float* mag, const float* field, const float* target, float* x_out,
                  float* loss_out, cudaStream_t st) {
@@ -431,85 +809,25 @@ int forward_impl(mpm_handle* h, const float* x0, const float* v0, const float* p
     if (h->N > 0 && P.loss_kind == 0 && !target) return fail(h, MPM_ERR_ARG, "target is required for loss_kind 0");
     h->forward_done = false;
     int rc;
+    // stage the inputs into library-owned buffers (the passes read only those)
+    if ((rc = dcopy(h, h->st_x0, x0, sizeof(float) * d * h->N, st))) return rc;
+    if (v0) {
+        if ((rc = dcopy(h, h->st_v0, v0, sizeof(float) * d * h->N, st))) return rc;
+    } else {
+        MPM_CUDA(h, cudaMemsetAsync(h->st_v0, 0, sizeof(float) * d * h->N, st));
+    }
     if ((rc = dcopy(h, h->phi_d, phi, sizeof(float) * h->Nd, st))) return rc;
     if ((rc = dcopy(h, h->mag_d, mag, sizeof(float) * d * h->Nd, st))) return rc;
     if ((rc = dcopy(h, h->field, field, sizeof(float) * h->n_inst * h->T * d, st))) return rc;
     if (target && (rc = dcopy(h, h->target, target, sizeof(float) * d * h->N, st))) return rc;
-    MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
-    MPM_CUDA(h, cudaMemsetAsync(h->mom, 0, sizeof(float) * h->T * h->n_inst, st));
-    MPM_CUDA(h, cudaMemsetAsync(h->Minst, 0, sizeof(float) * h->n_inst, st));
-    MPM_CUDA(h, cudaMemsetAsync(h->loss_acc, 0, sizeof(float) * h->n_inst, st));
-    MPM_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(float4) * h->total_nodes, st));
-    const long long S = (long long)h->ncomp * h->np;
-
-    float* cur = h->stA;
-    float* nxt = h->stB;
-    int* id_cur = h->idA;
-    int* id_nxt = h->idB;
-    h->launches++;
-    MPM_CUDA(h, mpm::launch_init_state(d, P, x0, v0, cur, id_cur, st));
-    for (int seg = 0; seg < h->n_seg; ++seg) {
-        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T);
-        // cell sort and reorder of the full state
-        h->launches += 4;
-        MPM_CUDA(h, mpm::launch_sort(d, P, cur, h->np, h->d_inst_off, h->sb, h->perm, h->d_err, st));
-        h->launches++;
-        MPM_CUDA(h, mpm::launch_reorder(h->ncomp, P, cur, nxt, h->perm, id_cur, id_nxt, st));
-        std::swap(cur, nxt);
-        std::swap(id_cur, id_nxt);
-        h->launches++;
-        MPM_CUDA(h, mpm::launch_gather_design(d, P, id_cur, h->d_inst_off, h->d_dbase, h->phi_d,
-                                              h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st));
-        MPM_CUDA(h, cudaMemcpyAsync(h->ck_state + S * seg, cur, sizeof(float) * S,
-                                    cudaMemcpyDeviceToDevice, st));
-        MPM_CUDA(h, cudaMemcpyAsync(h->ck_id + h->np * seg, id_cur, sizeof(int) * h->np,
-                                    cudaMemcpyDeviceToDevice, st));
-        MPM_CUDA(h, cudaMemcpyAsync(h->ck_perm + h->np * seg, h->perm, sizeof(int) * h->np,
-                                    cudaMemcpyDeviceToDevice, st));
-        StepArgs a = base_args(h);
-        a.mom = h->mom;
-        if (seg == 0) {
-            h->launches++;
-            MPM_CUDA(h, mpm::launch_instance_mass(P, h->phi_cur, h->d_inst_off, h->Minst, st));
-            a.s_in = cur;
-            a.acc = h->acc;
-            a.n_p2g = 0;
-            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
-                     return mpm::launch_forward(d, false, true, false, P, a, h->block, st);
-                 })))
-                return rc;
-        }
-        for (int n = s0; n < s1; ++n) {
-            if ((rc = timed(h, kGrid, 48.0 * h->total_nodes, st, [&] {
-                     return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, st);
-                 })))
-                return rc;
-            const bool p2g = n + 1 < h->T;
-            const bool all = n + 1 == s1;
-            a.s_in = cur;
-            a.s_out = nxt;
-            a.V = h->V;
-            a.acc = h->acc;
-            a.n_g2p = n;
-            a.n_p2g = n + 1;
-            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, all ? kFusedStore : kFused), st, [&] {
-                     return mpm::launch_forward(d, true, p2g, all, P, a, h->block, st);
-                 })))
-                return rc;
-            std::swap(cur, nxt);
-        }
-    }
-    h->launches++;
-    MPM_CUDA(h, mpm::launch_loss(d, P, cur, h->target, id_cur, h->d_inst_off, h->Minst, h->mom,
-                                 h->loss_acc, loss_out, st));
+    if ((rc = run_pass(h, 0, st))) return rc;
+    if ((rc = dcopy(h, loss_out, h->st_loss, sizeof(float) * h->n_inst, st))) return rc;
     if (x_out) {
         h->launches++;
-        MPM_CUDA(h, mpm::launch_to_input_order(d, P, cur, 0, id_cur, x_out, st));
+        MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, x_out, st));
     }
-    rc = check_device_flags(h, st);
+    rc = finish(h, 0, st);
     if (rc != MPM_OK) return rc;
-    h->cur = cur;
-    h->id_cur = id_cur;
     h->forward_done = true;
     return MPM_OK;
 }
@@ -519,127 +837,14 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
     if (!h->forward_done) return fail(h, MPM_ERR_STATE, "mpm_backward needs a successful mpm_forward first");
     if (!dloss) return fail(h, MPM_ERR_ARG, "dloss is NULL");
     const int d = h->dim;
-    const Params& P = h->P;
-    const long long S = (long long)h->ncomp * h->np;
     int rc;
     if ((rc = dcopy(h, h->dloss, dloss, sizeof(float) * h->n_inst, st))) return rc;
-    MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
-    MPM_CUDA(h, cudaMemsetAsync(h->gphi_d, 0, sizeof(float) * h->Nd, st));
-    MPM_CUDA(h, cudaMemsetAsync(h->gmag_d, 0, sizeof(float) * d * h->Nd, st));
-    MPM_CUDA(h, cudaMemsetAsync(h->gfield_d, 0, sizeof(float) * h->n_inst * h->T * d, st));
-    MPM_CUDA(h, cudaMemsetAsync(h->Vbar, 0, sizeof(float4) * h->total_nodes, st));
-    float* adj = h->adj;
-    float* adj_next = h->adj2;
-    for (int seg = h->n_seg - 1; seg >= 0; --seg) {
-        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T), Ks = s1 - s0;
-        const int* id_seg = h->ck_id + h->np * seg;
-        auto state = [&](int k) { return h->seg_state + S * k; };
-        auto gacc = [&](int k) { return h->seg_acc + h->total_nodes * k; };
-        auto gV = [&](int k) { return h->seg_V + h->total_nodes * k; };
-        MPM_CUDA(h, cudaMemcpyAsync(state(0), h->ck_state + S * seg, sizeof(float) * S,
-                                    cudaMemcpyDeviceToDevice, st));
-        h->launches++;
-        MPM_CUDA(h, mpm::launch_gather_design(d, P, id_seg, h->d_inst_off, h->d_dbase, h->phi_d,
-                                              h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st));
-        MPM_CUDA(h, cudaMemsetAsync(h->gphi_cur, 0, sizeof(float) * h->np, st));
-        MPM_CUDA(h, cudaMemsetAsync(h->gmag_cur, 0, sizeof(float) * d * h->np, st));
-        // --- recompute the segment, storing states and grids ---
-        MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * h->total_nodes, st));
-        StepArgs a = base_args(h);
-        a.s_in = state(0);
-        a.acc = gacc(0);
-        a.n_p2g = s0;
-        if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
-                 return mpm::launch_forward(d, false, true, false, P, a, h->block, st);
-             })))
-            return rc;
-        for (int k = 0; k < Ks; ++k) {
-            const int n = s0 + k;
-            float4* next_acc = k + 1 < Ks ? gacc(k + 1) : nullptr;
-            if ((rc = timed(h, kGrid, 48.0 * h->total_nodes, st, [&] {
-                     return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, st);
-                 })))
-                return rc;
-            a = base_args(h);
-            a.s_in = state(k);
-            a.s_out = state(k + 1);
-            a.V = gV(k);
-            a.acc = next_acc;
-            a.n_g2p = n;
-            a.n_p2g = n + 1;
-            const bool p2g = k + 1 < Ks;
-            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
-                     return mpm::launch_forward(d, true, p2g, true, P, a, h->block, st);
-                 })))
-                return rc;
-        }
-        // --- adjoint of the state at the segment end ---
-        if (s1 == h->T) {
-            h->launches++;
-            MPM_CUDA(h, mpm::launch_seed(d, P, state(Ks), h->target, id_seg, h->d_inst_off, h->phi_cur,
-                                         h->Minst, h->mom, h->dloss, adj, h->gphi_cur, st));
-        } else {
-            h->launches++;
-            MPM_CUDA(h, mpm::launch_unpermute(h->ncomp, P, adj_next, adj, h->ck_perm + h->np * (seg + 1), st));
-        }
-        // G2P^T of the last substep of the segment
-        a = base_args(h);
-        a.s_in = state(Ks);
-        a.s_aux = state(Ks - 1);
-        a.V = gV(Ks - 1);
-        a.Vbar = h->Vbar;
-        a.adj = adj;
-        a.mom = h->mom;
-        a.n_p2g = s1;
-        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kLastG2PT), st, [&] {
-                 return mpm::launch_adjoint(d, false, true, P, a, h->block, st);
-             })))
-            return rc;
-        for (int k = Ks - 1; k >= 1; --k) {
-            const int n = s0 + k;
-            if ((rc = timed(h, kGridAdj, 64.0 * h->total_nodes, st, [&] {
-                     return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, st);
-                 })))
-                return rc;
-            a = base_args(h);
-            a.s_in = state(k);
-            a.s_aux = state(k - 1);
-            a.V = gV(k - 1);
-            a.Vbar = h->Vbar;
-            a.gadj = h->gadj;
-            a.adj = adj;
-            a.mom = h->mom;
-            a.n_p2g = n;
-            if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
-                     return mpm::launch_adjoint(d, true, true, P, a, h->block, st);
-                 })))
-                return rc;
-        }
-        if ((rc = timed(h, kGridAdj, 64.0 * h->total_nodes, st, [&] {
-                 return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, st);
-             })))
-            return rc;
-        a = base_args(h);
-        a.s_in = state(0);
-        a.gadj = h->gadj;
-        a.adj = adj;
-        a.mom = h->mom;
-        a.n_p2g = s0;
-        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFirstP2GT), st, [&] {
-                 return mpm::launch_adjoint(d, true, false, P, a, h->block, st);
-             })))
-            return rc;
-        h->launches++;
-        MPM_CUDA(h, mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase,
-                                                    h->gphi_cur, h->gmag_cur, h->Nd, h->gphi_d,
-                                                    h->gmag_d, st));
-        std::swap(adj, adj_next);
-    }
+    if ((rc = run_pass(h, 1, st))) return rc;
     if (g_phi && (rc = dcopy(h, g_phi, h->gphi_d, sizeof(float) * h->Nd, st))) return rc;
     if (g_mag && (rc = dcopy(h, g_mag, h->gmag_d, sizeof(float) * d * h->Nd, st))) return rc;
     if (g_field && (rc = dcopy(h, g_field, h->gfield_d, sizeof(float) * h->n_inst * h->T * d, st)))
         return rc;
-    return check_device_flags(h, st);
+    return finish(h, 1, st);
 }
 
 }  // namespace
@@ -800,11 +1005,24 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
     switch (key) {
         case MPM_OPT_TIMING:
             if (value < 0) return fail(h, MPM_ERR_ARG, "timing stride must be >= 0");
+            if (h->timing_stride != (int)value) drop_graphs(h);
             h->timing_stride = (int)value;
+            for (int c = 0; c < kNumClasses; ++c) h->class_launch[c] = 0;
             return MPM_OK;
         case MPM_OPT_BLOCK:
             if (value < 32 || value > 256 || value % 32) return fail(h, MPM_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
+            if (h->block != (int)value) drop_graphs(h);
             h->block = (int)value;
+            return MPM_OK;
+        case MPM_OPT_FUSE_GRID:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "fuse_grid must be 0 or 1");
+            if (h->fuse != (value == 1)) drop_graphs(h);
+            h->fuse = value == 1;
+            return MPM_OK;
+        case MPM_OPT_GRAPHS:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "graphs must be 0 or 1");
+            if (value == 0) drop_graphs(h);
+            h->graphs = value == 1;
             return MPM_OK;
         default:
             return fail(h, MPM_ERR_ARG, "unknown option");

@@ -39,7 +39,7 @@ class Simulator:
     cfg: a ``workloads.MpmConfig`` (or any object with the same fields).
     """
 
-    def __init__(self, cfg, block: int | None = None):
+    def __init__(self, cfg, block: int | None = None, options: dict | None = None):
         self.lib = B.load()
         self.cfg = cfg
         self.d = int(cfg.dim)
@@ -77,6 +77,8 @@ class Simulator:
         self.generation = 0
         if block is not None:
             self.set_option(B.MPM_OPT_BLOCK, block)
+        for key, value in (options or {}).items():
+            self.set_option(key, value)
 
     # -- lifetime -------------------------------------------------------------
     def close(self):

@@ -30,8 +30,8 @@ def _t(a):
     return None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def run_gpu(w, backward=True, block=None):
-    sim = Simulator(w.cfg, block=block)
+def run_gpu(w, backward=True, block=None, options=None):
+    sim = Simulator(w.cfg, block=block, options=options)
     loss, x = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), target=_t(w.target),
                           v0=_t(w.v0), want_x=True)
     xs, v, C, F = sim.read_state()
@@ -308,3 +308,33 @@ def test_block_size_does_not_change_results(block):
     g = run_gpu(w, block=block)
     assert_state(g, of, w)
     assert_grads(g, ob, w)
+
+
+@pytest.mark.parametrize("fuse,graphs", [(1, 1), (1, 0), (0, 1), (0, 0)])
+@pytest.mark.parametrize("key", ["walker2d_128_s0.5_300", "walker3d_48_s0.25_60"])
+def test_execution_modes(key, fuse, graphs):
+    """Grid operation fused into the particle kernels or not, passes replayed
+    as CUDA graphs or launched directly: same results, twice in a row."""
+    w, of, ob = _oracle(key)
+    sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs}
+    for _ in range(2):
+        g = run_gpu(w, options=sim_opts)
+        assert_state(g, of, w)
+        assert_grads(g, ob, w)
+
+
+def test_graph_replay_with_new_inputs():
+    """A replayed graph reads the new call's inputs, not the captured ones."""
+    import oracle
+    w1 = W.walker_2d(seed=2, n_steps=120, scale=0.4, checkpoint_every=50)
+    w2 = W.walker_2d(seed=2, n_steps=120, scale=0.4, checkpoint_every=50)
+    w2.phi[:] = np.clip(w2.phi * 0.7 + 0.2, 0.0, 1.0)
+    w2.field[:] *= -1.5
+    sim = Simulator(w1.cfg)
+    for w in (w1, w2, w1):
+        loss, x = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), want_x=True)
+        gp, gm, gf = sim.backward(torch.ones(1, device="cuda"))
+        ob = oracle.backward(w)
+        assert cosine(gp.cpu().numpy(), ob["g_phi"]) >= GRAD_COS
+        assert rel_l2(gf.cpu().numpy(), ob["g_field"]) <= GRAD_REL
+    sim.close()
