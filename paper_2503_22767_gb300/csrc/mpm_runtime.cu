@@ -243,13 +243,16 @@ int timed(mpm_handle* h, int cls, double bytes, cudaStream_t st, F&& launch) {
         ea = ev->a;
         eb = ev->b;
     }
-    if (ea) MPM_CUDA(h, cudaEventRecord(ea, st));
+    // inside a capture an event must be recorded "external" to become an
+    // event-record node of the graph (a plain record only orders the capture)
+    const unsigned rec_flags = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (ea) MPM_CUDA(h, cudaEventRecordWithFlags(ea, st, rec_flags));
     cudaError_t e = launch();
     if (e != cudaSuccess) {
         h->err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
         return MPM_ERR_CUDA;
     }
-    if (eb) MPM_CUDA(h, cudaEventRecord(eb, st));
+    if (eb) MPM_CUDA(h, cudaEventRecordWithFlags(eb, st, rec_flags));
     return MPM_OK;
 }
 

@@ -338,3 +338,17 @@ def test_graph_replay_with_new_inputs():
         assert cosine(gp.cpu().numpy(), ob["g_phi"]) >= GRAD_COS
         assert rel_l2(gf.cpu().numpy(), ob["g_field"]) <= GRAD_REL
     sim.close()
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_kernel_timing_counts_launches(graphs):
+    """Sampled CUDA-event timing works with and without graph replay."""
+    w = W.walker_2d(seed=2, n_steps=60, scale=0.3, checkpoint_every=20)
+    sim = Simulator(w.cfg, options={B.MPM_OPT_GRAPHS: graphs, B.MPM_OPT_TIMING: 4})
+    for _ in range(2):
+        sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field))
+        sim.backward(torch.ones(1, device="cuda"))
+    st = sim.stats()
+    sim.close()
+    assert st["timed_launches"][0] > 0 and st["timed_launches"][1] > 0
+    assert all(ms > 0 for ms in st["timed_ms"][:2])
