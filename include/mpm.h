@@ -197,8 +197,11 @@ enum {
     MPM_OPT_FUSE_GRID = 3, /* 1 (default): the particle kernels apply the grid operation
                               (Eq. 16-18) and its reverse per stencil node, one kernel per
                               substep; 0: separate grid kernels */
-    MPM_OPT_GRAPHS = 4  /* 1 (default): each pass is captured once as a CUDA graph on an
+    MPM_OPT_GRAPHS = 4, /* 1 (default): each pass is captured once as a CUDA graph on an
                            internal stream and replayed on cuda_stream; 0: direct launches */
+    MPM_OPT_TILE = 5    /* 1 (default): the per-substep kernels stage the grid box of each
+                           CTA in shared memory and scatter through warp-aggregated
+                           shared-memory tiles; 0: direct global gathers and atomics */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);

@@ -15,90 +15,11 @@
 // Grids are float4 per node ([inst][node]): accumulators (m, mv), velocities
 // (v, 0), adjoints (mbar, mvbar).
 #include "kernels.h"
+#include "particle_io.cuh"
 
 namespace mpm {
 
 namespace {
-
-template <int D>
-struct Layout {
-    // F slot holds E = F - I
-    static constexpr int X = 0, V = D, C = 2 * D, F = 2 * D + D * D, N = 2 * D + 2 * D * D;
-};
-
-template <int D>
-__device__ __forceinline__ float4 pack4(float a, const float (&v)[D]) {
-    return make_float4(a, v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f);
-}
-
-template <int D>
-__device__ __forceinline__ void unpack3(const float4& g, float (&v)[D]) {
-    v[0] = g.x;
-    v[1 % D] = g.y;
-    if (D == 3) v[2 % D] = g.z;
-}
-
-template <int D>
-__device__ __forceinline__ void load_vec(const float* __restrict__ s, int base, long long np, int p,
-                                         float (&v)[D]) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = s[(long long)(base + a) * np + p];
-}
-
-template <int D>
-__device__ __forceinline__ void load_mat(const float* __restrict__ s, int base, long long np, int p,
-                                         float (&M)[D][D]) {
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b) M[a][b] = s[(long long)(base + a * D + b) * np + p];
-}
-
-template <int D>
-__device__ __forceinline__ void store_vec(float* __restrict__ s, int base, long long np, int p,
-                                          const float (&v)[D]) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) s[(long long)(base + a) * np + p] = v[a];
-}
-
-template <int D>
-__device__ __forceinline__ void store_mat(float* __restrict__ s, int base, long long np, int p,
-                                          const float (&M)[D][D]) {
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b) s[(long long)(base + a * D + b) * np + p] = M[a][b];
-}
-
-constexpr int kStencil2 = 9, kStencil3 = 27;
-template <int D>
-constexpr int stencil_size() { return D == 2 ? kStencil2 : kStencil3; }
-
-// ---------------------------------------------------------------------------
-// forward particle kernel
-// ---------------------------------------------------------------------------
-// Clears a.zero4 (grid-stride over the whole launch); fused mode only.
-__device__ __forceinline__ void clear_buffer(const StepArgs& a) {
-    if (a.zero4 == nullptr) return;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.zero_n; i += stride)
-        a.zero4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-// Grid velocity at a stencil node: read V (separate grid kernel) or apply
-// the grid operation (Eq. 16-18) to the node's accumulator (fused).
-template <int D, bool FUSE>
-__device__ __forceinline__ void node_velocity(const float4* __restrict__ grid, const NodeTerm<D>& t,
-                                              const Params& P, float (&gv)[D]) {
-    const float4 g = __ldg(grid + t.node);
-    if (FUSE) {
-        float mv[D];
-        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-        grid_velocity<D>(P, t.c, g.x, mv, gv);
-    } else {
-        unpack3<D>(g, gv);
-    }
-}
 
 template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE>
 __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {

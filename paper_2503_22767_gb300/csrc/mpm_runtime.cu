@@ -112,6 +112,7 @@ struct mpm_handle {
 
     // --- options ---
     bool fuse = true;     // grid operation folded into the particle kernels
+    bool tile = true;     // shared-memory tiled transfers in the per-substep kernels
     bool graphs = true;   // replay the forward / backward passes as CUDA graphs
     bool v0_given = false;
 
@@ -578,8 +579,10 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
                 a.V = h->V;
                 a.acc = h->acc;
             }
+            if (!p2g) a.acc = nullptr;
             if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, all ? kFusedStore : kFused), st, [&] {
-                     return mpm::launch_forward(d, true, p2g, all, fuse, P, a, h->block, st);
+                     return h->tile ? mpm::launch_forward_tiled(d, all, fuse, P, a, h->block, st)
+                                    : mpm::launch_forward(d, true, p2g, all, fuse, P, a, h->block, st);
                  })))
                 return rc;
             std::swap(cur, nxt);
@@ -659,7 +662,8 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
                 a.V = gV(k);
             }
             if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
-                     return mpm::launch_forward(d, true, p2g, true, fuse, P, a, h->block, st);
+                     return h->tile ? mpm::launch_forward_tiled(d, true, fuse, P, a, h->block, st)
+                                    : mpm::launch_forward(d, true, p2g, true, fuse, P, a, h->block, st);
                  })))
                 return rc;
         }
@@ -721,7 +725,8 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
                 a.gadj = h->gadj;
             }
             if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
-                     return mpm::launch_adjoint(d, true, true, fuse, P, a, h->block, st);
+                     return h->tile ? mpm::launch_adjoint_tiled(d, fuse, P, a, h->block, st)
+                                    : mpm::launch_adjoint(d, true, true, fuse, P, a, h->block, st);
                  })))
                 return rc;
         }
@@ -1021,6 +1026,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "fuse_grid must be 0 or 1");
             if (h->fuse != (value == 1)) drop_graphs(h);
             h->fuse = value == 1;
+            return MPM_OK;
+        case MPM_OPT_TILE:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "tile must be 0 or 1");
+            if (h->tile != (value == 1)) drop_graphs(h);
+            h->tile = value == 1;
             return MPM_OK;
         case MPM_OPT_GRAPHS:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "graphs must be 0 or 1");

@@ -310,13 +310,15 @@ def test_block_size_does_not_change_results(block):
     assert_grads(g, ob, w)
 
 
-@pytest.mark.parametrize("fuse,graphs", [(1, 1), (1, 0), (0, 1), (0, 0)])
-@pytest.mark.parametrize("key", ["walker2d_128_s0.5_300", "walker3d_48_s0.25_60"])
-def test_execution_modes(key, fuse, graphs):
+@pytest.mark.parametrize("fuse,graphs,tile", [(1, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 0),
+                                               (1, 1, 0), (0, 1, 0)])
+@pytest.mark.parametrize("key", ["walker2d_128_s0.5_300", "walker3d_48_s0.25_60", "plate3d_32_3tasks_60"])
+def test_execution_modes(key, fuse, graphs, tile):
     """Grid operation fused into the particle kernels or not, passes replayed
-    as CUDA graphs or launched directly: same results, twice in a row."""
+    as CUDA graphs or launched directly, shared-memory tiles or direct global
+    transfers: same results, twice in a row."""
     w, of, ob = _oracle(key)
-    sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs}
+    sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs, B.MPM_OPT_TILE: tile}
     for _ in range(2):
         g = run_gpu(w, options=sim_opts)
         assert_state(g, of, w)
