@@ -194,14 +194,16 @@ enum {
                            events (on the call's stream); 0 (default): off */
     MPM_OPT_BLOCK = 2,  /* threads per block of the particle kernels: a multiple of 32
                            in [32, 256] (default 128) */
-    MPM_OPT_FUSE_GRID = 3, /* 1 (default): the particle kernels apply the grid operation
-                              (Eq. 16-18) and its reverse per stencil node, one kernel per
-                              substep; 0: separate grid kernels */
+    MPM_OPT_FUSE_GRID = 3, /* bit 0: the forward particle kernels apply the grid operation
+                              (Eq. 16-18) per stencil node (one kernel per substep);
+                              bit 1: the adjoint particle kernels apply its reverse per
+                              stencil node; a clear bit keeps the separate grid kernel.
+                              Default 1 (forward fused, adjoint separate) */
     MPM_OPT_GRAPHS = 4, /* 1 (default): each pass is captured once as a CUDA graph on an
                            internal stream and replayed on cuda_stream; 0: direct launches */
-    MPM_OPT_TILE = 5    /* 1 (default): the per-substep kernels stage the grid box of each
-                           CTA in shared memory and scatter through warp-aggregated
-                           shared-memory tiles; 0: direct global gathers and atomics */
+    MPM_OPT_TILE = 5    /* 1: the per-substep kernels stage the grid box of each CTA in
+                           shared memory and scatter through warp-aggregated shared-memory
+                           tiles; 0 (default): direct global gathers and vector atomics */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);

@@ -111,8 +111,9 @@ struct mpm_handle {
     float4* Vbar3 = nullptr;  // fused mode: three rotating G2P^T scatter targets
 
     // --- options ---
-    bool fuse = true;     // grid operation folded into the particle kernels
-    bool tile = true;     // shared-memory tiled transfers in the per-substep kernels
+    bool fuse_fwd = true;   // grid operation folded into the forward particle kernels
+    bool fuse_adj = false;  // grid adjoint folded into the adjoint particle kernels
+    bool tile = false;      // shared-memory tiled transfers in the per-substep kernels
     bool graphs = true;   // replay the forward / backward passes as CUDA graphs
     bool v0_given = false;
 
@@ -504,7 +505,7 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
     const Params& P = h->P;
     const long long S = (long long)h->ncomp * h->np;
     const long long G = h->total_nodes;
-    const bool fuse = h->fuse;
+    const bool fuse = h->fuse_fwd;
     auto acc3 = [&](int i) { return h->acc3 + G * (i % 3); };
     int rc;
     MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
@@ -604,7 +605,8 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
     const Params& P = h->P;
     const long long S = (long long)h->ncomp * h->np;
     const long long G = h->total_nodes;
-    const bool fuse = h->fuse;
+    const bool fuse = h->fuse_adj;      // the adjoint kernels
+    const bool fuse_rec = h->fuse_fwd;  // the recomputation (forward) kernels
     int rc;
     MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     MPM_CUDA(h, cudaMemsetAsync(h->gphi_d, 0, sizeof(float) * h->Nd, st));
@@ -631,20 +633,20 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
         MPM_CUDA(h, cudaMemsetAsync(h->gphi_cur, 0, sizeof(float) * h->np, st));
         MPM_CUDA(h, cudaMemsetAsync(h->gmag_cur, 0, sizeof(float) * d * h->np, st));
         // --- recompute the segment, storing states and accumulators ---
-        MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * G * ((fuse && Ks >= 2) ? 2 : 1), st));
+        MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * G * ((fuse_rec && Ks >= 2) ? 2 : 1), st));
         StepArgs a = base_args(h);
         a.s_in = state(0);
         a.acc = gacc(0);
         a.n_p2g = s0;
         if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
-                 return mpm::launch_forward(d, false, true, false, fuse, P, a, h->block, st);
+                 return mpm::launch_forward(d, false, true, false, fuse_rec, P, a, h->block, st);
              })))
             return rc;
         for (int k = 0; k < Ks; ++k) {
             const int n = s0 + k;
             const bool p2g = k + 1 < Ks;
             float4* next_acc = p2g ? gacc(k + 1) : nullptr;
-            if (!fuse && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
+            if (!fuse_rec && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
                               return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, st);
                           })))
                 return rc;
@@ -654,7 +656,7 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
             a.acc = next_acc;
             a.n_g2p = n;
             a.n_p2g = n + 1;
-            if (fuse) {
+            if (fuse_rec) {
                 a.accG = gacc(k);
                 a.zero4 = k + 2 < Ks ? gacc(k + 2) : nullptr;
                 a.zero_n = G;
@@ -662,8 +664,8 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
                 a.V = gV(k);
             }
             if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
-                     return h->tile ? mpm::launch_forward_tiled(d, true, fuse, P, a, h->block, st)
-                                    : mpm::launch_forward(d, true, p2g, true, fuse, P, a, h->block, st);
+                     return h->tile ? mpm::launch_forward_tiled(d, true, fuse_rec, P, a, h->block, st)
+                                    : mpm::launch_forward(d, true, p2g, true, fuse_rec, P, a, h->block, st);
                  })))
                 return rc;
         }
@@ -1023,9 +1025,10 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             h->block = (int)value;
             return MPM_OK;
         case MPM_OPT_FUSE_GRID:
-            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "fuse_grid must be 0 or 1");
-            if (h->fuse != (value == 1)) drop_graphs(h);
-            h->fuse = value == 1;
+            if (value < 0 || value > 3) return fail(h, MPM_ERR_ARG, "fuse_grid must be in [0, 3]");
+            if (h->fuse_fwd != ((value & 1) != 0) || h->fuse_adj != ((value & 2) != 0)) drop_graphs(h);
+            h->fuse_fwd = (value & 1) != 0;
+            h->fuse_adj = (value & 2) != 0;
             return MPM_OK;
         case MPM_OPT_TILE:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "tile must be 0 or 1");

@@ -310,8 +310,8 @@ def test_block_size_does_not_change_results(block):
     assert_grads(g, ob, w)
 
 
-@pytest.mark.parametrize("fuse,graphs,tile", [(1, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 0),
-                                               (1, 1, 0), (0, 1, 0)])
+@pytest.mark.parametrize("fuse,graphs,tile", [(3, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 0),
+                                               (1, 1, 0), (2, 1, 0), (3, 0, 0)])
 @pytest.mark.parametrize("key", ["walker2d_128_s0.5_300", "walker3d_48_s0.25_60", "plate3d_32_3tasks_60"])
 def test_execution_modes(key, fuse, graphs, tile):
     """Grid operation fused into the particle kernels or not, passes replayed
