@@ -207,6 +207,23 @@ enum {
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);
+/* Current value of an option.  Errors: MPM_ERR_ARG. */
+int mpm_get_option(const mpm_handle* h, int key, long long* value);
+
+/*
+ * Autotuner (not in the paper; a launch-configuration search of this
+ * library).  Times forward + backward passes over the first sample_substeps
+ * substeps (0 = two checkpoint segments) of the inputs staged by the last
+ * mpm_forward, for every combination of block size {64, 128, 256}, grid
+ * fusion {0, 1, 3} and tiles {0, 1}, and keeps the fastest.  With a
+ * non-NULL cache_path, results are read from and written to that JSON file,
+ * keyed by dim, grid_res, particle count (rounded up to a power of 2),
+ * instances and checkpoint interval; a cache hit applies the stored choice
+ * without timing.  The tuning runs overwrite the forward result: call
+ * mpm_forward again before mpm_backward.  Errors: MPM_ERR_STATE (no forward),
+ * MPM_ERR_ARG, MPM_ERR_CUDA.
+ */
+int mpm_autotune(mpm_handle* h, const char* cache_path, int sample_substeps, void* cuda_stream);
 
 /*
  * Counters since creation or the last reset: kernel launches issued by the

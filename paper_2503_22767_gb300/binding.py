@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_CUDA", -3: "MPM_ERR
 #: every function the header declares (checked by the tests)
 EXPORTS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_forward", "mpm_backward",
            "mpm_forward_host", "mpm_backward_host", "mpm_read_state", "mpm_sort_particles",
-           "mpm_set_option", "mpm_get_stats", "mpm_reset_stats", "mpm_substep_noalloc"]
+           "mpm_set_option", "mpm_get_option", "mpm_autotune", "mpm_get_stats", "mpm_reset_stats",
+           "mpm_substep_noalloc"]
 MPM_NOALLOC_MAX_NODES = 262144
 
 
@@ -84,6 +85,8 @@ def load():
             "mpm_read_state": ([H, pf, pf, pf, pf, vp], c_int),
             "mpm_sort_particles": ([H, pf, pi, pi, vp], c_int),
             "mpm_set_option": ([H, c_int, c_longlong], c_int),
+            "mpm_get_option": ([H, c_int, ctypes.POINTER(c_longlong)], c_int),
+            "mpm_autotune": ([H, ctypes.c_char_p, c_int, vp], c_int),
             "mpm_get_stats": ([H, ctypes.POINTER(mpm_stats)], c_int),
             "mpm_reset_stats": ([H], c_int),
             "mpm_substep_noalloc": ([ctypes.POINTER(mpm_config), c_int, pf, pf, pf, pf, pf, vp], c_int),

@@ -126,6 +126,8 @@ struct mpm_handle {
     long long graph_launches[2] = {0, 0};  // kernels inside each captured graph
     bool ran_graph[2] = {false, false};
 
+    int tune_T = 0;  // > 0 while autotuning: passes stop after this many substeps
+
     // --- run state ---
     bool forward_done = false;
     float* cur = nullptr;  // final state of the last forward
@@ -519,10 +521,12 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
     float* nxt = h->stB;
     int* id_cur = h->idA;
     int* id_nxt = h->idB;
+    const int T = h->tune_T > 0 ? std::min(h->T, h->tune_T) : h->T;
+    const int n_seg = (T + h->K - 1) / h->K;
     if ((rc = counted(h, 1, [&] { return mpm::launch_init_state(d, P, h->st_x0, h->st_v0, cur, id_cur, st); })))
         return rc;
-    for (int seg = 0; seg < h->n_seg; ++seg) {
-        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T);
+    for (int seg = 0; seg < n_seg; ++seg) {
+        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T);
         // cell sort and reorder of the full state
         if ((rc = counted(h, 5, [&] {
                  return mpm::launch_sort(d, P, cur, h->np, h->d_inst_off, h->sb, h->perm, h->d_err, st);
@@ -565,7 +569,7 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
                               return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, st);
                           })))
                 return rc;
-            const bool p2g = n + 1 < h->T;
+            const bool p2g = n + 1 < T;
             const bool all = n + 1 == s1;
             a.s_in = cur;
             a.s_out = nxt;
@@ -617,8 +621,10 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
     auto vb3 = [&](int i) { return h->Vbar3 + G * (((i % 3) + 3) % 3); };
     float* adj = h->adj;
     float* adj_next = h->adj2;
-    for (int seg = h->n_seg - 1; seg >= 0; --seg) {
-        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, h->T), Ks = s1 - s0;
+    const int T = h->tune_T > 0 ? std::min(h->T, h->tune_T) : h->T;
+    const int n_seg = (T + h->K - 1) / h->K;
+    for (int seg = n_seg - 1; seg >= 0; --seg) {
+        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T), Ks = s1 - s0;
         const int* id_seg = h->ck_id + h->np * seg;
         auto state = [&](int k) { return h->seg_state + S * k; };
         auto gacc = [&](int k) { return h->seg_acc + G * k; };
@@ -670,7 +676,7 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
                 return rc;
         }
         // --- adjoint of the state at the segment end ---
-        if (s1 == h->T) {
+        if (s1 == T) {
             if ((rc = counted(h, 1, [&] {
                      return mpm::launch_seed(d, P, state(Ks), h->target, id_seg, h->d_inst_off, h->phi_cur,
                                              h->Minst, h->mom, h->dloss, adj, h->gphi_cur, st);
@@ -855,6 +861,145 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
     if (g_field && (rc = dcopy(h, g_field, h->gfield_d, sizeof(float) * h->n_inst * h->T * d, st)))
         return rc;
     return finish(h, 1, st);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time candidate launch configurations, keep the fastest
+// ---------------------------------------------------------------------------
+struct TuneChoice {
+    int block, fuse, tile;
+    double ms;
+};
+
+std::string tune_signature(const mpm_handle* h) {
+    // problem shape the choice depends on; particle counts bucketed by powers of 2
+    long long nb = 1;
+    while (nb < h->N) nb <<= 1;
+    return "d" + std::to_string(h->dim) + "_res" + std::to_string(h->res) + "_n" +
+           std::to_string(nb) + "_inst" + std::to_string(h->n_inst) + "_K" + std::to_string(h->K);
+}
+
+// cache file: one JSON object, one entry per line
+bool cache_lookup(const char* path, const std::string& sig, TuneChoice* out) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    const std::string key = "\"" + sig + "\": ";
+    while (std::fgets(line, sizeof line, f)) {
+        const char* p = std::strstr(line, key.c_str());
+        if (!p) continue;
+        TuneChoice c{};
+        if (std::sscanf(p + key.size(), "{\"block\": %d, \"fuse\": %d, \"tile\": %d, \"ms\": %lf}", &c.block,
+                        &c.fuse, &c.tile, &c.ms) == 4) {
+            *out = c;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char* path, const std::string& sig, const TuneChoice& c) {
+    if (!path) return;
+    std::vector<std::string> lines;
+    if (FILE* f = std::fopen(path, "r")) {
+        char line[512];
+        const std::string key = "\"" + sig + "\": ";
+        while (std::fgets(line, sizeof line, f)) {
+            std::string l(line);
+            if (l.find("\": {\"block\"") == std::string::npos || l.find(key) != std::string::npos) continue;
+            while (!l.empty() && (l.back() == '\n' || l.back() == ',')) l.pop_back();
+            lines.push_back(l);
+        }
+        std::fclose(f);
+    }
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "  \"%s\": {\"block\": %d, \"fuse\": %d, \"tile\": %d, \"ms\": %.4f}",
+                  sig.c_str(), c.block, c.fuse, c.tile, c.ms);
+    lines.push_back(buf);
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "{\n");
+    for (size_t i = 0; i < lines.size(); ++i) std::fprintf(f, "%s%s\n", lines[i].c_str(), i + 1 < lines.size() ? "," : "");
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
+
+void apply_choice(mpm_handle* h, const TuneChoice& c) {
+    drop_graphs(h);
+    h->block = c.block;
+    h->fuse_fwd = (c.fuse & 1) != 0;
+    h->fuse_adj = (c.fuse & 2) != 0;
+    h->tile = c.tile != 0;
+}
+
+int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cudaStream_t st,
+                  TuneChoice* best_out) {
+    if (!h->forward_done) return fail(h, MPM_ERR_STATE, "mpm_autotune needs a successful mpm_forward first");
+    const std::string sig = tune_signature(h);
+    TuneChoice best{};
+    if (cache_lookup(cache_path, sig, &best)) {
+        apply_choice(h, best);
+        *best_out = best;
+        return MPM_OK;
+    }
+    const int sample = sample_substeps > 0 ? sample_substeps : 2 * h->K;
+    const bool saved_graphs = h->graphs;
+    const int saved_timing = h->timing_stride;
+    h->timing_stride = 0;
+    cudaEvent_t e0, e1;
+    MPM_CUDA(h, cudaEventCreate(&e0));
+    MPM_CUDA(h, cudaEventCreate(&e1));
+    best.ms = 1e30;
+    int rc = MPM_OK;
+    for (int block : {64, 128, 256}) {
+        for (int fuse : {0, 1, 3}) {
+            for (int tile : {0, 1}) {
+                TuneChoice c{block, fuse, tile, 0.0};
+                apply_choice(h, c);
+                h->tune_T = sample;
+                // first run captures the graphs; then time the best of 3
+                for (int it = 0; it < 4 && rc == MPM_OK; ++it) {
+                    if (it > 0) rc = cudaEventRecord(e0, st) == cudaSuccess ? MPM_OK : MPM_ERR_CUDA;
+                    if (rc == MPM_OK) rc = run_pass(h, 0, st);
+                    if (rc == MPM_OK) rc = run_pass(h, 1, st);
+                    if (it > 0 && rc == MPM_OK) rc = cudaEventRecord(e1, st) == cudaSuccess ? MPM_OK : MPM_ERR_CUDA;
+                    if (rc == MPM_OK) rc = cudaStreamSynchronize(st) == cudaSuccess ? MPM_OK : MPM_ERR_CUDA;
+                    h->ran_graph[0] = h->ran_graph[1] = false;
+                    if (it > 0 && rc == MPM_OK) {
+                        float ms = 0.0f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        c.ms = it == 1 ? ms : std::min(c.ms, (double)ms);
+                    }
+                }
+                h->tune_T = 0;
+                if (rc != MPM_OK) break;
+                if (c.ms < best.ms) best = c;
+            }
+            if (rc != MPM_OK) break;
+        }
+        if (rc != MPM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tune_T = 0;
+    h->timing_stride = saved_timing;
+    h->graphs = saved_graphs;
+    if (rc != MPM_OK) {
+        drop_graphs(h);
+        if (h->err.empty()) h->err = "autotune run failed";
+        return rc;
+    }
+    apply_choice(h, best);
+    cache_store(cache_path, sig, best);
+    *best_out = best;
+    // the tuning runs overwrote the forward state; a new forward is needed
+    h->forward_done = false;
+    return MPM_OK;
 }
 
 }  // namespace
@@ -1042,6 +1187,29 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             return MPM_OK;
         default:
             return fail(h, MPM_ERR_ARG, "unknown option");
+    }
+}
+
+int mpm_autotune(mpm_handle* h, const char* cache_path, int sample_substeps, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    if (sample_substeps < 0) return fail(h, MPM_ERR_ARG, "sample_substeps must be >= 0");
+    try {
+        TuneChoice c{};
+        return autotune_impl(h, cache_path, sample_substeps, (cudaStream_t)cuda_stream, &c);
+    } catch (...) {
+        return fail(h, MPM_ERR_CUDA, "unexpected exception in mpm_autotune");
+    }
+}
+
+int mpm_get_option(const mpm_handle* h, int key, long long* value) {
+    if (!h || !value) return MPM_ERR_ARG;
+    switch (key) {
+        case MPM_OPT_TIMING: *value = h->timing_stride; return MPM_OK;
+        case MPM_OPT_BLOCK: *value = h->block; return MPM_OK;
+        case MPM_OPT_FUSE_GRID: *value = (h->fuse_fwd ? 1 : 0) | (h->fuse_adj ? 2 : 0); return MPM_OK;
+        case MPM_OPT_GRAPHS: *value = h->graphs ? 1 : 0; return MPM_OK;
+        case MPM_OPT_TILE: *value = h->tile ? 1 : 0; return MPM_OK;
+        default: return MPM_ERR_ARG;
     }
 }
 

@@ -165,6 +165,24 @@ class Simulator:
         self._check(st, "mpm_sort_particles")
         return keys, perm
 
+    def autotune(self, cache_path=None, sample_substeps=0):
+        """Pick block size, grid fusion and tiling by timing them on the inputs
+        of the last forward (see mpm_autotune); returns the chosen options.
+        The forward result is overwritten: run forward again afterwards."""
+        path = cache_path.encode() if cache_path else None
+        st = self.lib.mpm_autotune(self.handle, path, int(sample_substeps), _stream())
+        self._check(st, "mpm_autotune")
+        return self.options()
+
+    def options(self):
+        out = {}
+        for name, key in (("block", B.MPM_OPT_BLOCK), ("fuse_grid", B.MPM_OPT_FUSE_GRID),
+                          ("tile", B.MPM_OPT_TILE), ("graphs", B.MPM_OPT_GRAPHS)):
+            v = ctypes.c_longlong()
+            self._check(self.lib.mpm_get_option(self.handle, key, ctypes.byref(v)), "mpm_get_option")
+            out[name] = v.value
+        return out
+
     def set_option(self, key, value):
         self._check(self.lib.mpm_set_option(self.handle, int(key), int(value)), "mpm_set_option")
 

@@ -354,3 +354,66 @@ def test_kernel_timing_counts_launches(graphs):
     sim.close()
     assert st["timed_launches"][0] > 0 and st["timed_launches"][1] > 0
     assert all(ms > 0 for ms in st["timed_ms"][:2])
+
+
+def test_autotune_picks_and_caches(tmp_path):
+    """The autotuner times the candidate configurations, writes its cache,
+    a second handle reads the cache, and results stay at oracle parity."""
+    import json
+    import oracle
+    w = W.walker_2d(seed=3, n_steps=200, scale=0.4, checkpoint_every=50)
+    cache = str(tmp_path / "tune.json")
+    sim = Simulator(w.cfg)
+    sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field))
+    chosen = sim.autotune(cache_path=cache, sample_substeps=100)
+    entries = json.load(open(cache))
+    assert len(entries) == 1
+    (entry,) = entries.values()
+    assert entry["block"] == chosen["block"] and entry["tile"] == chosen["tile"]
+    with pytest.raises(B.MpmError):  # the tuning runs invalidated the forward result
+        sim.backward(torch.ones(1, device="cuda"))
+    loss, x = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), want_x=True)
+    gp, gm, gf = sim.backward(torch.ones(1, device="cuda"))
+    sim.close()
+    of, ob = oracle.forward(w), oracle.backward(w)
+    assert rel_l2(x.cpu().numpy(), of["x"]) <= STATE_TOL
+    assert_grads(dict(g_phi=gp.cpu().numpy(), g_mag=gm.cpu().numpy(), g_field=gf.cpu().numpy()), ob, w)
+    sim2 = Simulator(w.cfg)
+    sim2.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field))
+    assert sim2.autotune(cache_path=cache) == chosen  # cache hit
+    sim2.close()
+
+
+PRECISION_CASES = {
+    "C1 beam2d 64^2, 4,096 p, 200 steps": lambda: W.beam_2d(seed=0, per_axis=4),
+    "C2 walker2d 128^2, 30,000 p, first 400 steps": lambda: W.walker_2d(seed=0, n_steps=400),
+    "C3 plate3d 64^3, 3 x 200,000 p, first 20 steps": lambda: W.plate_3d(seed=0, n_steps=20),
+    "C4 walker3d 128^3, ~1,000,000 p, first 6 steps": lambda: W.walker_3d(seed=0, n_steps=6,
+                                                                              checkpoint_every=3),
+    "C5 batch 8 x walker2d 128^2, first 100 steps": lambda: W.walker_batch_2d(seed=0, n_instances=8,
+                                                                              n_steps=100),
+}
+
+
+@pytest.mark.parametrize("name", list(PRECISION_CASES))
+def test_precision_report(name):
+    """FP32 (GPU) against FP64 (oracle) on the five workload shapes: relative
+    L2 error of positions, velocities, deformation gradients, loss and each
+    gradient block, printed as a table row; the tolerances hold."""
+    import oracle
+    w = PRECISION_CASES[name]()
+    g = run_gpu(w)
+    of = oracle.forward(w)
+    ob = oracle.backward(w, ckpt_every=max(1, w.cfg.n_steps // 4))
+    row = {
+        "x": rel_l2(g["x"], of["x"]), "v": rel_l2(g["v"], of["v"]), "F": rel_l2(g["F"], of["F"]),
+        "loss": rel_l2(g["loss"], of["loss"]),
+        "g_phi": rel_l2(g["g_phi"], ob["g_phi"]), "g_mag": rel_l2(g["g_mag"], ob["g_mag"]),
+        "g_field": rel_l2(g["g_field"], ob["g_field"]),
+        "cos_min": min(cosine(g[k], ob[k]) for k in ("g_phi", "g_mag", "g_field")),
+    }
+    print("PRECISION |", name, "|", " | ".join(f"{k} {v:.2e}" if k != "cos_min" else f"{k} {v:.7f}"
+                                                for k, v in row.items()))
+    assert row["x"] <= STATE_TOL and row["v"] <= STATE_TOL and row["F"] <= STATE_TOL
+    assert row["cos_min"] >= GRAD_COS
+    assert max(row["g_phi"], row["g_mag"], row["g_field"]) <= GRAD_REL
