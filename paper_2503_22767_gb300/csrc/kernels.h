@@ -48,15 +48,16 @@ cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, bool fus
                            const Params& P, const StepArgs& a, int block, cudaStream_t st);
 // adjoint particle kernel: P2G^T of substep n_p2g and/or G2P^T of n_p2g - 1
 // (or, without P2G^T, of substep n_p2g).
-// fuse: grid adjoint from (a.accP, a.VbarIn) and grid velocity from a.accG.
-cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, const Params& P,
+// fuse: grid adjoint from (a.accP, a.VbarIn); fuse_v: grid velocity of the
+// G2P^T substep from a.accG through the grid operation (fuse implies fuse_v).
+cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, bool fuse_v, const Params& P,
                            const StepArgs& a, int block, cudaStream_t st);
 // Shared-memory tiled versions (kernels_tiled.cu): the forward kernel with
 // G2P (and P2G when a.acc is set), the adjoint kernel with P2G^T and G2P^T.
 cudaError_t launch_forward_tiled(int dim, bool write_all, bool fuse, const Params& P,
                                  const StepArgs& a, int block, cudaStream_t st);
-cudaError_t launch_adjoint_tiled(int dim, bool fuse, const Params& P, const StepArgs& a, int block,
-                                 cudaStream_t st);
+cudaError_t launch_adjoint_tiled(int dim, bool fuse, bool fuse_v, const Params& P, const StepArgs& a,
+                                 int block, cudaStream_t st);
 // grid operation on every node of every instance: acc -> V; clears acc
 // (lean) or clears acc_next (store pass).
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,

@@ -191,10 +191,12 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
 //         the adjoint of state m+1, scatters Vbar, writes the partial
 //         adjoint (x, F) of state m.
 // ---------------------------------------------------------------------------
-template <int D, bool P2GT, bool G2PT, bool FUSE>
+// FUSE: P2G^T evaluates the grid adjoint per stencil node from (accP, VbarIn);
+// FUSE_V: G2P^T takes the grid velocity from accG through the grid operation.
+template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V>
 __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
     using L = Layout<D>;
-    if (FUSE) clear_buffer(a);
+    clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
@@ -371,14 +373,14 @@ __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
                 Ct[i][j] = Cb[i][j] + P.dt * fft;
                 Fo[i][j] = ctf;
             }
-        const float4* __restrict__ Vi = (FUSE ? a.accG : a.V) + (long long)inst * P.nodes;
+        const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
         float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
             NodeTerm<D> t;
             node_term<D>(s, k, P, t);
             float gv[D];
-            node_velocity<D, FUSE>(Vi, t, P, gv);
+            node_velocity<D, FUSE_V>(Vi, t, P, gv);
             // Eq. 19-20 reversed: v' = sum w V, C' = kappa sum w V dpos^T
             float vdot = 0.0f, vcd = 0.0f, cd[D];
 #pragma unroll
@@ -612,25 +614,30 @@ cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, bool fus
                 : forward_d<3, false>(g2p, p2g, write_all, P, a, block, st);
 }
 
-template <int D, bool FUSE>
+template <int D, bool FUSE, bool FUSE_V>
 static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepArgs& a, int block,
                              cudaStream_t st) {
-    if (P.n_total == 0 && !(FUSE && a.zero4)) return cudaSuccess;
+    if (P.n_total == 0 && !a.zero4) return cudaSuccess;
     long long threads = P.n_total > 0 ? P.n_total : block;
     dim3 grid(blocks_for(threads, block));
-    if (p2gt && g2pt) k_adjoint<D, true, true, FUSE><<<grid, block, 0, st>>>(P, a);
-    else if (p2gt) k_adjoint<D, true, false, FUSE><<<grid, block, 0, st>>>(P, a);
-    else k_adjoint<D, false, true, FUSE><<<grid, block, 0, st>>>(P, a);
+    if (p2gt && g2pt) k_adjoint<D, true, true, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
+    else if (p2gt) k_adjoint<D, true, false, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
+    else k_adjoint<D, false, true, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, const Params& P,
+template <int D>
+static cudaError_t adjoint_dim(bool p2gt, bool g2pt, bool fuse, bool fuse_v, const Params& P,
+                               const StepArgs& a, int block, cudaStream_t st) {
+    if (fuse) return adjoint_d<D, true, true>(p2gt, g2pt, P, a, block, st);
+    if (fuse_v) return adjoint_d<D, false, true>(p2gt, g2pt, P, a, block, st);
+    return adjoint_d<D, false, false>(p2gt, g2pt, P, a, block, st);
+}
+
+cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, bool fuse_v, const Params& P,
                            const StepArgs& a, int block, cudaStream_t st) {
-    if (dim == 2)
-        return fuse ? adjoint_d<2, true>(p2gt, g2pt, P, a, block, st)
-                    : adjoint_d<2, false>(p2gt, g2pt, P, a, block, st);
-    return fuse ? adjoint_d<3, true>(p2gt, g2pt, P, a, block, st)
-                : adjoint_d<3, false>(p2gt, g2pt, P, a, block, st);
+    return dim == 2 ? adjoint_dim<2>(p2gt, g2pt, fuse, fuse_v, P, a, block, st)
+                    : adjoint_dim<3>(p2gt, g2pt, fuse, fuse_v, P, a, block, st);
 }
 
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,

@@ -231,14 +231,16 @@ __global__ void __launch_bounds__(256) k_forward_tiled(Params P, StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-template <int D, bool FUSE>
+// FUSE: grid adjoint staged from (accP, VbarIn); FUSE_V: grid velocity of
+// substep n-1 staged from accG through the grid operation.
+template <int D, bool FUSE, bool FUSE_V>
 __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
     using L = Layout<D>;
     __shared__ float4 tileG[kTileMax];  // grid adjoint of substep n, then V of n-1
     __shared__ float4 tileS[kTileMax];  // Vbar scatter of substep n-1
     __shared__ int red[(2 * D + 2) * 32];
     __shared__ TileBox<D> s_box;
-    if (FUSE) clear_buffer(a);
+    clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
@@ -415,11 +417,11 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
     TileBox<D> box2;
     block_box<D>(s2.base, active, inst, box2, red, &s_box);  // all gathers from tileG are done
     {
-        const float4* src = (FUSE ? a.accG : a.V) + (long long)box2.inst * P.nodes;
+        const float4* src = (FUSE_V ? a.accG : a.V) + (long long)box2.inst * P.nodes;
         for (int t = threadIdx.x; t < box2.n; t += blockDim.x) {
             int c[D];
             box_coords<D>(box2, t, c);
-            tileG[t] = stage_velocity<D, FUSE>(src, c, P);
+            tileG[t] = stage_velocity<D, FUSE_V>(src, c, P);
         }
     }
     __syncthreads();
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
     }
     const int lane = threadIdx.x & 31;
     const Segments sg = make_segments(active && box2.use ? box_index<D>(box2, s2.base) : -1 - lane);
-    const float4* direct = (FUSE ? a.accG : a.V) + (long long)(active ? inst : 0) * P.nodes;
+    const float4* direct = (FUSE_V ? a.accG : a.V) + (long long)(active ? inst : 0) * P.nodes;
     float4* __restrict__ Vbi = a.Vbar + (long long)(active ? inst : 0) * P.nodes;
     float* tS = reinterpret_cast<float*>(tileS);
 #pragma unroll
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
         if (active) {
             node_term<D>(s2, k, P, t);
             float gv[D];
-            unpack3<D>(gather_node<D, FUSE>(box2, tileG, direct, t, P), gv);
+            unpack3<D>(gather_node<D, FUSE_V>(box2, tileG, direct, t, P), gv);
             float vdot = 0.0f, vcd = 0.0f, cd[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
@@ -508,12 +510,20 @@ cudaError_t forward_tiled_d(bool all, const Params& P, const StepArgs& a, int bl
     return cudaGetLastError();
 }
 
-template <int D, bool FUSE>
+template <int D, bool FUSE, bool FUSE_V>
 cudaError_t adjoint_tiled_d(const Params& P, const StepArgs& a, int block, cudaStream_t st) {
-    if (P.n_total == 0 && !(FUSE && a.zero4)) return cudaSuccess;
+    if (P.n_total == 0 && !a.zero4) return cudaSuccess;
     dim3 grid(blocks_for(P.n_total > 0 ? P.n_total : block, block));
-    k_adjoint_tiled<D, FUSE><<<grid, block, 0, st>>>(P, a);
+    k_adjoint_tiled<D, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
     return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t adjoint_tiled_dim(bool fuse, bool fuse_v, const Params& P, const StepArgs& a, int block,
+                              cudaStream_t st) {
+    if (fuse) return adjoint_tiled_d<D, true, true>(P, a, block, st);
+    if (fuse_v) return adjoint_tiled_d<D, false, true>(P, a, block, st);
+    return adjoint_tiled_d<D, false, false>(P, a, block, st);
 }
 
 }  // namespace
@@ -527,11 +537,10 @@ cudaError_t launch_forward_tiled(int dim, bool write_all, bool fuse, const Param
                 : forward_tiled_d<3, false>(write_all, P, a, block, st);
 }
 
-cudaError_t launch_adjoint_tiled(int dim, bool fuse, const Params& P, const StepArgs& a, int block,
-                                 cudaStream_t st) {
-    if (dim == 2)
-        return fuse ? adjoint_tiled_d<2, true>(P, a, block, st) : adjoint_tiled_d<2, false>(P, a, block, st);
-    return fuse ? adjoint_tiled_d<3, true>(P, a, block, st) : adjoint_tiled_d<3, false>(P, a, block, st);
+cudaError_t launch_adjoint_tiled(int dim, bool fuse, bool fuse_v, const Params& P, const StepArgs& a,
+                                 int block, cudaStream_t st) {
+    return dim == 2 ? adjoint_tiled_dim<2>(fuse, fuse_v, P, a, block, st)
+                    : adjoint_tiled_dim<3>(fuse, fuse_v, P, a, block, st);
 }
 
 }  // namespace mpm

@@ -611,6 +611,9 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
     const long long G = h->total_nodes;
     const bool fuse = h->fuse_adj;      // the adjoint kernels
     const bool fuse_rec = h->fuse_fwd;  // the recomputation (forward) kernels
+    // G2P^T needs the grid velocity: stored by the grid kernel, or (fused
+    // recomputation) recovered from the stored accumulator
+    const bool fuse_v = fuse || fuse_rec;
     int rc;
     MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     MPM_CUDA(h, cudaMemsetAsync(h->gphi_d, 0, sizeof(float) * h->Nd, st));
@@ -696,16 +699,16 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
         a.mom = h->mom;
         a.n_p2g = s1;
         if (fuse) {
-            a.accG = gacc(Ks - 1);
             a.Vbar = vb3(s1 - 1);
             a.zero4 = vb3(s1 + 1);
             a.zero_n = G;
         } else {
-            a.V = gV(Ks - 1);
             a.Vbar = h->Vbar;
         }
+        if (fuse_v) a.accG = gacc(Ks - 1);
+        else a.V = gV(Ks - 1);
         if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kLastG2PT), st, [&] {
-                 return mpm::launch_adjoint(d, false, true, fuse, P, a, h->block, st);
+                 return mpm::launch_adjoint(d, false, true, fuse, fuse_v, P, a, h->block, st);
              })))
             return rc;
         for (int k = Ks - 1; k >= 1; --k) {
@@ -723,18 +726,18 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
             if (fuse) {
                 a.accP = gacc(k);
                 a.VbarIn = vb3(n);
-                a.accG = gacc(k - 1);
                 a.Vbar = vb3(n - 1);
                 a.zero4 = vb3(n + 1);
                 a.zero_n = G;
             } else {
-                a.V = gV(k - 1);
                 a.Vbar = h->Vbar;
                 a.gadj = h->gadj;
             }
+            if (fuse_v) a.accG = gacc(k - 1);
+            else a.V = gV(k - 1);
             if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
-                     return h->tile ? mpm::launch_adjoint_tiled(d, fuse, P, a, h->block, st)
-                                    : mpm::launch_adjoint(d, true, true, fuse, P, a, h->block, st);
+                     return h->tile ? mpm::launch_adjoint_tiled(d, fuse, fuse_v, P, a, h->block, st)
+                                    : mpm::launch_adjoint(d, true, true, fuse, fuse_v, P, a, h->block, st);
                  })))
                 return rc;
         }
@@ -756,7 +759,7 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
             a.gadj = h->gadj;
         }
         if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFirstP2GT), st, [&] {
-                 return mpm::launch_adjoint(d, true, false, fuse, P, a, h->block, st);
+                 return mpm::launch_adjoint(d, true, false, fuse, fuse_v, P, a, h->block, st);
              })))
             return rc;
         if ((rc = counted(h, 1, [&] {
