@@ -201,9 +201,12 @@ enum {
                               Default 1 (forward fused, adjoint separate) */
     MPM_OPT_GRAPHS = 4, /* 1 (default): each pass is captured once as a CUDA graph on an
                            internal stream and replayed on cuda_stream; 0: direct launches */
-    MPM_OPT_TILE = 5    /* 1: the per-substep kernels stage the grid box of each CTA in
+    MPM_OPT_TILE = 5,   /* 1: the per-substep kernels stage the grid box of each CTA in
                            shared memory and scatter through warp-aggregated shared-memory
                            tiles; 0 (default): direct global gathers and vector atomics */
+    MPM_OPT_STREAMS = 6 /* 2 (default): the backward pass recomputes checkpoint segment s-1
+                           on a second stream while the adjoint of segment s runs (two
+                           sets of segment buffers); 1: one stream */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);

@@ -119,6 +119,9 @@ struct mpm_handle {
 
     // --- CUDA graphs of the two passes (captured on first use) ---
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;  // recomputation stream of the backward pass
+    cudaEvent_t ev_fork = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr};
+    bool two_streams = true;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     std::vector<TimedLaunch> graph_timing[2];
     bool capturing = false;
@@ -193,6 +196,12 @@ void free_all(mpm_handle* h) {
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
+    if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+    h->aux_stream = nullptr;
+    for (cudaEvent_t* e : {&h->ev_fork, &h->ev_rec[0], &h->ev_rec[1], &h->ev_adj[0], &h->ev_adj[1]}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     for (int c = 0; c < kNumClasses; ++c) {
@@ -428,9 +437,10 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->ck_state, S * h->n_seg);
     ALLOC(h->ck_id, h->np * h->n_seg);
     ALLOC(h->ck_perm, h->np * h->n_seg);
-    ALLOC(h->seg_state, S * (h->K + 1));
-    ALLOC(h->seg_acc, h->total_nodes * h->K);
-    ALLOC(h->seg_V, h->total_nodes * h->K);
+    // two sets of segment buffers: recomputation and adjoint overlap
+    ALLOC(h->seg_state, 2 * S * (h->K + 1));
+    ALLOC(h->seg_acc, 2 * h->total_nodes * h->K);
+    ALLOC(h->seg_V, 2 * h->total_nodes * h->K);
     ALLOC(h->acc, h->total_nodes);
     ALLOC(h->V, h->total_nodes);
     ALLOC(h->Vbar, h->total_nodes);
@@ -439,8 +449,8 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->Vbar3, 3 * h->total_nodes);
     ALLOC(h->adj, S);
     ALLOC(h->adj2, S);
-    ALLOC(h->phi_cur, h->np);
-    ALLOC(h->mag_cur, d * h->np);
+    ALLOC(h->phi_cur, 2 * h->np);
+    ALLOC(h->mag_cur, 2 * d * h->np);
     ALLOC(h->gphi_cur, h->np);
     ALLOC(h->gmag_cur, d * h->np);
     ALLOC(h->phi_d, h->Nd);
@@ -476,6 +486,9 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     MPM_CUDA(h, cudaMemset(h->stA, 0, sizeof(float) * S));
     MPM_CUDA(h, cudaMemset(h->stB, 0, sizeof(float) * S));
     MPM_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    MPM_CUDA(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&h->ev_fork, &h->ev_rec[0], &h->ev_rec[1], &h->ev_adj[0], &h->ev_adj[1]})
+        MPM_CUDA(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return MPM_OK;
 }
 
@@ -604,170 +617,244 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
 }
 
 // --- the backward pass: from h->dloss to gphi_d / gmag_d / gfield_d ---
-int backward_pass(mpm_handle* h, cudaStream_t st) {
+//
+// Per checkpoint segment, in reverse: recompute the segment from its
+// checkpoint (storing every state and grid), then run its adjoint.  The
+// recomputation of segment s-1 does not depend on the adjoint of segment s,
+// so with two streams they overlap: the segment buffers and the
+// current-order design come in two sets, used by segment parity.
+struct SegSet {
+    float* state;   // [K + 1] states
+    float4* acc;    // [K] accumulators
+    float4* V;      // [K] grid velocities
+    float* phi;     // current-order design of the segment
+    float* mag;
+};
+
+SegSet seg_set(mpm_handle* h, int b) {
+    const long long S = (long long)h->ncomp * h->np;
+    const long long G = h->total_nodes;
+    SegSet ss;
+    ss.state = h->seg_state + (long long)b * S * (h->K + 1);
+    ss.acc = h->seg_acc + (long long)b * G * h->K;
+    ss.V = h->seg_V + (long long)b * G * h->K;
+    ss.phi = h->phi_cur + (long long)b * h->np;
+    ss.mag = h->mag_cur + (long long)b * h->dim * h->np;
+    return ss;
+}
+
+int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStream_t st) {
     const int d = h->dim;
     const Params& P = h->P;
     const long long S = (long long)h->ncomp * h->np;
     const long long G = h->total_nodes;
-    const bool fuse = h->fuse_adj;      // the adjoint kernels
-    const bool fuse_rec = h->fuse_fwd;  // the recomputation (forward) kernels
+    const bool fuse_rec = h->fuse_fwd;
+    const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T), Ks = s1 - s0;
+    const int* id_seg = h->ck_id + h->np * seg;
+    auto state = [&](int k) { return ss.state + S * k; };
+    auto gacc = [&](int k) { return ss.acc + G * k; };
+    auto gV = [&](int k) { return ss.V + G * k; };
+    int rc;
+    MPM_CUDA(h, cudaMemcpyAsync(state(0), h->ck_state + S * seg, sizeof(float) * S,
+                                cudaMemcpyDeviceToDevice, st));
+    if ((rc = counted(h, 1, [&] {
+             return mpm::launch_gather_design(d, P, id_seg, h->d_inst_off, h->d_dbase, h->phi_d,
+                                              h->mag_d, h->Nd, ss.phi, ss.mag, st);
+         })))
+        return rc;
+    MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * G * ((fuse_rec && Ks >= 2) ? 2 : 1), st));
+    StepArgs a = base_args(h);
+    a.phi = ss.phi;
+    a.mag = ss.mag;
+    a.s_in = state(0);
+    a.acc = gacc(0);
+    a.n_p2g = s0;
+    if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
+             return mpm::launch_forward(d, false, true, false, fuse_rec, P, a, h->block, st);
+         })))
+        return rc;
+    for (int k = 0; k < Ks; ++k) {
+        const int n = s0 + k;
+        const bool p2g = k + 1 < Ks;
+        float4* next_acc = p2g ? gacc(k + 1) : nullptr;
+        if (!fuse_rec && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
+                          return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, st);
+                      })))
+            return rc;
+        a = base_args(h);
+        a.phi = ss.phi;
+        a.mag = ss.mag;
+        a.s_in = state(k);
+        a.s_out = state(k + 1);
+        a.acc = next_acc;
+        a.n_g2p = n;
+        a.n_p2g = n + 1;
+        if (fuse_rec) {
+            a.accG = gacc(k);
+            a.zero4 = k + 2 < Ks ? gacc(k + 2) : nullptr;
+            a.zero_n = G;
+        } else {
+            a.V = gV(k);
+        }
+        if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
+                 return h->tile ? mpm::launch_forward_tiled(d, true, fuse_rec, P, a, h->block, st)
+                                : mpm::launch_forward(d, true, p2g, true, fuse_rec, P, a, h->block, st);
+             })))
+            return rc;
+    }
+    return MPM_OK;
+}
+
+int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj, float* adj_next,
+                    cudaStream_t st) {
+    const int d = h->dim;
+    const Params& P = h->P;
+    const long long S = (long long)h->ncomp * h->np;
+    const long long G = h->total_nodes;
+    const bool fuse = h->fuse_adj;  // grid adjoint evaluated inside the adjoint kernels
     // G2P^T needs the grid velocity: stored by the grid kernel, or (fused
     // recomputation) recovered from the stored accumulator
-    const bool fuse_v = fuse || fuse_rec;
+    const bool fuse_v = fuse || h->fuse_fwd;
+    const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T), Ks = s1 - s0;
+    const int* id_seg = h->ck_id + h->np * seg;
+    auto state = [&](int k) { return ss.state + S * k; };
+    auto gacc = [&](int k) { return ss.acc + G * k; };
+    auto gV = [&](int k) { return ss.V + G * k; };
+    auto vb3 = [&](int i) { return h->Vbar3 + G * (((i % 3) + 3) % 3); };
+    auto args = [&]() {
+        StepArgs a = base_args(h);
+        a.phi = ss.phi;
+        a.mag = ss.mag;
+        a.adj = adj;
+        a.mom = h->mom;
+        return a;
+    };
+    int rc;
+    MPM_CUDA(h, cudaMemsetAsync(h->gphi_cur, 0, sizeof(float) * h->np, st));
+    MPM_CUDA(h, cudaMemsetAsync(h->gmag_cur, 0, sizeof(float) * d * h->np, st));
+    // --- adjoint of the state at the segment end ---
+    if (s1 == T) {
+        if ((rc = counted(h, 1, [&] {
+                 return mpm::launch_seed(d, P, state(Ks), h->target, id_seg, h->d_inst_off, ss.phi,
+                                         h->Minst, h->mom, h->dloss, adj, h->gphi_cur, st);
+             })))
+            return rc;
+    } else {
+        if ((rc = counted(h, 1, [&] {
+                 return mpm::launch_unpermute(h->ncomp, P, adj_next, adj, h->ck_perm + h->np * (seg + 1), st);
+             })))
+            return rc;
+    }
+    // G2P^T of the last substep of the segment
+    StepArgs a = args();
+    a.s_in = state(Ks);
+    a.s_aux = state(Ks - 1);
+    a.n_p2g = s1;
+    if (fuse) {
+        a.Vbar = vb3(s1 - 1);
+        a.zero4 = vb3(s1 + 1);
+        a.zero_n = G;
+    } else {
+        a.Vbar = h->Vbar;
+    }
+    if (fuse_v) a.accG = gacc(Ks - 1);
+    else a.V = gV(Ks - 1);
+    if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kLastG2PT), st, [&] {
+             return mpm::launch_adjoint(d, false, true, fuse, fuse_v, P, a, h->block, st);
+         })))
+        return rc;
+    for (int k = Ks - 1; k >= 1; --k) {
+        const int n = s0 + k;
+        if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
+                          return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, st);
+                      })))
+            return rc;
+        a = args();
+        a.s_in = state(k);
+        a.s_aux = state(k - 1);
+        a.n_p2g = n;
+        if (fuse) {
+            a.accP = gacc(k);
+            a.VbarIn = vb3(n);
+            a.Vbar = vb3(n - 1);
+            a.zero4 = vb3(n + 1);
+            a.zero_n = G;
+        } else {
+            a.Vbar = h->Vbar;
+            a.gadj = h->gadj;
+        }
+        if (fuse_v) a.accG = gacc(k - 1);
+        else a.V = gV(k - 1);
+        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
+                 return h->tile ? mpm::launch_adjoint_tiled(d, fuse, fuse_v, P, a, h->block, st)
+                                : mpm::launch_adjoint(d, true, true, fuse, fuse_v, P, a, h->block, st);
+             })))
+            return rc;
+    }
+    if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
+                      return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, st);
+                  })))
+        return rc;
+    a = args();
+    a.s_in = state(0);
+    a.n_p2g = s0;
+    if (fuse) {
+        a.accP = gacc(0);
+        a.VbarIn = vb3(s0);
+        a.zero4 = vb3(s0 + 2);
+        a.zero_n = G;
+    } else {
+        a.gadj = h->gadj;
+    }
+    if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFirstP2GT), st, [&] {
+             return mpm::launch_adjoint(d, true, false, fuse, fuse_v, P, a, h->block, st);
+         })))
+        return rc;
+    return counted(h, 1, [&] {
+        return mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase, h->gphi_cur,
+                                               h->gmag_cur, h->Nd, h->gphi_d, h->gmag_d, st);
+    });
+}
+
+int backward_pass(mpm_handle* h, cudaStream_t st) {
+    const int d = h->dim;
+    const long long G = h->total_nodes;
     int rc;
     MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     MPM_CUDA(h, cudaMemsetAsync(h->gphi_d, 0, sizeof(float) * h->Nd, st));
     MPM_CUDA(h, cudaMemsetAsync(h->gmag_d, 0, sizeof(float) * d * h->Nd, st));
     MPM_CUDA(h, cudaMemsetAsync(h->gfield_d, 0, sizeof(float) * h->n_inst * h->T * d, st));
-    if (fuse) MPM_CUDA(h, cudaMemsetAsync(h->Vbar3, 0, sizeof(float4) * 3 * G, st));
+    if (h->fuse_adj) MPM_CUDA(h, cudaMemsetAsync(h->Vbar3, 0, sizeof(float4) * 3 * G, st));
     else MPM_CUDA(h, cudaMemsetAsync(h->Vbar, 0, sizeof(float4) * G, st));
-    auto vb3 = [&](int i) { return h->Vbar3 + G * (((i % 3) + 3) % 3); };
-    float* adj = h->adj;
-    float* adj_next = h->adj2;
     const int T = h->tune_T > 0 ? std::min(h->T, h->tune_T) : h->T;
     const int n_seg = (T + h->K - 1) / h->K;
+    float* adj = h->adj;
+    float* adj_next = h->adj2;
+    if (!h->two_streams || n_seg < 2) {
+        for (int seg = n_seg - 1; seg >= 0; --seg) {
+            const SegSet ss = seg_set(h, 0);
+            if ((rc = recompute_segment(h, seg, T, ss, st))) return rc;
+            if ((rc = adjoint_segment(h, seg, T, ss, adj, adj_next, st))) return rc;
+            std::swap(adj, adj_next);
+        }
+        return MPM_OK;
+    }
+    // recomputation one segment ahead on the second stream
+    cudaStream_t aux = h->aux_stream;
+    MPM_CUDA(h, cudaEventRecord(h->ev_fork, st));
+    MPM_CUDA(h, cudaStreamWaitEvent(aux, h->ev_fork, 0));
+    if ((rc = recompute_segment(h, n_seg - 1, T, seg_set(h, (n_seg - 1) & 1), aux))) return rc;
+    MPM_CUDA(h, cudaEventRecord(h->ev_rec[(n_seg - 1) & 1], aux));
     for (int seg = n_seg - 1; seg >= 0; --seg) {
-        const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T), Ks = s1 - s0;
-        const int* id_seg = h->ck_id + h->np * seg;
-        auto state = [&](int k) { return h->seg_state + S * k; };
-        auto gacc = [&](int k) { return h->seg_acc + G * k; };
-        auto gV = [&](int k) { return h->seg_V + G * k; };
-        MPM_CUDA(h, cudaMemcpyAsync(state(0), h->ck_state + S * seg, sizeof(float) * S,
-                                    cudaMemcpyDeviceToDevice, st));
-        if ((rc = counted(h, 1, [&] {
-                 return mpm::launch_gather_design(d, P, id_seg, h->d_inst_off, h->d_dbase, h->phi_d,
-                                                  h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st);
-             })))
-            return rc;
-        MPM_CUDA(h, cudaMemsetAsync(h->gphi_cur, 0, sizeof(float) * h->np, st));
-        MPM_CUDA(h, cudaMemsetAsync(h->gmag_cur, 0, sizeof(float) * d * h->np, st));
-        // --- recompute the segment, storing states and accumulators ---
-        MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * G * ((fuse_rec && Ks >= 2) ? 2 : 1), st));
-        StepArgs a = base_args(h);
-        a.s_in = state(0);
-        a.acc = gacc(0);
-        a.n_p2g = s0;
-        if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
-                 return mpm::launch_forward(d, false, true, false, fuse_rec, P, a, h->block, st);
-             })))
-            return rc;
-        for (int k = 0; k < Ks; ++k) {
-            const int n = s0 + k;
-            const bool p2g = k + 1 < Ks;
-            float4* next_acc = p2g ? gacc(k + 1) : nullptr;
-            if (!fuse_rec && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
-                              return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, st);
-                          })))
-                return rc;
-            a = base_args(h);
-            a.s_in = state(k);
-            a.s_out = state(k + 1);
-            a.acc = next_acc;
-            a.n_g2p = n;
-            a.n_p2g = n + 1;
-            if (fuse_rec) {
-                a.accG = gacc(k);
-                a.zero4 = k + 2 < Ks ? gacc(k + 2) : nullptr;
-                a.zero_n = G;
-            } else {
-                a.V = gV(k);
-            }
-            if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
-                     return h->tile ? mpm::launch_forward_tiled(d, true, fuse_rec, P, a, h->block, st)
-                                    : mpm::launch_forward(d, true, p2g, true, fuse_rec, P, a, h->block, st);
-                 })))
-                return rc;
+        if (seg >= 1) {
+            // set (seg-1)&1 was last read by the adjoint of segment seg+1
+            if (seg + 1 <= n_seg - 1) MPM_CUDA(h, cudaStreamWaitEvent(aux, h->ev_adj[(seg + 1) & 1], 0));
+            if ((rc = recompute_segment(h, seg - 1, T, seg_set(h, (seg - 1) & 1), aux))) return rc;
+            MPM_CUDA(h, cudaEventRecord(h->ev_rec[(seg - 1) & 1], aux));
         }
-        // --- adjoint of the state at the segment end ---
-        if (s1 == T) {
-            if ((rc = counted(h, 1, [&] {
-                     return mpm::launch_seed(d, P, state(Ks), h->target, id_seg, h->d_inst_off, h->phi_cur,
-                                             h->Minst, h->mom, h->dloss, adj, h->gphi_cur, st);
-                 })))
-                return rc;
-        } else {
-            if ((rc = counted(h, 1, [&] {
-                     return mpm::launch_unpermute(h->ncomp, P, adj_next, adj, h->ck_perm + h->np * (seg + 1), st);
-                 })))
-                return rc;
-        }
-        // G2P^T of the last substep of the segment
-        a = base_args(h);
-        a.s_in = state(Ks);
-        a.s_aux = state(Ks - 1);
-        a.adj = adj;
-        a.mom = h->mom;
-        a.n_p2g = s1;
-        if (fuse) {
-            a.Vbar = vb3(s1 - 1);
-            a.zero4 = vb3(s1 + 1);
-            a.zero_n = G;
-        } else {
-            a.Vbar = h->Vbar;
-        }
-        if (fuse_v) a.accG = gacc(Ks - 1);
-        else a.V = gV(Ks - 1);
-        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kLastG2PT), st, [&] {
-                 return mpm::launch_adjoint(d, false, true, fuse, fuse_v, P, a, h->block, st);
-             })))
-            return rc;
-        for (int k = Ks - 1; k >= 1; --k) {
-            const int n = s0 + k;
-            if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
-                              return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, st);
-                          })))
-                return rc;
-            a = base_args(h);
-            a.s_in = state(k);
-            a.s_aux = state(k - 1);
-            a.adj = adj;
-            a.mom = h->mom;
-            a.n_p2g = n;
-            if (fuse) {
-                a.accP = gacc(k);
-                a.VbarIn = vb3(n);
-                a.Vbar = vb3(n - 1);
-                a.zero4 = vb3(n + 1);
-                a.zero_n = G;
-            } else {
-                a.Vbar = h->Vbar;
-                a.gadj = h->gadj;
-            }
-            if (fuse_v) a.accG = gacc(k - 1);
-            else a.V = gV(k - 1);
-            if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
-                     return h->tile ? mpm::launch_adjoint_tiled(d, fuse, fuse_v, P, a, h->block, st)
-                                    : mpm::launch_adjoint(d, true, true, fuse, fuse_v, P, a, h->block, st);
-                 })))
-                return rc;
-        }
-        if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
-                          return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, st);
-                      })))
-            return rc;
-        a = base_args(h);
-        a.s_in = state(0);
-        a.adj = adj;
-        a.mom = h->mom;
-        a.n_p2g = s0;
-        if (fuse) {
-            a.accP = gacc(0);
-            a.VbarIn = vb3(s0);
-            a.zero4 = vb3(s0 + 2);
-            a.zero_n = G;
-        } else {
-            a.gadj = h->gadj;
-        }
-        if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFirstP2GT), st, [&] {
-                 return mpm::launch_adjoint(d, true, false, fuse, fuse_v, P, a, h->block, st);
-             })))
-            return rc;
-        if ((rc = counted(h, 1, [&] {
-                 return mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase,
-                                                        h->gphi_cur, h->gmag_cur, h->Nd, h->gphi_d,
-                                                        h->gmag_d, st);
-             })))
-            return rc;
+        MPM_CUDA(h, cudaStreamWaitEvent(st, h->ev_rec[seg & 1], 0));
+        if ((rc = adjoint_segment(h, seg, T, seg_set(h, seg & 1), adj, adj_next, st))) return rc;
+        MPM_CUDA(h, cudaEventRecord(h->ev_adj[seg & 1], st));
         std::swap(adj, adj_next);
     }
     return MPM_OK;
@@ -1183,6 +1270,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (h->tile != (value == 1)) drop_graphs(h);
             h->tile = value == 1;
             return MPM_OK;
+        case MPM_OPT_STREAMS:
+            if (value != 1 && value != 2) return fail(h, MPM_ERR_ARG, "streams must be 1 or 2");
+            if (h->two_streams != (value == 2)) drop_graphs(h);
+            h->two_streams = value == 2;
+            return MPM_OK;
         case MPM_OPT_GRAPHS:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "graphs must be 0 or 1");
             if (value == 0) drop_graphs(h);
@@ -1212,6 +1304,7 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_FUSE_GRID: *value = (h->fuse_fwd ? 1 : 0) | (h->fuse_adj ? 2 : 0); return MPM_OK;
         case MPM_OPT_GRAPHS: *value = h->graphs ? 1 : 0; return MPM_OK;
         case MPM_OPT_TILE: *value = h->tile ? 1 : 0; return MPM_OK;
+        case MPM_OPT_STREAMS: *value = h->two_streams ? 2 : 1; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }
