@@ -163,11 +163,13 @@ def run_ours(args):
         tuned = sim.autotune(sample_substeps=min(cfg.n_steps, 200))
         tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
 
+    # timing events are part of the captured graphs: switch them on before the
+    # warm-up so that the warm-up (not the timed region) captures the graphs
+    sim.set_option(1, args.timing_stride)  # time every k-th launch of each kernel class
     for _ in range(args.warmup):
         iteration()
     torch.cuda.synchronize()
     sim.reset_stats()
-    sim.set_option(1, args.timing_stride)  # time every k-th launch of each kernel class
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     if dist:
@@ -231,6 +233,10 @@ def run_ours(args):
     hgm = torch.empty(mag.shape).pin_memory()
     hgf = torch.empty(field.shape).pin_memory()
     e2e_steps = args.e2e_steps if args.e2e_steps else max(1, min(args.steps, 3))
+    # one untimed pass through the host entry points (re-captures the graphs
+    # without timing events)
+    sim.forward_host(hx0, hphi, hmag, hfield, None, None, None, hloss)
+    sim.backward_host(hdl, hgp, hgm, hgf)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):

@@ -204,9 +204,12 @@ enum {
     MPM_OPT_TILE = 5,   /* 1: the per-substep kernels stage the grid box of each CTA in
                            shared memory and scatter through warp-aggregated shared-memory
                            tiles; 0 (default): direct global gathers and vector atomics */
-    MPM_OPT_STREAMS = 6 /* 2 (default): the backward pass recomputes checkpoint segment s-1
-                           on a second stream while the adjoint of segment s runs (two
-                           sets of segment buffers); 1: one stream */
+    MPM_OPT_STREAMS = 6, /* 2 (default): the backward pass recomputes checkpoint segment s-1
+                            on a second stream while the adjoint of segment s runs (two
+                            sets of segment buffers); 1: one stream */
+    MPM_OPT_PDL = 7     /* 1 (default): per-substep kernels use programmatic dependent
+                           launch, so a kernel's CTAs are scheduled while its predecessor
+                           drains; 0: plain stream order */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);

@@ -24,6 +24,8 @@ namespace {
 template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE>
 __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
+    pdl_wait();
+    pdl_trigger();
     if (FUSE) clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
@@ -152,6 +154,8 @@ template <int D>
 __global__ void __launch_bounds__(256) k_grid(Params P, float4* __restrict__ acc,
                                               float4* __restrict__ V, float4* __restrict__ acc_next,
                                               bool clear_acc, long long total) {
+    pdl_wait();
+    pdl_trigger();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     float4 g = acc[i];
@@ -169,6 +173,8 @@ template <int D>
 __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __restrict__ acc,
                                                       float4* __restrict__ Vbar,
                                                       float4* __restrict__ gadj, long long total) {
+    pdl_wait();
+    pdl_trigger();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     float4 g = acc[i];
@@ -196,6 +202,8 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
 template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V>
 __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
     using L = Layout<D>;
+    pdl_wait();
+    pdl_trigger();
     clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
@@ -594,13 +602,13 @@ static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, cons
     long long threads = P.n_total > 0 ? P.n_total : block;
     dim3 grid(blocks_for(threads, block));
     if (g2p && p2g) {
-        if (all) k_forward<D, true, true, true, FUSE><<<grid, block, 0, st>>>(P, a);
-        else k_forward<D, true, true, false, FUSE><<<grid, block, 0, st>>>(P, a);
+        if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, true, true, false, FUSE>, grid, block, st, P, a);
     } else if (g2p) {
-        if (all) k_forward<D, true, false, true, FUSE><<<grid, block, 0, st>>>(P, a);
-        else k_forward<D, true, false, false, FUSE><<<grid, block, 0, st>>>(P, a);
+        if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, true, false, false, FUSE>, grid, block, st, P, a);
     } else {
-        k_forward<D, false, true, false, FUSE><<<grid, block, 0, st>>>(P, a);
+        return launch_chain(P, k_forward<D, false, true, false, FUSE>, grid, block, st, P, a);
     }
     return cudaGetLastError();
 }
@@ -620,10 +628,9 @@ static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepAr
     if (P.n_total == 0 && !a.zero4) return cudaSuccess;
     long long threads = P.n_total > 0 ? P.n_total : block;
     dim3 grid(blocks_for(threads, block));
-    if (p2gt && g2pt) k_adjoint<D, true, true, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
-    else if (p2gt) k_adjoint<D, true, false, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
-    else k_adjoint<D, false, true, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
-    return cudaGetLastError();
+    if (p2gt && g2pt) return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V>, grid, block, st, P, a);
+    if (p2gt) return launch_chain(P, k_adjoint<D, true, false, FUSE, FUSE_V>, grid, block, st, P, a);
+    return launch_chain(P, k_adjoint<D, false, true, FUSE, FUSE_V>, grid, block, st, P, a);
 }
 
 template <int D>
@@ -644,18 +651,16 @@ cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4
                         bool clear_acc, cudaStream_t st) {
     long long total = P.nodes * P.n_inst;
     dim3 grid(blocks_for(total, 256));
-    if (dim == 2) k_grid<2><<<grid, 256, 0, st>>>(P, acc, V, acc_next, clear_acc, total);
-    else k_grid<3><<<grid, 256, 0, st>>>(P, acc, V, acc_next, clear_acc, total);
-    return cudaGetLastError();
+    if (dim == 2) return launch_chain(P, k_grid<2>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc, total);
+    return launch_chain(P, k_grid<3>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc, total);
 }
 
 cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, float4* Vbar,
                                 float4* gadj, cudaStream_t st) {
     long long total = P.nodes * P.n_inst;
     dim3 grid(blocks_for(total, 256));
-    if (dim == 2) k_grid_adjoint<2><<<grid, 256, 0, st>>>(P, acc, Vbar, gadj, total);
-    else k_grid_adjoint<3><<<grid, 256, 0, st>>>(P, acc, Vbar, gadj, total);
-    return cudaGetLastError();
+    if (dim == 2) return launch_chain(P, k_grid_adjoint<2>, grid, dim3(256), st, P, acc, Vbar, gadj, total);
+    return launch_chain(P, k_grid_adjoint<3>, grid, dim3(256), st, P, acc, Vbar, gadj, total);
 }
 
 cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0, float* s,

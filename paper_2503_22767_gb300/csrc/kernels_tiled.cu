@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(256) k_forward_tiled(Params P, StepArgs a) {
     __shared__ float4 tileA[kTileMax];
     __shared__ int red[(2 * D + 2) * 32];
     __shared__ TileBox<D> s_box;
+    pdl_wait();
+    pdl_trigger();
     if (FUSE) clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
@@ -240,6 +242,8 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
     __shared__ float4 tileS[kTileMax];  // Vbar scatter of substep n-1
     __shared__ int red[(2 * D + 2) * 32];
     __shared__ TileBox<D> s_box;
+    pdl_wait();
+    pdl_trigger();
     clear_buffer(a);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
@@ -505,17 +509,15 @@ template <int D, bool FUSE>
 cudaError_t forward_tiled_d(bool all, const Params& P, const StepArgs& a, int block, cudaStream_t st) {
     if (P.n_total == 0 && !(FUSE && a.zero4)) return cudaSuccess;
     dim3 grid(blocks_for(P.n_total > 0 ? P.n_total : block, block));
-    if (all) k_forward_tiled<D, true, FUSE><<<grid, block, 0, st>>>(P, a);
-    else k_forward_tiled<D, false, FUSE><<<grid, block, 0, st>>>(P, a);
-    return cudaGetLastError();
+    if (all) return launch_chain(P, k_forward_tiled<D, true, FUSE>, grid, dim3(block), st, P, a);
+    return launch_chain(P, k_forward_tiled<D, false, FUSE>, grid, dim3(block), st, P, a);
 }
 
 template <int D, bool FUSE, bool FUSE_V>
 cudaError_t adjoint_tiled_d(const Params& P, const StepArgs& a, int block, cudaStream_t st) {
     if (P.n_total == 0 && !a.zero4) return cudaSuccess;
     dim3 grid(blocks_for(P.n_total > 0 ? P.n_total : block, block));
-    k_adjoint_tiled<D, FUSE, FUSE_V><<<grid, block, 0, st>>>(P, a);
-    return cudaGetLastError();
+    return launch_chain(P, k_adjoint_tiled<D, FUSE, FUSE_V>, grid, dim3(block), st, P, a);
 }
 
 template <int D>

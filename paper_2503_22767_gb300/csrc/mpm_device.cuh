@@ -29,7 +29,15 @@ struct Params {
     float dx, inv_dx, dt, kappa;  // kappa = 4/dx^2 (inverse B-spline inertia)
     float p_vol, rho0, G, K, eps, damping, mu;
     float gravity[3];
+    int pdl;  // per-substep kernels launched with programmatic dependent launch
 };
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor drains; it must wait (here,
+// before any global access) until the predecessor's writes are visible.
+// Without a programmatic predecessor both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Index of the instance owning particle p (instance ranges are contiguous
 // and survive the cell sort, whose key starts with the instance).

@@ -423,6 +423,7 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     P.damping = (float)c->damping_c;
     P.mu = (float)c->floor_mu;
     for (int i = 0; i < 3; ++i) P.gravity[i] = (float)c->gravity[i];
+    P.pdl = 1;
 
     const long long S = (long long)h->ncomp * h->np;
     const int d = h->dim;
@@ -1270,6 +1271,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (h->tile != (value == 1)) drop_graphs(h);
             h->tile = value == 1;
             return MPM_OK;
+        case MPM_OPT_PDL:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "pdl must be 0 or 1");
+            if (h->P.pdl != (int)value) drop_graphs(h);
+            h->P.pdl = (int)value;
+            return MPM_OK;
         case MPM_OPT_STREAMS:
             if (value != 1 && value != 2) return fail(h, MPM_ERR_ARG, "streams must be 1 or 2");
             if (h->two_streams != (value == 2)) drop_graphs(h);
@@ -1305,6 +1311,7 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_GRAPHS: *value = h->graphs ? 1 : 0; return MPM_OK;
         case MPM_OPT_TILE: *value = h->tile ? 1 : 0; return MPM_OK;
         case MPM_OPT_STREAMS: *value = h->two_streams ? 2 : 1; return MPM_OK;
+        case MPM_OPT_PDL: *value = h->P.pdl; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

@@ -6,9 +6,29 @@
 // float4 per node.
 #pragma once
 
+#include <utility>
+
 #include "kernels.h"
 
 namespace mpm {
+
+// Launch a per-substep kernel; with P.pdl the launch allows programmatic
+// dependent launch (the kernel begins with pdl_wait()).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chain(const Params& P, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                         cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = P.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <int D>
 struct Layout {
