@@ -21,8 +21,9 @@ namespace mpm {
 
 namespace {
 
+// 3D: at most 64 registers (32 warps per SM) to keep more gathers in flight
 template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE>
-__global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
+__global__ void __launch_bounds__(256, D == 3 ? 4 : 1) k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
     pdl_wait();
     pdl_trigger();
@@ -50,11 +51,13 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
             Stencil<D> s;
             if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
             const float4* __restrict__ Vi = (FUSE ? a.accG : a.V) + (long long)inst * P.nodes;
+            // Eq. 19-20 with x_i - x_p = (o - r) dx for stencil offset o:
+            //   v = sum w V,  C = (4/dx) (sum w V o^T - v r^T)
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 v[i] = 0.0f;
 #pragma unroll
-                for (int j = 0; j < D; ++j) C[i][j] = 0.0f;
+                for (int j = 0; j < D; ++j) C[i][j] = 0.0f;  // sum w V o^T
             }
 #pragma unroll
             for (int k = 0; k < stencil_size<D>(); ++k) {
@@ -64,16 +67,22 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
                 node_velocity<D, FUSE>(Vi, t, P, gv);
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    v[i] += t.w * gv[i];                          // Eq. 19
+                    const float wv = t.w * gv[i];
+                    v[i] += wv;
 #pragma unroll
-                    for (int j = 0; j < D; ++j) C[i][j] += t.w * gv[i] * t.dpos[j];  // Eq. 20
+                    for (int j = 0; j < D; ++j) {
+                        const int o = stencil_offset<D>(k, j);
+                        if (o == 1) C[i][j] += wv;
+                        else if (o == 2) C[i][j] += 2.0f * wv;
+                    }
                 }
             }
             float Fn[D][D];
+            const float c4 = 4.0f * P.inv_dx;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) C[i][j] *= P.kappa;
+                for (int j = 0; j < D; ++j) C[i][j] = c4 * (C[i][j] - v[i] * s.r[j]);
                 x[i] += P.dt * v[i];                              // Eq. 21
             }
             // Eq. 22 in strain form: E' = E + dt C (I + E)
@@ -129,6 +138,19 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
                 A[i][j] = mp * C[i][j] - sc * pft;
             }
         float4* __restrict__ ai = a.acc + (long long)inst * P.nodes;
+        // Eq. 15 with x_i - x_p = (o - r) dx: node momentum w (u + dx A o),
+        // u = m v - dx A r
+        float u[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float ar = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                A[i][j] *= P.dx;
+                ar += A[i][j] * s.r[j];
+            }
+            u[i] = mp * v[i] - ar;
+        }
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
             NodeTerm<D> t;
@@ -136,10 +158,14 @@ __global__ void __launch_bounds__(256) k_forward(Params P, StepArgs a) {
             float mv[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                float ad = 0.0f;
+                float m = u[i];
 #pragma unroll
-                for (int j = 0; j < D; ++j) ad += A[i][j] * t.dpos[j];
-                mv[i] = t.w * (mp * v[i] + ad);   // Eq. 15
+                for (int j = 0; j < D; ++j) {
+                    const int o = stencil_offset<D>(k, j);
+                    if (o == 1) m += A[i][j];
+                    else if (o == 2) m += 2.0f * A[i][j];
+                }
+                mv[i] = t.w * m;
             }
             atomicAdd(ai + t.node, pack4<D>(t.w * mp, mv));  // Eq. 14 in .x
         }

@@ -93,7 +93,7 @@ __device__ __forceinline__ bool make_stencil(const float (&x)[D], const Params& 
 
 template <int D>
 struct NodeTerm {
-    long long node;  // node index within the instance grid
+    int node;        // node index within the instance grid (< 2^31 by configuration check)
     int c[D];        // node coordinates
     float w;         // weight N(x_p - x_i)
     float gw[D];     // d w / d x_p
@@ -115,7 +115,7 @@ __device__ __forceinline__ void node_term(const Stencil<D>& s, int k, const Para
 #pragma unroll
     for (int a = 0; a < D; ++a) w *= s.w[a][o[a]];
     t.w = w;
-    long long idx = 0;
+    int idx = 0;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
         float g = s.dw[c][o[c]] * P.inv_dx;
@@ -128,6 +128,13 @@ __device__ __forceinline__ void node_term(const Stencil<D>& s, int k, const Para
         idx = idx * P.res + t.c[c];
     }
     t.node = idx;
+}
+
+// offset along axis b of stencil node k (node k = (o0, o1[, o2]), last axis fastest);
+// a compile-time constant inside unrolled loops over k
+template <int D>
+__device__ __forceinline__ constexpr int stencil_offset(int k, int b) {
+    return D == 2 ? (b == 0 ? k / 3 : k % 3) : (b == 0 ? k / 9 : (b == 1 ? (k / 3) % 3 : k % 3));
 }
 
 // ---------------------------------------------------------------------------
