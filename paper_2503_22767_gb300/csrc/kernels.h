@@ -39,7 +39,6 @@ struct StepArgs {
     const float4* VbarIn = nullptr;  // Vbar of the P2G^T substep
     float4* zero4 = nullptr;         // buffer the kernel clears for a later substep
     long long zero_n = 0;            // its length in float4
-    int agg = 0;                     // warp-aggregate scatters of lanes sharing a cell
 };
 
 // forward particle kernel: G2P of substep n_g2p and/or P2G of n_p2g.

@@ -16,7 +16,6 @@
 // (v, 0), adjoints (mbar, mvbar).
 #include "kernels.h"
 #include "particle_io.cuh"
-#include "tile.cuh"
 
 namespace mpm {
 
@@ -113,83 +112,62 @@ __global__ void __launch_bounds__(256, D == 3 ? 4 : 1) k_forward(Params P, StepA
         if (P.loss_kind == 1 && a.mom != nullptr)
             warp_add_per_instance<1>(mom_x, inst, a.mom + (long long)a.n_g2p * P.n_inst, 1);
     }
-    if (P2G) {
+    if (P2G && active) {
         Stencil<D> s;
+        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        StressParts<D> S;
+        stress_parts<D>(F, phi, P, S);
+        if (!(S.J > 0.0f)) flags |= kErrNumeric;
+        float Br[D], Ba[D], Pk[D][D], A[D][D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) s.base[i] = 0;
-        float A[D][D], u[D];
-        if (active) {
-            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
-            StressParts<D> S;
-            stress_parts<D>(F, phi, P, S);
-            if (!(S.J > 0.0f)) flags |= kErrNumeric;
-            float Br[D], Ba[D], Pk[D][D];
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                Br[i] = a.mag[(long long)i * np + p];
-                Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
-            }
-            piola<D>(S, Br, Ba, Pk);
-            const float sc = P.dt * P.kappa * P.p_vol;
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
-#pragma unroll
-                    for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
-                    // MLS-MPM affine momentum (Eq. 15 with the time step and the
-                    // x_i - x_p offset of the MLS-MPM form): m C - dt (4/dx^2) V P F^T
-                    A[i][j] = mp * C[i][j] - sc * pft;
-                }
-            // Eq. 15 with x_i - x_p = (o - r) dx: node momentum w (u + dx A o),
-            // u = m v - dx A r
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                float ar = 0.0f;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    A[i][j] *= P.dx;
-                    ar += A[i][j] * s.r[j];
-                }
-                u[i] = mp * v[i] - ar;
-            }
+        for (int i = 0; i < D; ++i) {
+            Br[i] = a.mag[(long long)i * np + p];
+            Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
         }
-        float4* __restrict__ ai = a.acc + (long long)(active ? inst : 0) * P.nodes;
-        // warp aggregation: lanes of one run of equal (instance, base cell) sum
-        // their node contributions with shuffles; the run's first lane adds them.
-        // The key fits in an int: instances x cells is bounded below 2^31 at
-        // creation (the sort's key space), and idle lanes take distinct negatives.
-        int key = -1 - (int)(threadIdx.x & 31);
-        if (active) key = (int)(inst * P.nodes) + grid_index<D>(s.base, P.res);
-        const Segments sg = a.agg ? make_segments(key) : Segments{0, 0, true};
+        piola<D>(S, Br, Ba, Pk);
+        const float sc = P.dt * P.kappa * P.p_vol;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
+#pragma unroll
+                for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
+                // MLS-MPM affine momentum (Eq. 15 with the time step and the
+                // x_i - x_p offset of the MLS-MPM form): m C - dt (4/dx^2) V P F^T
+                A[i][j] = mp * C[i][j] - sc * pft;
+            }
+        float4* __restrict__ ai = a.acc + (long long)inst * P.nodes;
+        // Eq. 15 with x_i - x_p = (o - r) dx: node momentum w (u + dx A o),
+        // u = m v - dx A r
+        float u[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float ar = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                A[i][j] *= P.dx;
+                ar += A[i][j] * s.r[j];
+            }
+            u[i] = mp * v[i] - ar;
+        }
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
             NodeTerm<D> t;
-            float val[D + 1];
+            node_term<D>(s, k, P, t);
+            float mv[D];
 #pragma unroll
-            for (int c = 0; c <= D; ++c) val[c] = 0.0f;
-            if (active) {
-                node_term<D>(s, k, P, t);
-                val[0] = t.w * mp;  // Eq. 14
+            for (int i = 0; i < D; ++i) {
+                float m = u[i];
 #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    float m = u[i];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        const int o = stencil_offset<D>(k, j);
-                        if (o == 1) m += A[i][j];
-                        else if (o == 2) m += 2.0f * A[i][j];
-                    }
-                    val[1 + i] = t.w * m;
+                for (int j = 0; j < D; ++j) {
+                    const int o = stencil_offset<D>(k, j);
+                    if (o == 1) m += A[i][j];
+                    else if (o == 2) m += 2.0f * A[i][j];
                 }
+                mv[i] = t.w * m;
             }
-            if (a.agg) {
-#pragma unroll
-                for (int c = 0; c <= D; ++c) val[c] = seg_sum(val[c], sg);
-            }
-            if (active && sg.head)
-                atomicAdd(ai + t.node, make_float4(val[0], val[1], val[2 % (D + 1)], D == 3 ? val[3 % (D + 1)] : 0.0f));
+            atomicAdd(ai + t.node, pack4<D>(t.w * mp, mv));  // Eq. 14 in .x
         }
     }
     if (flags) atomicOr(a.err, flags);
@@ -398,87 +376,70 @@ __global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
             store_mat<D>(a.adj, L::F, np, p, Fb);
         }
     }
-    if (G2PT) {
-        Stencil<D> s;
-#pragma unroll
-        for (int i = 0; i < D; ++i) s.base[i] = 0;
-        float vt[D], Ct[D][D], Fo[D][D];
-        if (active) {
-            if (!P2GT) {
-                // adjoint of state m+1 and C_{m+1} from memory
-                load_vec<D>(a.adj, L::X, np, p, xb);
-                load_vec<D>(a.adj, L::V, np, p, vb);
-                load_mat<D>(a.adj, L::C, np, p, Cb);
-                load_mat<D>(a.adj, L::F, np, p, Fb);
-                load_mat<D>(a.s_in, L::C, np, p, Cn);
-            }
-            float x[D], F[D][D];
-            load_vec<D>(a.s_aux, L::X, np, p, x);
-            load_mat<D>(a.s_aux, L::F, np, p, F);
-            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
-            // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
-#pragma unroll
-            for (int i = 0; i < D; ++i) vt[i] = vb[i] + P.dt * xb[i];
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    float fft = Fb[i][j], ctf = Fb[i][j];  // F = I + E
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        fft += Fb[i][k] * F[j][k];          // (Fbar F^T)_ij
-                        ctf += P.dt * Cn[k][i] * Fb[k][j];  // ((I + dt C')^T Fbar)_ij
-                    }
-                    Ct[i][j] = Cb[i][j] + P.dt * fft;
-                    Fo[i][j] = ctf;
-                }
+    if (G2PT && active) {
+        if (!P2GT) {
+            // adjoint of state m+1 and C_{m+1} from memory
+            load_vec<D>(a.adj, L::X, np, p, xb);
+            load_vec<D>(a.adj, L::V, np, p, vb);
+            load_mat<D>(a.adj, L::C, np, p, Cb);
+            load_mat<D>(a.adj, L::F, np, p, Fb);
+            load_mat<D>(a.s_in, L::C, np, p, Cn);
         }
-        const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)(active ? inst : 0) * P.nodes;
-        float4* __restrict__ Vbi = a.Vbar + (long long)(active ? inst : 0) * P.nodes;
-        int key = -1 - (int)(threadIdx.x & 31);
-        if (active) key = (int)(inst * P.nodes) + grid_index<D>(s.base, P.res);
-        const Segments sg = a.agg ? make_segments(key) : Segments{0, 0, true};
+        float x[D], F[D][D];
+        load_vec<D>(a.s_aux, L::X, np, p, x);
+        load_mat<D>(a.s_aux, L::F, np, p, F);
+        Stencil<D> s;
+        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
+        float vt[D], Ct[D][D], Fo[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) vt[i] = vb[i] + P.dt * xb[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                float fft = Fb[i][j], ctf = Fb[i][j];  // F = I + E
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    fft += Fb[i][k] * F[j][k];          // (Fbar F^T)_ij
+                    ctf += P.dt * Cn[k][i] * Fb[k][j];  // ((I + dt C')^T Fbar)_ij
+                }
+                Ct[i][j] = Cb[i][j] + P.dt * fft;
+                Fo[i][j] = ctf;
+            }
+        const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
+        float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
             NodeTerm<D> t;
+            node_term<D>(s, k, P, t);
+            float gv[D];
+            node_velocity<D, FUSE_V>(Vi, t, P, gv);
+            // Eq. 19-20 reversed: v' = sum w V, C' = kappa sum w V dpos^T
+            float vdot = 0.0f, vcd = 0.0f, cd[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                cd[i] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) cd[i] += Ct[i][j] * t.dpos[j];
+                vdot += gv[i] * vt[i];
+                vcd += gv[i] * cd[i];
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                float ctv = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) ctv += Ct[i][c] * gv[i];
+                xb[c] += t.gw[c] * (vdot + P.kappa * vcd) - P.kappa * t.w * ctv;
+            }
             float sv[D];
 #pragma unroll
-            for (int i = 0; i < D; ++i) sv[i] = 0.0f;
-            if (active) {
-                node_term<D>(s, k, P, t);
-                float gv[D];
-                node_velocity<D, FUSE_V>(Vi, t, P, gv);
-                // Eq. 19-20 reversed: v' = sum w V, C' = kappa sum w V dpos^T
-                float vdot = 0.0f, vcd = 0.0f, cd[D];
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    cd[i] = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) cd[i] += Ct[i][j] * t.dpos[j];
-                    vdot += gv[i] * vt[i];
-                    vcd += gv[i] * cd[i];
-                }
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    float ctv = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) ctv += Ct[i][c] * gv[i];
-                    xb[c] += t.gw[c] * (vdot + P.kappa * vcd) - P.kappa * t.w * ctv;
-                }
-#pragma unroll
-                for (int i = 0; i < D; ++i) sv[i] = t.w * (vt[i] + P.kappa * cd[i]);
-            }
-            if (a.agg) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) sv[i] = seg_sum(sv[i], sg);
-            }
-            if (active && sg.head)
-                atomicAdd(Vbi + t.node, make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f));
+            for (int i = 0; i < D; ++i) sv[i] = t.w * (vt[i] + P.kappa * cd[i]);
+            float4 c4 = make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f);
+            atomicAdd(Vbi + t.node, c4);
         }
-        if (active) {
-            store_vec<D>(a.adj, L::X, np, p, xb);
-            store_mat<D>(a.adj, L::F, np, p, Fo);
-        }
+        store_vec<D>(a.adj, L::X, np, p, xb);
+        store_mat<D>(a.adj, L::F, np, p, Fo);
     }
     if (flags) atomicOr(a.err, flags);
 }

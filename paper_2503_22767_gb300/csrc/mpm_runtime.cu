@@ -114,7 +114,6 @@ struct mpm_handle {
     bool fuse_fwd = true;   // grid operation folded into the forward particle kernels
     bool fuse_adj = false;  // grid adjoint folded into the adjoint particle kernels
     bool tile = false;      // shared-memory tiled transfers in the per-substep kernels
-    bool agg = true;        // warp-aggregated scatters in the direct (untiled) kernels
     bool graphs = true;   // replay the forward / backward passes as CUDA graphs
     bool v0_given = false;
 
@@ -496,7 +495,6 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
 
 StepArgs base_args(mpm_handle* h) {
     StepArgs a;
-    a.agg = h->agg ? 1 : 0;
     a.phi = h->phi_cur;
     a.mag = h->mag_cur;
     a.field = h->field;
@@ -960,7 +958,7 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
 // autotuner: time candidate launch configurations, keep the fastest
 // ---------------------------------------------------------------------------
 struct TuneChoice {
-    int block, fuse, tile, agg;
+    int block, fuse, tile;
     double ms;
 };
 
@@ -984,8 +982,8 @@ bool cache_lookup(const char* path, const std::string& sig, TuneChoice* out) {
         const char* p = std::strstr(line, key.c_str());
         if (!p) continue;
         TuneChoice c{};
-        if (std::sscanf(p + key.size(), "{\"block\": %d, \"fuse\": %d, \"tile\": %d, \"agg\": %d, \"ms\": %lf}",
-                        &c.block, &c.fuse, &c.tile, &c.agg, &c.ms) == 5) {
+        if (std::sscanf(p + key.size(), "{\"block\": %d, \"fuse\": %d, \"tile\": %d, \"ms\": %lf}", &c.block,
+                        &c.fuse, &c.tile, &c.ms) == 4) {
             *out = c;
             found = true;
         }
@@ -1009,8 +1007,8 @@ void cache_store(const char* path, const std::string& sig, const TuneChoice& c) 
         std::fclose(f);
     }
     char buf[512];
-    std::snprintf(buf, sizeof buf, "  \"%s\": {\"block\": %d, \"fuse\": %d, \"tile\": %d, \"agg\": %d, \"ms\": %.4f}",
-                  sig.c_str(), c.block, c.fuse, c.tile, c.agg, c.ms);
+    std::snprintf(buf, sizeof buf, "  \"%s\": {\"block\": %d, \"fuse\": %d, \"tile\": %d, \"ms\": %.4f}",
+                  sig.c_str(), c.block, c.fuse, c.tile, c.ms);
     lines.push_back(buf);
     std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
@@ -1028,7 +1026,6 @@ void apply_choice(mpm_handle* h, const TuneChoice& c) {
     h->fuse_fwd = (c.fuse & 1) != 0;
     h->fuse_adj = (c.fuse & 2) != 0;
     h->tile = c.tile != 0;
-    h->agg = c.agg != 0;
 }
 
 int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cudaStream_t st,
@@ -1052,8 +1049,8 @@ int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cu
     int rc = MPM_OK;
     for (int block : {64, 128, 256}) {
         for (int fuse : {0, 1, 3}) {
-            for (int agg : {0, 1}) {
-                TuneChoice c{block, fuse, 0, agg, 0.0};
+            for (int tile : {0, 1}) {
+                TuneChoice c{block, fuse, tile, 0.0};
                 apply_choice(h, c);
                 h->tune_T = sample;
                 // first run captures the graphs; then time the best of 3
@@ -1274,11 +1271,6 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (h->tile != (value == 1)) drop_graphs(h);
             h->tile = value == 1;
             return MPM_OK;
-        case MPM_OPT_AGG:
-            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "agg must be 0 or 1");
-            if (h->agg != (value == 1)) drop_graphs(h);
-            h->agg = value == 1;
-            return MPM_OK;
         case MPM_OPT_PDL:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "pdl must be 0 or 1");
             if (h->P.pdl != (int)value) drop_graphs(h);
@@ -1320,7 +1312,6 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_TILE: *value = h->tile ? 1 : 0; return MPM_OK;
         case MPM_OPT_STREAMS: *value = h->two_streams ? 2 : 1; return MPM_OK;
         case MPM_OPT_PDL: *value = h->P.pdl; return MPM_OK;
-        case MPM_OPT_AGG: *value = h->agg ? 1 : 0; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

@@ -153,9 +153,7 @@ __device__ __forceinline__ Segments make_segments(int key) {
 
 __device__ __forceinline__ float seg_sum(float v, const Segments& s) {
     const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-        if (r >= s.rounds) break;  // warp-uniform
+    for (int r = 0; r < s.rounds; ++r) {
         const int off = 1 << r;
         const float y = __shfl_down_sync(0xffffffffu, v, off);
         if (lane + off <= s.end) v += y;

@@ -319,8 +319,7 @@ def test_execution_modes(key, fuse, graphs, tile):
     transfers: same results, twice in a row."""
     w, of, ob = _oracle(key)
     sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs, B.MPM_OPT_TILE: tile,
-                B.MPM_OPT_STREAMS: 1 + (fuse + graphs + tile) % 2, B.MPM_OPT_PDL: (fuse + tile) % 2,
-                B.MPM_OPT_AGG: (graphs + tile + 1) % 2}
+                B.MPM_OPT_STREAMS: 1 + (fuse + graphs + tile) % 2, B.MPM_OPT_PDL: (fuse + tile) % 2}
     for _ in range(2):
         g = run_gpu(w, options=sim_opts)
         assert_state(g, of, w)
