@@ -163,6 +163,14 @@ def run_ours(args):
         tuned = sim.autotune(sample_substeps=min(cfg.n_steps, 200))
         tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
 
+    if args.options:
+        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "tile": 5, "streams": 6, "pdl": 7}
+        for item in args.options.split(","):
+            name, value = item.split("=")
+            sim.set_option(keys[name.strip()], int(value))
+        if tuned is not None:
+            tuned = {**sim.options(), "tuning_s": tuned["tuning_s"], "overridden": args.options}
+
     # timing events are part of the captured graphs: switch them on before the
     # warm-up so that the warm-up (not the timed region) captures the graphs
     sim.set_option(1, args.timing_stride)  # time every k-th launch of each kernel class
@@ -233,8 +241,17 @@ def run_ours(args):
     hgm = torch.empty(mag.shape).pin_memory()
     hgf = torch.empty(field.shape).pin_memory()
     e2e_steps = args.e2e_steps if args.e2e_steps else max(1, min(args.steps, 3))
-    # one untimed pass through the host entry points (re-captures the graphs
-    # without timing events)
+    # the device-buffer iteration timed the same way (host wall clock around
+    # synchronised iterations), so the two paths compare directly; its first,
+    # untimed call re-captures the graphs without timing events
+    iteration()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        iteration()
+    torch.cuda.synchronize()
+    dev_wall_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    # one untimed pass through the host entry points
     sim.forward_host(hx0, hphi, hmag, hfield, None, None, None, hloss)
     sim.backward_host(hdl, hgp, hgm, hgf)
     torch.cuda.synchronize()
@@ -248,6 +265,7 @@ def run_ours(args):
     d2h = 4 * (cfg.n_instances + w.phi.size + w.mag.size + w.field.size)
     e2e = {"value": round(ps / (e2e_ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3), "steps": e2e_steps,
+           "device_buffers_wall_ms_per_step": round(dev_wall_ms, 3),
            "api": "mpm_forward_host + mpm_backward_host (C ABI, pinned host buffers)"}
     if dist:
         t2 = torch.tensor([e2e_ms], device=dev)
@@ -351,6 +369,9 @@ def main(argv=None):
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch options")
+    ap.add_argument("--options", default="",
+                    help="launch options applied after autotuning, e.g. block=64,fuse_grid=0 "
+                         "(names as in Simulator.options())")
     ap.add_argument("--substeps", type=int, default=4000,
                     help="horizon of the timed workload (4000 = the full configuration)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end iterations (default min(steps, 3))")

@@ -19,11 +19,27 @@
 
 namespace mpm {
 
+// Resident 256-thread blocks per SM that the register allocation must allow
+// (the compiler caps registers at 65536 / (256 x this)).  The 3D transfer
+// kernels are latency-bound, so occupancy is traded against spills here.
+#ifndef MPM_MIN_BLOCKS_FORWARD3
+#define MPM_MIN_BLOCKS_FORWARD3 4
+#endif
+#ifndef MPM_MIN_BLOCKS_ADJOINT3
+#define MPM_MIN_BLOCKS_ADJOINT3 1
+#endif
+#ifndef MPM_MIN_BLOCKS_ADJOINT2
+#define MPM_MIN_BLOCKS_ADJOINT2 1
+#endif
+constexpr int kMinBlocksForward3 = MPM_MIN_BLOCKS_FORWARD3;
+constexpr int kMinBlocksAdjoint3 = MPM_MIN_BLOCKS_ADJOINT3;
+constexpr int kMinBlocksAdjoint2 = MPM_MIN_BLOCKS_ADJOINT2;
+
 namespace {
 
 // 3D: at most 64 registers (32 warps per SM) to keep more gathers in flight
 template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE>
-__global__ void __launch_bounds__(256, D == 3 ? 4 : 1) k_forward(Params P, StepArgs a) {
+__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
     pdl_wait();
     pdl_trigger();
@@ -226,7 +242,7 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
 // FUSE: P2G^T evaluates the grid adjoint per stencil node from (accP, VbarIn);
 // FUSE_V: G2P^T takes the grid velocity from accG through the grid operation.
 template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V>
-__global__ void __launch_bounds__(256) k_adjoint(Params P, StepArgs a) {
+__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksAdjoint3 : kMinBlocksAdjoint2) k_adjoint(Params P, StepArgs a) {
     using L = Layout<D>;
     pdl_wait();
     pdl_trigger();

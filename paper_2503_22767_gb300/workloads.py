@@ -348,18 +348,46 @@ def walker_batch_2d(seed: int = 0, n_instances: int = 64, n_steps: int = 2000, r
         w = walker_2d(seed=int(rng.integers(1 << 30)), n_steps=n_steps, res=res,
                       scale=float(np.sqrt(n_i / 30000.0)), checkpoint_every=checkpoint_every)
         parts.append(w)
-    cfg = parts[0].cfg
-    counts = [p.cfg.counts[0] for p in parts]
-    cfg = MpmConfig(**{**cfg.as_dict(), "counts": counts, "design_of_instance": None})
-    return Workload(
-        "walker2d_batch64", cfg,
-        np.concatenate([p.x0 for p in parts], axis=1),
-        None,
-        np.concatenate([p.phi for p in parts]),
-        np.concatenate([p.mag for p in parts], axis=1),
-        np.concatenate([p.field for p in parts], axis=0),
-        None,
-    )
+    return batch(parts, name="walker2d_batch64")
+
+
+def batch(parts, design_of_instance: Optional[List[int]] = None, name: str = "batch") -> Workload:
+    """Concatenate single-instance workloads into one batch.
+
+    Configs must agree except for the particle count.  With
+    ``design_of_instance``, design ``k`` takes phi / mag from the first part
+    that uses it, and every part with that design must have its particle
+    count (multi-task sharing, Eq. 35).  Otherwise every part keeps its own
+    design.
+    """
+    counts = [int(p.cfg.counts[0]) for p in parts]
+    if any(p.cfg.n_instances != 1 for p in parts):
+        raise ValueError("batch() takes single-instance workloads")
+    if design_of_instance is None:
+        phi = np.concatenate([p.phi for p in parts])
+        mag = np.concatenate([p.mag for p in parts], axis=1)
+    else:
+        if len(design_of_instance) != len(parts):
+            raise ValueError("design_of_instance needs one entry per part")
+        first = {}
+        for i, d in enumerate(design_of_instance):
+            first.setdefault(int(d), i)
+            if counts[i] != counts[first[int(d)]]:
+                raise ValueError("instances sharing a design need equal particle counts")
+        if sorted(first) != list(range(len(first))):
+            raise ValueError("design ids must be 0..n_designs-1")
+        phi = np.concatenate([parts[first[d]].phi for d in range(len(first))])
+        mag = np.concatenate([parts[first[d]].mag for d in range(len(first))], axis=1)
+    v0 = None
+    if any(p.v0 is not None for p in parts):
+        v0 = np.concatenate([p.v0 if p.v0 is not None else np.zeros_like(p.x0) for p in parts], axis=1)
+    target = None
+    if all(p.target is not None for p in parts):
+        target = np.concatenate([p.target for p in parts], axis=1)
+    cfg = MpmConfig(**{**parts[0].cfg.as_dict(), "counts": counts,
+                       "design_of_instance": list(design_of_instance) if design_of_instance is not None else None})
+    return Workload(name, cfg, np.concatenate([p.x0 for p in parts], axis=1), v0, phi, mag,
+                    np.concatenate([p.field for p in parts], axis=0), target)
 
 
 def tiny_2d(seed: int = 0, n_steps: int = 20, res: int = 16, per_axis: int = 2, cells=(4, 2),
