@@ -1,11 +1,13 @@
 """Throughput of the differentiable magneto-elastic MPM on one GB300.
 
-One bench step = one design iteration of the 2D locomotion workload: the
+One bench step = one design iteration of a workload (default: the 2D
+locomotion configuration, 30,000 particles on 128^2 for 4,000 substeps): the
 forward pass over the whole horizon (cell sort, P2G, grid operation, G2P,
 objective) plus the checkpointed adjoint (recomputation and the reverse
 kernels), producing dL/dphi, dL/dB~_r and dL/dB_applied.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload walker2d_128|beam2d_64|plate3d_64|walker3d_128|walker2d_batch64]
 
 Prints one JSON line (rank 0).  ``value`` is particle-steps per second of
 forward+adjoint over all ranks (sum of particles x substeps / max time);
@@ -37,19 +39,36 @@ CLASS_NAMES = ["forward particle (G2P+P2G)", "adjoint particle (P2G^T+G2P^T)", "
                "grid adjoint"]
 
 
-def workload(seed=0, substeps=4000):
-    """The 2D locomotion workload (walker_2d: 30,000 particles, 128^2 grid);
-    ``substeps`` below 4,000 only for short profiling runs."""
-    return W.walker_2d(seed=seed, n_steps=substeps, checkpoint_every=100)
+# the paper's five workload shapes: generator and full horizon.  The default,
+# walker2d_128, is the configuration the metric is quoted on; the others are
+# for measuring the same step on the other shapes.
+WORKLOADS = {
+    "walker2d_128": (lambda seed, n: W.walker_2d(seed=seed, n_steps=n, checkpoint_every=100), 4000),
+    "beam2d_64": (lambda seed, n: W.beam_2d(seed=seed, n_steps=n), 200),
+    "plate3d_64": (lambda seed, n: W.with_steps(W.plate_3d(seed=seed, n_steps=n), n, checkpoint_every=100), 1000),
+    "walker3d_128": (lambda seed, n: W.walker_3d(seed=seed, n_steps=n, checkpoint_every=100), 5000),
+    "walker2d_batch64": (lambda seed, n: W.walker_batch_2d(seed=seed, n_steps=n, checkpoint_every=100), 2000),
+}
 
 
-def workload_desc(w):
+def workload(name="walker2d_128", seed=0, substeps=None):
+    """A named workload; ``substeps`` shortens the horizon (profiling runs)."""
+    make, full = WORKLOADS[name]
+    return make(seed, substeps if substeps else full)
+
+
+def workload_desc(w, name):
     c = w.cfg
+    contact = f"Coulomb floor mu={c.floor_mu}" if c.wall_mode == 1 else "non-slip walls"
+    loss = "locomotion loss (Eq. 40)" if c.loss_kind == 1 else "final-position MSE (Eq. 38)"
+    inst = (f"{c.n_instances} instances sharing {c.n_designs} design(s)" if c.n_instances > 1
+            else "one instance")
+    ckpt = f"checkpoint every {c.checkpoint_every}" if c.checkpoint_every else "every substep stored"
     return {
-        "workload": (f"walker2d_128: 2D locomotion, {c.res}^2 grid, {c.n_total} particles, "
-                     f"{c.n_steps} substeps dt={c.dt}, Coulomb floor mu={c.floor_mu}, "
-                     f"16-coefficient Fourier field per axis, checkpoint every {c.checkpoint_every}"),
+        "workload": (f"{name}: {c.dim}D, {c.res}^{c.dim} grid, {c.n_total} particles, {inst}, "
+                     f"{c.n_steps} substeps dt={c.dt}, {contact}, {loss}, {ckpt}"),
         "particles": c.n_total,
+        "instances": c.n_instances,
         "substeps": c.n_steps,
         "grid": f"{c.res}^{c.dim}",
         "checkpoint_every": c.checkpoint_every,
@@ -141,30 +160,31 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_2503_22767_gb300.sim import Simulator
 
-    w = workload(seed=rank, substeps=args.substeps)
+    w = workload(args.workload, seed=rank, substeps=args.substeps)
     cfg = w.cfg
     sim = Simulator(cfg)
     t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     x0, phi, mag, field = t(w.x0), t(w.phi), t(w.mag), t(w.field)
+    target, v0 = t(w.target), t(w.v0)
     dloss = torch.ones(cfg.n_instances, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
     def iteration():
-        loss, _ = sim.forward(x0, phi, mag, field)
+        loss, _ = sim.forward(x0, phi, mag, field, target=target, v0=v0)
         g = sim.backward(dloss)
         return loss, g
 
     # launch configuration picked by the library's autotuner (outside the timed region)
     tuned = None
     if not args.no_autotune:
-        sim.forward(x0, phi, mag, field)
+        sim.forward(x0, phi, mag, field, target=target, v0=v0)
         t0 = time.perf_counter()
         tuned = sim.autotune(sample_substeps=min(cfg.n_steps, 200))
         tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
 
     if args.options:
-        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "tile": 5, "streams": 6, "pdl": 7}
+        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "tile": 5, "streams": 6, "pdl": 7, "adjoint_blocks": 8}
         for item in args.options.split(","):
             name, value = item.split("=")
             sim.set_option(keys[name.strip()], int(value))
@@ -235,6 +255,8 @@ def run_ours(args):
     # end to end through the host-buffer entry points (pinned memory)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hx0, hphi, hmag, hfield = pin(w.x0), pin(w.phi), pin(w.mag), pin(w.field)
+    htarget = pin(w.target) if w.target is not None else None
+    hv0 = pin(w.v0) if w.v0 is not None else None
     hloss = torch.empty(cfg.n_instances).pin_memory()
     hdl = torch.ones(cfg.n_instances).pin_memory()
     hgp = torch.empty(phi.shape).pin_memory()
@@ -252,16 +274,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     dev_wall_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     # one untimed pass through the host entry points
-    sim.forward_host(hx0, hphi, hmag, hfield, None, None, None, hloss)
+    sim.forward_host(hx0, hphi, hmag, hfield, htarget, hv0, None, hloss)
     sim.backward_host(hdl, hgp, hgm, hgf)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        sim.forward_host(hx0, hphi, hmag, hfield, None, None, None, hloss)
+        sim.forward_host(hx0, hphi, hmag, hfield, htarget, hv0, None, hloss)
         sim.backward_host(hdl, hgp, hgm, hgf)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    h2d = 4 * (w.x0.size + w.phi.size + w.mag.size + w.field.size + cfg.n_instances)
+    h2d = 4 * (w.x0.size + w.phi.size + w.mag.size + w.field.size + cfg.n_instances
+               + (w.target.size if w.target is not None else 0) + (w.v0.size if w.v0 is not None else 0))
     d2h = 4 * (cfg.n_instances + w.phi.size + w.mag.size + w.field.size)
     e2e = {"value": round(ps / (e2e_ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3), "steps": e2e_steps,
@@ -289,8 +312,8 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded walker body, design and field schedule; see workloads.walker_2d)",
-        "config": {**workload_desc(w), "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "data": f"synthetic (seeded bodies, designs and field schedules; workloads.py, {args.workload})",
+        "config": {**workload_desc(w, args.workload), "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "launch": tuned if tuned else sim_options,
                    "l2": "256 MB buffer written between timed iterations (outside the timed events)"},
         "ms_per_design_iteration": round(ms_per_step, 3),
@@ -322,7 +345,16 @@ def _oracle_sample(w, n_steps):
     return ws.cfg.n_total * n_steps / dt, dt
 
 
+def sample_steps(w, n_steps):
+    """Oracle sample length: the requested substeps, or (0) about 7 million
+    particle-steps, some 10-20 s of one host core."""
+    if n_steps > 0:
+        return min(n_steps, w.cfg.n_steps)
+    return int(max(1, min(w.cfg.n_steps, 7.0e6 // max(w.cfg.n_total, 1))))
+
+
 def cpu_baseline(w, n_steps):
+    n_steps = sample_steps(w, n_steps)
     v, dt = _oracle_sample(w, n_steps)
     return {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"first {n_steps} of {w.cfg.n_steps} substeps, all {w.cfg.n_total} particles, "
@@ -333,8 +365,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload()
-    n = args.cpu_sample_steps
+    w = workload(args.workload, substeps=args.substeps)
+    n = sample_steps(w, args.cpu_sample_steps)
     for _ in range(args.warmup):
         _oracle_sample(w, max(1, n // 4))
     times = []
@@ -351,7 +383,7 @@ def run_reference(args):
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {**workload_desc(w), "parallelism": "CPU, one core"},
+        "config": {**workload_desc(w, args.workload), "parallelism": "CPU, one core"},
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -366,14 +398,17 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--timing-stride", type=int, default=32,
                     help="time every k-th launch of each kernel class with CUDA events")
-    ap.add_argument("--cpu-sample-steps", type=int, default=100)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="walker2d_128",
+                    help="workload shape (default: the 2D locomotion configuration)")
+    ap.add_argument("--cpu-sample-steps", type=int, default=0,
+                    help="substeps of the oracle sample (0: about 7 million particle-steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch options")
     ap.add_argument("--options", default="",
                     help="launch options applied after autotuning, e.g. block=64,fuse_grid=0 "
                          "(names as in Simulator.options())")
-    ap.add_argument("--substeps", type=int, default=4000,
-                    help="horizon of the timed workload (4000 = the full configuration)")
+    ap.add_argument("--substeps", type=int, default=0,
+                    help="horizon of the timed workload (0: the configuration's full horizon)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end iterations (default min(steps, 3))")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")

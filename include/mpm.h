@@ -207,9 +207,13 @@ enum {
     MPM_OPT_STREAMS = 6, /* 2 (default): the backward pass recomputes checkpoint segment s-1
                             on a second stream while the adjoint of segment s runs (two
                             sets of segment buffers); 1: one stream */
-    MPM_OPT_PDL = 7     /* 1 (default): per-substep kernels use programmatic dependent
+    MPM_OPT_PDL = 7,    /* 1 (default): per-substep kernels use programmatic dependent
                            launch, so a kernel's CTAs are scheduled while its predecessor
                            drains; 0: plain stream order */
+    MPM_OPT_ADJOINT_BLOCKS = 8 /* register budget of the fused adjoint particle kernel, as
+                           resident 256-thread blocks per SM: 2 (default, <= 128 registers)
+                           or 3 (<= 80 registers: more warps to hide gather latency, at the
+                           cost of spills) */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);
@@ -221,7 +225,8 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value);
  * library).  Times forward + backward passes over the first sample_substeps
  * substeps (0 = two checkpoint segments) of the inputs staged by the last
  * mpm_forward, for every combination of block size {64, 128, 256}, grid
- * fusion {0, 1, 3} and tiles {0, 1}, and keeps the fastest.  With a
+ * fusion {0, 1, 3} and adjoint register budget {2, 3} (tiles off), and keeps
+ * the fastest.  With a
  * non-NULL cache_path, results are read from and written to that JSON file,
  * keyed by dim, grid_res, particle count (rounded up to a power of 2),
  * instances and checkpoint interval; a cache hit applies the stored choice

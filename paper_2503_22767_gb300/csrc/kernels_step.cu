@@ -20,20 +20,11 @@
 namespace mpm {
 
 // Resident 256-thread blocks per SM that the register allocation must allow
-// (the compiler caps registers at 65536 / (256 x this)).  The 3D transfer
-// kernels are latency-bound, so occupancy is traded against spills here.
-#ifndef MPM_MIN_BLOCKS_FORWARD3
-#define MPM_MIN_BLOCKS_FORWARD3 4
-#endif
-#ifndef MPM_MIN_BLOCKS_ADJOINT3
-#define MPM_MIN_BLOCKS_ADJOINT3 1
-#endif
-#ifndef MPM_MIN_BLOCKS_ADJOINT2
-#define MPM_MIN_BLOCKS_ADJOINT2 1
-#endif
-constexpr int kMinBlocksForward3 = MPM_MIN_BLOCKS_FORWARD3;
-constexpr int kMinBlocksAdjoint3 = MPM_MIN_BLOCKS_ADJOINT3;
-constexpr int kMinBlocksAdjoint2 = MPM_MIN_BLOCKS_ADJOINT2;
+// (the compiler caps registers at 65536 / (256 x this)).  The transfer kernels
+// are latency-bound, so occupancy is traded against spills: the 3D forward
+// kernel is held to 64 registers, and the adjoint kernel is compiled for 2
+// (<= 128 registers) and 3 (<= 80) blocks, chosen per launch (Params::adj_blocks).
+constexpr int kMinBlocksForward3 = 4;
 
 namespace {
 
@@ -241,8 +232,8 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
 // ---------------------------------------------------------------------------
 // FUSE: P2G^T evaluates the grid adjoint per stencil node from (accP, VbarIn);
 // FUSE_V: G2P^T takes the grid velocity from accG through the grid operation.
-template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V>
-__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksAdjoint3 : kMinBlocksAdjoint2) k_adjoint(Params P, StepArgs a) {
+template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     using L = Layout<D>;
     pdl_wait();
     pdl_trigger();
@@ -670,9 +661,13 @@ static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepAr
     if (P.n_total == 0 && !a.zero4) return cudaSuccess;
     long long threads = P.n_total > 0 ? P.n_total : block;
     dim3 grid(blocks_for(threads, block));
-    if (p2gt && g2pt) return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V>, grid, block, st, P, a);
-    if (p2gt) return launch_chain(P, k_adjoint<D, true, false, FUSE, FUSE_V>, grid, block, st, P, a);
-    return launch_chain(P, k_adjoint<D, false, true, FUSE, FUSE_V>, grid, block, st, P, a);
+    if (p2gt && g2pt) {
+        if (P.adj_blocks == 3) return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 3>, grid, block, st, P, a);
+        return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 2>, grid, block, st, P, a);
+    }
+    // the segment-edge halves run once per checkpoint segment
+    if (p2gt) return launch_chain(P, k_adjoint<D, true, false, FUSE, FUSE_V, 2>, grid, block, st, P, a);
+    return launch_chain(P, k_adjoint<D, false, true, FUSE, FUSE_V, 2>, grid, block, st, P, a);
 }
 
 template <int D>

@@ -30,6 +30,7 @@ struct Params {
     float p_vol, rho0, G, K, eps, damping, mu;
     float gravity[3];
     int pdl;  // per-substep kernels launched with programmatic dependent launch
+    int adj_blocks;  // register budget of the adjoint particle kernel: 256-thread blocks per SM (2 or 3)
 };
 
 // Programmatic dependent launch: a kernel launched with programmatic stream

@@ -424,6 +424,7 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     P.mu = (float)c->floor_mu;
     for (int i = 0; i < 3; ++i) P.gravity[i] = (float)c->gravity[i];
     P.pdl = 1;
+    P.adj_blocks = 2;
 
     const long long S = (long long)h->ncomp * h->np;
     const int d = h->dim;
@@ -958,7 +959,7 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
 // autotuner: time candidate launch configurations, keep the fastest
 // ---------------------------------------------------------------------------
 struct TuneChoice {
-    int block, fuse, tile;
+    int block, fuse, tile, adj;
     double ms;
 };
 
@@ -982,8 +983,9 @@ bool cache_lookup(const char* path, const std::string& sig, TuneChoice* out) {
         const char* p = std::strstr(line, key.c_str());
         if (!p) continue;
         TuneChoice c{};
-        if (std::sscanf(p + key.size(), "{\"block\": %d, \"fuse\": %d, \"tile\": %d, \"ms\": %lf}", &c.block,
-                        &c.fuse, &c.tile, &c.ms) == 4) {
+        if (std::sscanf(p + key.size(), "{\"block\": %d, \"fuse\": %d, \"tile\": %d, \"adj\": %d, \"ms\": %lf}",
+                        &c.block, &c.fuse, &c.tile, &c.adj, &c.ms) == 5 &&
+            (c.adj == 2 || c.adj == 3)) {
             *out = c;
             found = true;
         }
@@ -1007,8 +1009,8 @@ void cache_store(const char* path, const std::string& sig, const TuneChoice& c) 
         std::fclose(f);
     }
     char buf[512];
-    std::snprintf(buf, sizeof buf, "  \"%s\": {\"block\": %d, \"fuse\": %d, \"tile\": %d, \"ms\": %.4f}",
-                  sig.c_str(), c.block, c.fuse, c.tile, c.ms);
+    std::snprintf(buf, sizeof buf, "  \"%s\": {\"block\": %d, \"fuse\": %d, \"tile\": %d, \"adj\": %d, \"ms\": %.4f}",
+                  sig.c_str(), c.block, c.fuse, c.tile, c.adj, c.ms);
     lines.push_back(buf);
     std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
@@ -1026,6 +1028,7 @@ void apply_choice(mpm_handle* h, const TuneChoice& c) {
     h->fuse_fwd = (c.fuse & 1) != 0;
     h->fuse_adj = (c.fuse & 2) != 0;
     h->tile = c.tile != 0;
+    h->P.adj_blocks = c.adj;
 }
 
 int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cudaStream_t st,
@@ -1049,8 +1052,8 @@ int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cu
     int rc = MPM_OK;
     for (int block : {64, 128, 256}) {
         for (int fuse : {0, 1, 3}) {
-            for (int tile : {0, 1}) {
-                TuneChoice c{block, fuse, tile, 0.0};
+            for (int adj : {2, 3}) {
+                TuneChoice c{block, fuse, 0, adj, 0.0};
                 apply_choice(h, c);
                 h->tune_T = sample;
                 // first run captures the graphs; then time the best of 3
@@ -1271,6 +1274,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (h->tile != (value == 1)) drop_graphs(h);
             h->tile = value == 1;
             return MPM_OK;
+        case MPM_OPT_ADJOINT_BLOCKS:
+            if (value != 2 && value != 3) return fail(h, MPM_ERR_ARG, "adjoint blocks must be 2 or 3");
+            if (h->P.adj_blocks != (int)value) drop_graphs(h);
+            h->P.adj_blocks = (int)value;
+            return MPM_OK;
         case MPM_OPT_PDL:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "pdl must be 0 or 1");
             if (h->P.pdl != (int)value) drop_graphs(h);
@@ -1312,6 +1320,7 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_TILE: *value = h->tile ? 1 : 0; return MPM_OK;
         case MPM_OPT_STREAMS: *value = h->two_streams ? 2 : 1; return MPM_OK;
         case MPM_OPT_PDL: *value = h->P.pdl; return MPM_OK;
+        case MPM_OPT_ADJOINT_BLOCKS: *value = h->P.adj_blocks; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

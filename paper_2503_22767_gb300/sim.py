@@ -166,7 +166,7 @@ class Simulator:
         return keys, perm
 
     def autotune(self, cache_path=None, sample_substeps=0):
-        """Pick block size, grid fusion and tiling by timing them on the inputs
+        """Pick block size, grid fusion and the adjoint register budget by timing them on the inputs
         of the last forward (see mpm_autotune); returns the chosen options.
         The forward result is overwritten: run forward again afterwards."""
         path = cache_path.encode() if cache_path else None
@@ -178,7 +178,8 @@ class Simulator:
         out = {}
         for name, key in (("block", B.MPM_OPT_BLOCK), ("fuse_grid", B.MPM_OPT_FUSE_GRID),
                           ("tile", B.MPM_OPT_TILE), ("graphs", B.MPM_OPT_GRAPHS),
-                          ("streams", B.MPM_OPT_STREAMS), ("pdl", B.MPM_OPT_PDL)):
+                          ("streams", B.MPM_OPT_STREAMS), ("pdl", B.MPM_OPT_PDL),
+                          ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS)):
             v = ctypes.c_longlong()
             self._check(self.lib.mpm_get_option(self.handle, key, ctypes.byref(v)), "mpm_get_option")
             out[name] = v.value
