@@ -184,7 +184,7 @@ def run_ours(args):
         tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
 
     if args.options:
-        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "tile": 5, "streams": 6, "pdl": 7, "adjoint_blocks": 8}
+        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "tile": 5, "streams": 6, "pdl": 7, "adjoint_blocks": 8, "warp_box": 9}
         for item in args.options.split(","):
             name, value = item.split("=")
             sim.set_option(keys[name.strip()], int(value))
@@ -295,6 +295,9 @@ def run_ours(args):
         dist.all_reduce(t2, op=dist.ReduceOp.MAX)
         e2e["value"] = round(ps * world / (float(t2.item()) / 1e3), 1)
 
+    sequential = None
+    if cfg.n_instances > 1 and not args.no_sequential:
+        sequential = run_sequential(w, dev, g, ps)
     sim.close()
     if rank != 0:
         if dist:
@@ -324,11 +327,71 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "device_bytes": stats["device_bytes"],
     }
+    if sequential is not None:
+        sequential["batched_speedup"] = round(value / world / sequential["value"], 3)
+        out["sequential"] = sequential
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_sample_steps)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_sequential(w, dev, batched_grads, ps):
+    """The batch's instances as single-instance simulations run one after
+    another on the same stream: same kernels, launch options tuned once on the
+    first instance.  Returns their throughput and the gradient difference
+    from the batched run (equal accuracy check)."""
+    import torch
+    from paper_2503_22767_gb300 import shard
+    from paper_2503_22767_gb300.sim import Simulator
+
+    cfg = w.cfg
+    p = shard.plan(cfg.counts, cfg.design_of_instance, cfg.n_instances)  # one instance per slot
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    runs = []
+    for r in range(cfg.n_instances):
+        lw = shard.local_workload(w, p, r)
+        runs.append((p.local[r][0], Simulator(lw.cfg), (t(lw.x0), t(lw.phi), t(lw.mag), t(lw.field)),
+                     dict(target=t(lw.target), v0=t(lw.v0))))
+    first = runs[0]
+    first[1].forward(*first[2], **first[3])
+    tuned = first[1].autotune(sample_substeps=min(cfg.n_steps, 200))
+    for _, sim, _, _ in runs[1:]:
+        for key, name in ((2, "block"), (3, "fuse_grid"), (8, "adjoint_blocks")):
+            sim.set_option(key, tuned[name])
+    one = torch.ones(1, device=dev)
+
+    def sweep():
+        grads = {}
+        for i, sim, a, kw in runs:
+            sim.forward(*a, **kw)
+            grads[i] = sim.backward(one)
+        return grads
+
+    sweep()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    grads = sweep()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # gradient of each instance's design against its slice of the batched gradient
+    gp_b = batched_grads[0].cpu().numpy()
+    doff = np.concatenate([[0], np.cumsum(cfg.design_counts())]).astype(int)
+    num = den = 0.0
+    for i, (gp, _, _) in grads.items():
+        d = cfg.designs[i]
+        ref = gp_b[doff[d]:doff[d + 1]]
+        num += float(np.sum((gp.cpu().numpy() - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+    for _, sim, _, _ in runs:
+        sim.close()
+    return {"value": round(ps / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 3),
+            "instances": cfg.n_instances, "launch": {k: tuned[k] for k in ("block", "fuse_grid", "adjoint_blocks")},
+            "g_phi_rel_l2_vs_batched": float(np.sqrt(num / max(den, 1e-300))),
+            "what": "each instance as its own single-instance simulation, one after another"}
 
 
 # ---------------------------------------------------------------------------
@@ -404,6 +467,8 @@ def main(argv=None):
                     help="substeps of the oracle sample (0: about 7 million particle-steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch options")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="skip the one-instance-at-a-time comparison of multi-instance workloads")
     ap.add_argument("--options", default="",
                     help="launch options applied after autotuning, e.g. block=64,fuse_grid=0 "
                          "(names as in Simulator.options())")

@@ -210,10 +210,14 @@ enum {
     MPM_OPT_PDL = 7,    /* 1 (default): per-substep kernels use programmatic dependent
                            launch, so a kernel's CTAs are scheduled while its predecessor
                            drains; 0: plain stream order */
-    MPM_OPT_ADJOINT_BLOCKS = 8 /* register budget of the fused adjoint particle kernel, as
+    MPM_OPT_ADJOINT_BLOCKS = 8, /* register budget of the fused adjoint particle kernel, as
                            resident 256-thread blocks per SM: 2 (default, <= 128 registers)
                            or 3 (<= 80 registers: more warps to hide gather latency, at the
                            cost of spills) */
+    MPM_OPT_WARP_BOX = 9 /* 1 (default): in the direct particle kernels, each fully active
+                           warp whose stencils fit a 128-node box loads that box into shared
+                           memory once, and its gathers read from there; 0: every gather
+                           reads global memory */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);

@@ -19,6 +19,7 @@ MPM_ERR_STATE, MPM_ERR_NUMERIC, MPM_ERR_DOMAIN, MPM_ERR_TIMEOUT = -4, -5, -6, -7
 MPM_OPT_TIMING, MPM_OPT_BLOCK, MPM_OPT_FUSE_GRID, MPM_OPT_GRAPHS, MPM_OPT_TILE, MPM_OPT_STREAMS = 1, 2, 3, 4, 5, 6
 MPM_OPT_PDL = 7
 MPM_OPT_ADJOINT_BLOCKS = 8
+MPM_OPT_WARP_BOX = 9
 STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_CUDA", -3: "MPM_ERR_OOM",
                 -4: "MPM_ERR_STATE", -5: "MPM_ERR_NUMERIC", -6: "MPM_ERR_DOMAIN",
                 -7: "MPM_ERR_TIMEOUT"}

@@ -16,6 +16,7 @@
 // (v, 0), adjoints (mbar, mvbar).
 #include "kernels.h"
 #include "particle_io.cuh"
+#include "warp_box.cuh"
 
 namespace mpm {
 
@@ -54,10 +55,27 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
     }
     if (G2P) {
         float mom_x[1] = {0.0f};
+        Stencil<D> s;
+#pragma unroll
+        for (int i = 0; i < D; ++i) s.base[i] = 0;
+        if (active && !make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        const float4* __restrict__ Vg = FUSE ? a.accG : a.V;
+        __shared__ float4 s_box[kBoxWarps * box_nodes<D>()];
+        float4* sm = s_box + (threadIdx.x >> 5) * box_nodes<D>();
+        const WarpBox<D> box = warp_box<D>(s.base, active, inst, P.box != 0);
+        if (box.use) {
+            const float4* __restrict__ Vb = Vg + (long long)box.inst * P.nodes;
+            stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
+                const float4 g = __ldg(Vb + node);
+                if (!FUSE) return g;
+                float mv[D], gv[D];
+                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                grid_velocity<D>(P, c, g.x, mv, gv);  // Eq. 16-18 once per node
+                return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
+            });
+        }
         if (active) {
-            Stencil<D> s;
-            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
-            const float4* __restrict__ Vi = (FUSE ? a.accG : a.V) + (long long)inst * P.nodes;
+            const float4* __restrict__ Vi = Vg + (long long)inst * P.nodes;
             // Eq. 19-20 with x_i - x_p = (o - r) dx for stencil offset o:
             //   v = sum w V,  C = (4/dx) (sum w V o^T - v r^T)
 #pragma unroll
@@ -71,7 +89,11 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
                 NodeTerm<D> t;
                 node_term<D>(s, k, P, t);
                 float gv[D];
-                node_velocity<D, FUSE>(Vi, t, P, gv);
+                if (box.use) {
+                    unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
+                } else {
+                    node_velocity<D, FUSE>(Vi, t, P, gv);
+                }
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
                     const float wv = t.w * gv[i];
@@ -243,6 +265,11 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
     const long long np = P.np;
     int flags = 0;
+    // warps with every lane active may stage their stencil nodes (the staging
+    // runs inside the per-particle branches)
+    const bool full_warp = __ballot_sync(0xffffffffu, active) == 0xffffffffu;
+    __shared__ float4 s_box[kBoxWarps * box_nodes<D>()];
+    float4* sm = s_box + (threadIdx.x >> 5) * box_nodes<D>();
     // adjoint of the state between the two halves (state n if P2GT)
     float xb[D], vb[D], Cb[D][D], Fb[D][D];
     float Cn[D][D];  // C of state n (= m+1), needed by G2P^T
@@ -282,22 +309,50 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
                     A[i][j] = mp * Cn[i][j] - sc * pft;
                 }
-            float mpb = 0.0f, Ab[D][D];
+            // Node sums factored with x_i - x_p = (o - r) dx (o the stencil offset):
+            //   S0 = sum w mvb,  T = sum w mvb o^T,  mbs = sum w mb
+            // give vbar = mp S0, Abar = dx (T - S0 r^T) and
+            // mbar_p = mbs + S0 . v + C : Abar.  Per node there remain A^T mvb
+            // (for the x adjoint) and the value of the node's contribution,
+            //   inner = mb mp + mvb . (mp v + A dpos) = mb mp + mvb . u + dx (A^T mvb) . o,
+            // with u = mp v - dx A r.
+            float S0[D], T[D][D], u[D], mbs = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                vb[i] = 0.0f;
+                S0[i] = 0.0f;
+                float ar = 0.0f;
 #pragma unroll
-                for (int j = 0; j < D; ++j) Ab[i][j] = 0.0f;
+                for (int j = 0; j < D; ++j) {
+                    T[i][j] = 0.0f;
+                    ar += A[i][j] * s.r[j];
+                }
+                u[i] = mp * v[i] - P.dx * ar;
             }
             const float4* __restrict__ gi = (FUSE ? a.accP : a.gadj) + (long long)inst * P.nodes;
             const float4* __restrict__ vbi = FUSE ? a.VbarIn + (long long)inst * P.nodes : nullptr;
+            const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
+            if (box.use)
+                stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
+                    const float4 g = __ldg(gi + node);
+                    if (!FUSE) return g;
+                    // grid adjoint (reverse of Eq. 16-18) once per node
+                    float mv[D], vbv[D], mbv, mvb[D];
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                    unpack3<D>(__ldg(vbi + node), vbv);
+                    grid_velocity_adjoint<D>(P, c, g.x, mv, vbv, mbv, mvb);
+                    return make_float4(mbv, mvb[0], mvb[1], D == 3 ? mvb[D - 1] : 0.0f);
+                });
 #pragma unroll
             for (int k = 0; k < stencil_size<D>(); ++k) {
                 NodeTerm<D> t;
                 node_term<D>(s, k, P, t);
-                float4 g = __ldg(gi + t.node);
+                float4 g;
                 float mvb[D];
-                if (FUSE) {
+                if (box.use) {
+                    g = sm[box_slot<D>(box, t.c)];
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
+                } else if (FUSE) {
+                    g = __ldg(gi + t.node);
                     // grid adjoint (reverse of Eq. 16-18) of this node, on the fly
                     float mv[D], vbv[D], mbv;
                     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
@@ -305,34 +360,45 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     grid_velocity_adjoint<D>(P, t.c, g.x, mv, vbv, mbv, mvb);
                     g.x = mbv;
                 } else {
+                    g = __ldg(gi + t.node);
                     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
                 }
-                // value of this node's contribution: w * (mb mp + mvb . (mp v + A dpos))
-                float inner = g.x * mp, vcd = 0.0f;
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    float ad = 0.0f, cd = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        ad += A[i][j] * t.dpos[j];
-                        cd += Cn[i][j] * t.dpos[j];
-                    }
-                    inner += mvb[i] * (mp * v[i] + ad);
-                    vcd += mvb[i] * (v[i] + cd);
-                }
-                mpb += t.w * (g.x + vcd);
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    vb[i] += t.w * mp * mvb[i];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) Ab[i][j] += t.w * mvb[i] * t.dpos[j];
-                }
+                float atm[D], ao = 0.0f, inner = g.x * mp;
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    float atm = 0.0f;
+                    atm[c] = 0.0f;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) atm += A[i][c] * mvb[i];
-                    xb[c] += t.gw[c] * inner - t.w * atm;
+                    for (int i = 0; i < D; ++i) atm[c] += A[i][c] * mvb[i];
+                    const int o = stencil_offset<D>(k, c);
+                    if (o == 1) ao += atm[c];
+                    else if (o == 2) ao += 2.0f * atm[c];
+                    inner += mvb[c] * u[c];
+                }
+                inner += P.dx * ao;
+                mbs += t.w * g.x;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float wm = t.w * mvb[i];
+                    S0[i] += wm;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const int o = stencil_offset<D>(k, j);
+                        if (o == 1) T[i][j] += wm;
+                        else if (o == 2) T[i][j] += 2.0f * wm;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < D; ++c) xb[c] += t.gw[c] * inner - t.w * atm[c];
+            }
+            float Ab[D][D], mpb = mbs;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                vb[i] = mp * S0[i];
+                mpb += S0[i] * v[i];
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    Ab[i][j] = P.dx * (T[i][j] - S0[i] * s.r[j]);
+                    mpb += Cn[i][j] * Ab[i][j];
                 }
             }
             // A = mp C - sc P F^T
@@ -416,32 +482,57 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
             }
         const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
         float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
+        const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
+        if (box.use)
+            stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
+                const float4 g = __ldg(Vi + node);
+                if (!FUSE_V) return g;
+                float mv[D], gv[D];
+                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                grid_velocity<D>(P, c, g.x, mv, gv);  // Eq. 16-18 once per node
+                return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
+            });
+        // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T), factored
+        // with dpos = (o - r) dx: the node's velocity adjoint is
+        //   w (vt + kappa Ct dpos) = w (q + kappa dx Ct o),  q = vt - kappa dx Ct r
+        float q[D];
+        const float kdx = P.kappa * P.dx;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float cr = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) cr += Ct[i][j] * s.r[j];
+            q[i] = vt[i] - kdx * cr;
+        }
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
             NodeTerm<D> t;
             node_term<D>(s, k, P, t);
             float gv[D];
-            node_velocity<D, FUSE_V>(Vi, t, P, gv);
-            // Eq. 19-20 reversed: v' = sum w V, C' = kappa sum w V dpos^T
-            float vdot = 0.0f, vcd = 0.0f, cd[D];
+            if (box.use) unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
+            else node_velocity<D, FUSE_V>(Vi, t, P, gv);
+            float sv[D], dot = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                cd[i] = 0.0f;
+                float co = 0.0f;  // (Ct o)_i
 #pragma unroll
-                for (int j = 0; j < D; ++j) cd[i] += Ct[i][j] * t.dpos[j];
-                vdot += gv[i] * vt[i];
-                vcd += gv[i] * cd[i];
+                for (int j = 0; j < D; ++j) {
+                    const int o = stencil_offset<D>(k, j);
+                    if (o == 1) co += Ct[i][j];
+                    else if (o == 2) co += 2.0f * Ct[i][j];
+                }
+                sv[i] = q[i] + kdx * co;
+                dot += gv[i] * sv[i];  // gv . (vt + kappa Ct dpos)
             }
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 float ctv = 0.0f;
 #pragma unroll
                 for (int i = 0; i < D; ++i) ctv += Ct[i][c] * gv[i];
-                xb[c] += t.gw[c] * (vdot + P.kappa * vcd) - P.kappa * t.w * ctv;
+                xb[c] += t.gw[c] * dot - P.kappa * t.w * ctv;
             }
-            float sv[D];
 #pragma unroll
-            for (int i = 0; i < D; ++i) sv[i] = t.w * (vt[i] + P.kappa * cd[i]);
+            for (int i = 0; i < D; ++i) sv[i] *= t.w;
             float4 c4 = make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f);
             atomicAdd(Vbi + t.node, c4);
         }

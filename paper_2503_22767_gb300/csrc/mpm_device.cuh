@@ -31,6 +31,7 @@ struct Params {
     float gravity[3];
     int pdl;  // per-substep kernels launched with programmatic dependent launch
     int adj_blocks;  // register budget of the adjoint particle kernel: 256-thread blocks per SM (2 or 3)
+    int box;         // 1: warps stage their stencil nodes in shared memory before gathering
 };
 
 // Programmatic dependent launch: a kernel launched with programmatic stream

@@ -425,6 +425,7 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     for (int i = 0; i < 3; ++i) P.gravity[i] = (float)c->gravity[i];
     P.pdl = 1;
     P.adj_blocks = 2;
+    P.box = 1;
 
     const long long S = (long long)h->ncomp * h->np;
     const int d = h->dim;
@@ -1274,6 +1275,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (h->tile != (value == 1)) drop_graphs(h);
             h->tile = value == 1;
             return MPM_OK;
+        case MPM_OPT_WARP_BOX:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "warp box must be 0 or 1");
+            if (h->P.box != (int)value) drop_graphs(h);
+            h->P.box = (int)value;
+            return MPM_OK;
         case MPM_OPT_ADJOINT_BLOCKS:
             if (value != 2 && value != 3) return fail(h, MPM_ERR_ARG, "adjoint blocks must be 2 or 3");
             if (h->P.adj_blocks != (int)value) drop_graphs(h);
@@ -1321,6 +1327,7 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_STREAMS: *value = h->two_streams ? 2 : 1; return MPM_OK;
         case MPM_OPT_PDL: *value = h->P.pdl; return MPM_OK;
         case MPM_OPT_ADJOINT_BLOCKS: *value = h->P.adj_blocks; return MPM_OK;
+        case MPM_OPT_WARP_BOX: *value = h->P.box; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

@@ -1,0 +1,112 @@
+// Warp-cooperative staging of grid nodes for the particle gathers (G2P,
+// P2G^T, G2P^T).
+//
+// The 32 cell-sorted particles of a warp have base cells in a small box: the
+// sort orders cells block by block, with the last axis fastest.  A warp
+// typically holds one row of 4 (3D) or 8 (2D) cells, so its 27- / 9-node
+// stencils touch ~54 / ~30 distinct nodes instead of 864 / 288 node reads.
+// The warp loads the box's nodes once into its own shared-memory slots, four
+// float4 loads per lane that are all in flight together.  Each lane then reads
+// its stencil from shared memory.  A thread otherwise pays one L2 round trip
+// per few gathers, limited by the registers that in-flight loads need.
+//
+// The box has a fixed shape of 2^box_log(a) nodes per axis, 128 nodes in all:
+// 8 x 16 in 2D and 4 x 4 x 8 in 3D.  A warp whose stencils do not fit it, or
+// whose particles belong to more than one instance, gathers directly from
+// global memory, with the same results.
+#pragma once
+
+#include <climits>
+
+#include "mpm_device.cuh"
+
+namespace mpm {
+
+template <int D>
+__host__ __device__ constexpr int box_log(int a) {
+    return D == 2 ? (a == 0 ? 3 : 4) : (a == D - 1 ? 3 : 2);
+}
+
+template <int D>
+__host__ __device__ constexpr int box_nodes() {
+    return 128;
+}
+
+constexpr int kBoxWarps = 8;  // warps per block (blocks of at most 256 threads)
+
+template <int D>
+struct WarpBox {
+    int lo[D];   // first node per axis
+    int ext[D];  // nodes per axis that some stencil of the warp touches
+    int inst;    // instance of every active lane (when use)
+    bool use;    // warp-uniform: stage the box, else gather directly
+};
+
+// With enable, every lane of the warp must call this (base cells of active
+// lanes count).  enable must be warp-uniform; without it nothing is exchanged
+// and the box is not used, so a partly active warp may call it inside a branch.
+template <int D>
+__device__ __forceinline__ WarpBox<D> warp_box(const int (&base)[D], bool active, int inst, bool enable) {
+    const unsigned full = 0xffffffffu;
+    WarpBox<D> b;
+    b.use = false;
+    b.inst = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) b.lo[a] = b.ext[a] = 0;
+    if (!enable) return b;
+    bool fit = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int lo = __reduce_min_sync(full, active ? base[a] : INT_MAX);
+        const int hi = __reduce_max_sync(full, active ? base[a] : INT_MIN);
+        const bool any = lo <= hi;
+        b.lo[a] = any ? lo : 0;
+        b.ext[a] = any ? hi - lo + 3 : 0;
+        fit = fit && any && b.ext[a] <= (1 << box_log<D>(a));
+    }
+    const int i0 = __reduce_min_sync(full, active ? inst : INT_MAX);
+    const int i1 = __reduce_max_sync(full, active ? inst : INT_MIN);
+    b.inst = i0;
+    b.use = fit && i0 == i1;
+    return b;
+}
+
+// Slot of node coordinates c in the box (c inside the box).
+template <int D>
+__device__ __forceinline__ int box_slot(const WarpBox<D>& b, const int (&c)[D]) {
+    int i = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) i = (i << box_log<D>(a)) | (c[a] - b.lo[a]);
+    return i;
+}
+
+// Every lane of the warp: fill this warp's slots `sm` with load(c, node) for
+// the box nodes inside the touched extent.  node is the index within the
+// instance grid.  The other slots are left as they are and never read.
+template <int D, typename Load>
+__device__ __forceinline__ void stage_box(const WarpBox<D>& b, int res, float4* sm, Load load) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();  // earlier reads of these slots are done
+#pragma unroll
+    for (int t0 = 0; t0 < box_nodes<D>(); t0 += 32) {
+        const int t = t0 + lane;
+        int c[D], rem = t;
+        bool in = true;
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+            const int r = rem & ((1 << box_log<D>(a)) - 1);
+            rem >>= box_log<D>(a);
+            c[a] = b.lo[a] + r;
+            in = in && r < b.ext[a];
+        }
+        if (in) {
+            int node = 0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) node = node * res + c[a];
+            sm[t] = load(c, node);
+        }
+    }
+    __syncwarp();
+}
+
+}  // namespace mpm

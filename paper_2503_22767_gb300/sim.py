@@ -179,7 +179,7 @@ class Simulator:
         for name, key in (("block", B.MPM_OPT_BLOCK), ("fuse_grid", B.MPM_OPT_FUSE_GRID),
                           ("tile", B.MPM_OPT_TILE), ("graphs", B.MPM_OPT_GRAPHS),
                           ("streams", B.MPM_OPT_STREAMS), ("pdl", B.MPM_OPT_PDL),
-                          ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS)):
+                          ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS), ("warp_box", B.MPM_OPT_WARP_BOX)):
             v = ctypes.c_longlong()
             self._check(self.lib.mpm_get_option(self.handle, key, ctypes.byref(v)), "mpm_get_option")
             out[name] = v.value

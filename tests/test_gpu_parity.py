@@ -317,11 +317,11 @@ def test_execution_modes(key, fuse, graphs, tile):
     """Grid operation fused into the particle kernels or not, passes replayed
     as CUDA graphs or launched directly, shared-memory tiles or direct global
     transfers, one or two streams, PDL on or off, either adjoint register
-    budget: same results, twice in a row."""
+    budget, warp-staged or direct gathers: same results, twice in a row."""
     w, of, ob = _oracle(key)
     sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs, B.MPM_OPT_TILE: tile,
                 B.MPM_OPT_STREAMS: 1 + (fuse + graphs + tile) % 2, B.MPM_OPT_PDL: (fuse + tile) % 2,
-                B.MPM_OPT_ADJOINT_BLOCKS: 2 + (fuse + graphs) % 2}
+                B.MPM_OPT_ADJOINT_BLOCKS: 2 + (fuse + graphs) % 2, B.MPM_OPT_WARP_BOX: (fuse + graphs + 1) % 2}
     for _ in range(2):
         g = run_gpu(w, options=sim_opts)
         assert_state(g, of, w)
