@@ -214,10 +214,10 @@ enum {
                            resident 256-thread blocks per SM: 2 (default, <= 128 registers)
                            or 3 (<= 80 registers: more warps to hide gather latency, at the
                            cost of spills) */
-    MPM_OPT_WARP_BOX = 9 /* 1 (default): in the direct particle kernels, each fully active
-                           warp whose stencils fit a 128-node box loads that box into shared
-                           memory once, and its gathers read from there; 0: every gather
-                           reads global memory */
+    MPM_OPT_WARP_BOX = 9 /* 1 (default in 3D): in the direct particle kernels, each fully
+                           active warp whose stencils fit a 128-node box loads that box into
+                           shared memory once, and its gathers read from there; 0 (default
+                           in 2D): every gather reads global memory */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);
@@ -229,8 +229,8 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value);
  * library).  Times forward + backward passes over the first sample_substeps
  * substeps (0 = two checkpoint segments) of the inputs staged by the last
  * mpm_forward, for every combination of block size {64, 128, 256}, grid
- * fusion {0, 1, 3} and adjoint register budget {2, 3} (tiles off), and keeps
- * the fastest.  With a
+ * fusion {0, 1}, adjoint register budget {2, 3} and warp-staged gathers
+ * {0, 1} (tiles off), and keeps the fastest.  With a
  * non-NULL cache_path, results are read from and written to that JSON file,
  * keyed by dim, grid_res, particle count (rounded up to a power of 2),
  * instances and checkpoint interval; a cache hit applies the stored choice

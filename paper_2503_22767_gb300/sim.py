@@ -166,7 +166,7 @@ class Simulator:
         return keys, perm
 
     def autotune(self, cache_path=None, sample_substeps=0):
-        """Pick block size, grid fusion and the adjoint register budget by timing them on the inputs
+        """Pick block size, grid fusion, the adjoint register budget and warp-staged gathers by timing them on the inputs
         of the last forward (see mpm_autotune); returns the chosen options.
         The forward result is overwritten: run forward again afterwards."""
         path = cache_path.encode() if cache_path else None

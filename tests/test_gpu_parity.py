@@ -374,6 +374,7 @@ def test_autotune_picks_and_caches(tmp_path):
     (entry,) = entries.values()
     assert entry["block"] == chosen["block"] and entry["tile"] == chosen["tile"]
     assert entry["adj"] == chosen["adjoint_blocks"] and entry["adj"] in (2, 3)
+    assert entry["box"] == chosen["warp_box"] and entry["fuse"] in (0, 1)
     with pytest.raises(B.MpmError):  # the tuning runs invalidated the forward result
         sim.backward(torch.ones(1, device="cuda"))
     loss, x = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), want_x=True)
