@@ -28,8 +28,19 @@ STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_CUDA", -3: "MPM_ERR
 EXPORTS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_forward", "mpm_backward",
            "mpm_forward_host", "mpm_backward_host", "mpm_read_state", "mpm_sort_particles",
            "mpm_set_option", "mpm_get_option", "mpm_autotune", "mpm_get_stats", "mpm_reset_stats",
-           "mpm_substep_noalloc"]
+           "mpm_substep_noalloc",
+           # design maps and optimiser step (mpm_design.h)
+           "mpm_design_create", "mpm_design_destroy", "mpm_design_last_error", "mpm_design_forward",
+           "mpm_design_backward", "mpm_adam_step"]
 MPM_NOALLOC_MAX_NODES = 262144
+
+
+class mpm_design_config(ctypes.Structure):
+    """Mirror of mpm_design_config (include/mpm_design.h)."""
+    _fields_ = [("dim", c_int), ("n_particles", c_int), ("n_regions", c_int), ("n_tasks", c_int),
+                ("n_steps", c_int), ("dt", ctypes.c_double), ("filter_radius", ctypes.c_double),
+                ("Br_max", ctypes.c_double), ("B_max", ctypes.c_double), ("f_min", ctypes.c_double),
+                ("f_max", ctypes.c_double), ("delta", ctypes.c_double)]
 
 
 class mpm_config(ctypes.Structure):
@@ -93,6 +104,14 @@ def load():
             "mpm_get_stats": ([H, ctypes.POINTER(mpm_stats)], c_int),
             "mpm_reset_stats": ([H], c_int),
             "mpm_substep_noalloc": ([ctypes.POINTER(mpm_config), c_int, pf, pf, pf, pf, pf, vp], c_int),
+            "mpm_design_create": ([ctypes.POINTER(mpm_design_config), pf, pi, ctypes.POINTER(c_void_p), vp],
+                                  c_int),
+            "mpm_design_destroy": ([H], c_int),
+            "mpm_design_last_error": ([H], ctypes.c_char_p),
+            "mpm_design_forward": ([H, ctypes.c_float, pf, pf, pf, pf, pf, pf, pf, pf, pf, vp], c_int),
+            "mpm_design_backward": ([H, pf, pf, pf, pf, pf, pf, pf, pf, pf, vp], c_int),
+            "mpm_adam_step": ([c_longlong, pf, pf, pf, pf, c_int, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp], c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

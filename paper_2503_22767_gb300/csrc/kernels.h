@@ -109,6 +109,9 @@ struct SortBuffers {
     long long n_keys = 0;
 };
 long long sort_key_space(int dim, int res, int n_inst);
+// exclusive prefix sum of n ints (in == out allowed); tmp holds
+// sort_scan_tmp_len(n) ints
+cudaError_t launch_scan_exclusive(const int* in, int* out, long long n, int* tmp, cudaStream_t st);
 long long sort_scan_tmp_len(long long n_keys);
 // keys, stable permutation perm[new] = old for positions x (component stride
 // xstride); flags kErrDomain for stencils outside the grid (keys clamp).

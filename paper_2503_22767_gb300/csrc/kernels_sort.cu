@@ -142,6 +142,10 @@ cudaError_t scan_exclusive(const int* in, int* out, long long n, int* tmp, cudaS
 
 }  // namespace
 
+cudaError_t launch_scan_exclusive(const int* in, int* out, long long n, int* tmp, cudaStream_t st) {
+    return scan_exclusive(in, out, n, tmp, st);
+}
+
 long long sort_key_space(int dim, int res, int n_inst) {
     int bs = dim == 2 ? 8 : 4;
     long long nb = (res + bs - 1) / bs, per = 1;

@@ -10,13 +10,16 @@ from paper_2503_22767_gb300 import binding as B
 from paper_2503_22767_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "mpm.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 def _declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mpm_\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mpm_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -44,17 +47,21 @@ def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "layout.c"
     fields = [f[0] for f in B.mpm_config._fields_]
     sfields = [f[0] for f in B.mpm_stats._fields_]
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpm.h"', "int main(void) {"]
+    dfields = [f[0] for f in B.mpm_design_config._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpm_design.h"', "int main(void) {"]
     lines += [f'printf("%zu\\n", offsetof(mpm_config, {f}));' for f in fields]
     lines += ['printf("%zu\\n", sizeof(mpm_config));']
     lines += [f'printf("%zu\\n", offsetof(mpm_stats, {f}));' for f in sfields]
-    lines += ['printf("%zu\\n", sizeof(mpm_stats));', "return 0; }"]
+    lines += ['printf("%zu\\n", sizeof(mpm_stats));']
+    lines += [f'printf("%zu\\n", offsetof(mpm_design_config, {f}));' for f in dfields]
+    lines += ['printf("%zu\\n", sizeof(mpm_design_config));', "return 0; }"]
     src.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     assert os.system(f"gcc -I {ROOT}/include -o {exe} {src}") == 0
     got = [int(v) for v in os.popen(str(exe)).read().split()]
     want = [getattr(B.mpm_config, f).offset for f in fields] + [ctypes.sizeof(B.mpm_config)]
     want += [getattr(B.mpm_stats, f).offset for f in sfields] + [ctypes.sizeof(B.mpm_stats)]
+    want += [getattr(B.mpm_design_config, f).offset for f in dfields] + [ctypes.sizeof(B.mpm_design_config)]
     assert got == want
 
 
@@ -105,3 +112,40 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.mpm_destroy(None) == B.MPM_ERR_ARG
     assert lib.mpm_set_option(None, 1, 1) == B.MPM_ERR_ARG
     assert lib.mpm_last_error(None) == b"null handle"
+
+
+def _dcfg(**kw):
+    c = B.mpm_design_config()
+    c.dim, c.n_particles, c.n_regions, c.n_tasks, c.n_steps = 2, 0, 0, 1, 10
+    c.dt, c.filter_radius, c.Br_max, c.B_max, c.f_min, c.f_max, c.delta = 1e-4, 0.02, 0.1, 0.02, 1.0, 10.0, 1e-6
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+@pytest.mark.parametrize("field,value", [("dim", 1), ("n_tasks", 0), ("n_steps", 0), ("dt", 0.0),
+                                         ("filter_radius", 0.0), ("delta", -1.0), ("f_max", 0.5),
+                                         ("n_particles", -1)])
+def test_design_create_rejects_bad_config_on_host(lib, field, value):
+    h = ctypes.c_void_p()
+    c = _dcfg(**{field: value})
+    assert lib.mpm_design_create(ctypes.byref(c), None, None, ctypes.byref(h), None) == B.MPM_ERR_ARG
+    assert not h.value
+
+
+def test_design_create_needs_region_exactly_with_regions(lib):
+    h = ctypes.c_void_p()
+    c = _dcfg(n_regions=4)
+    assert lib.mpm_design_create(ctypes.byref(c), None, None, ctypes.byref(h), None) == B.MPM_ERR_ARG
+
+
+def test_design_and_adam_null_arguments_fail_cleanly(lib):
+    assert lib.mpm_design_destroy(None) == B.MPM_ERR_ARG
+    assert lib.mpm_design_forward(None, 1.0, *([None] * 10)) == B.MPM_ERR_ARG
+    assert lib.mpm_design_backward(None, *([None] * 10)) == B.MPM_ERR_ARG
+    assert lib.mpm_design_last_error(None) == b"null handle"
+    assert lib.mpm_adam_step(-1, None, None, None, None, 1, 0.1, 0.9, 0.999, 1e-8, 0.0, 1.0, None) == B.MPM_ERR_ARG
+    assert lib.mpm_adam_step(4, None, None, None, None, 1, 0.1, 0.9, 0.999, 1e-8, 0.0, 1.0, None) == B.MPM_ERR_ARG
+    assert lib.mpm_adam_step(0, None, None, None, None, 0, 0.1, 0.9, 0.999, 1e-8, 0.0, 1.0, None) == B.MPM_ERR_ARG
+    assert lib.mpm_adam_step(0, None, None, None, None, 1, 0.1, 0.9, 0.999, 1e-8, 1.0, 0.0, None) == B.MPM_ERR_ARG
+    assert lib.mpm_adam_step(0, None, None, None, None, 1, 0.1, 0.9, 0.999, 1e-8, 0.0, 1.0, None) == B.MPM_OK
