@@ -33,9 +33,13 @@ namespace {
 template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE>
 __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
-    pdl_wait();
-    pdl_trigger();
-    if (FUSE) clear_buffer(a);
+    // Early loads: with the grid operation in its own kernel, this kernel's
+    // predecessor is that grid kernel, which writes none of the particle
+    // arrays read first here.  Every kernel of the chain waits before it
+    // triggers its dependents, so when this kernel starts, the particle
+    // kernel before the grid kernel has completed, and the state loads can
+    // overlap the grid kernel's tail.
+    constexpr bool kEarly = G2P && !FUSE;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
@@ -43,7 +47,7 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
     int flags = 0;
     float x[D], v[D], C[D][D], F[D][D];
     float phi = 0.0f, mp = 0.0f;
-    if (active) {
+    auto load_state = [&]() {
         load_vec<D>(a.s_in, L::X, np, p, x);
         load_mat<D>(a.s_in, L::F, np, p, F);
         phi = a.phi[p];
@@ -52,7 +56,12 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
             load_vec<D>(a.s_in, L::V, np, p, v);
             load_mat<D>(a.s_in, L::C, np, p, C);
         }
-    }
+    };
+    if (kEarly && active) load_state();
+    pdl_wait();
+    pdl_trigger();
+    if (FUSE) clear_buffer(a);
+    if (!kEarly && active) load_state();
     if (G2P) {
         float mom_x[1] = {0.0f};
         Stencil<D> s;
@@ -257,36 +266,48 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
 template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     using L = Layout<D>;
-    pdl_wait();
-    pdl_trigger();
-    clear_buffer(a);
+    // Early loads as in k_forward: the fused kernel without grid-adjoint
+    // fusion follows the grid adjoint kernel, which writes none of the
+    // particle arrays of state n, the partial adjoint or the design.
+    constexpr bool kEarly = P2GT && G2PT && !FUSE;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
     const long long np = P.np;
     int flags = 0;
+    // adjoint of the state between the two halves (state n if P2GT)
+    float xb[D], vb[D], Cb[D][D], Fb[D][D];
+    float Cn[D][D];  // C of state n (= m+1), needed by G2P^T
+    float x_n[D], v_n[D], F_n[D][D], phi_n = 0.0f;  // state n and design (P2G^T)
+    auto load_state_n = [&]() {
+        load_vec<D>(a.s_in, L::X, np, p, x_n);
+        load_vec<D>(a.s_in, L::V, np, p, v_n);
+        load_mat<D>(a.s_in, L::C, np, p, Cn);
+        load_mat<D>(a.s_in, L::F, np, p, F_n);
+        load_vec<D>(a.adj, L::X, np, p, xb);
+        load_mat<D>(a.adj, L::F, np, p, Fb);
+        phi_n = a.phi[p];
+    };
+    if (kEarly && active) load_state_n();
+    pdl_wait();
+    pdl_trigger();
+    clear_buffer(a);
+    if (P2GT && !kEarly && active) load_state_n();
     // warps with every lane active may stage their stencil nodes (the staging
     // runs inside the per-particle branches)
     const bool full_warp = __ballot_sync(0xffffffffu, active) == 0xffffffffu;
     __shared__ float4 s_box[kBoxWarps * box_nodes<D>()];
     float4* sm = s_box + (threadIdx.x >> 5) * box_nodes<D>();
-    // adjoint of the state between the two halves (state n if P2GT)
-    float xb[D], vb[D], Cb[D][D], Fb[D][D];
-    float Cn[D][D];  // C of state n (= m+1), needed by G2P^T
     float bab[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) bab[i] = 0.0f;
     if (P2GT) {
         if (active) {
             const int n = a.n_p2g;
-            float x[D], v[D], F[D][D];
-            load_vec<D>(a.s_in, L::X, np, p, x);
-            load_vec<D>(a.s_in, L::V, np, p, v);
-            load_mat<D>(a.s_in, L::C, np, p, Cn);
-            load_mat<D>(a.s_in, L::F, np, p, F);
-            load_vec<D>(a.adj, L::X, np, p, xb);
-            load_mat<D>(a.adj, L::F, np, p, Fb);
-            const float phi = a.phi[p];
+            float(&x)[D] = x_n;
+            float(&v)[D] = v_n;
+            float(&F)[D][D] = F_n;
+            const float phi = phi_n;
             const float mp = phi * P.rho0 * P.p_vol;
             float Br[D], Ba[D], Pk[D][D], A[D][D];
 #pragma unroll
