@@ -58,8 +58,9 @@ typedef enum {
  *   dim, grid_res     2 or 3; res nodes per axis, dx = 1/res, node i at i*dx.
  *   dt, n_steps       substep size and horizon N.
  *   n_instances, n_particles
- *                     independent simulations and their particle counts (host
- *                     array [n_instances]); each instance has its own grid.
+ *                     independent simulations (1..65535) and their particle
+ *                     counts (host array [n_instances]); each instance has its
+ *                     own grid.
  *   n_designs, design_of_instance
  *                     topology phi and magnetisation B~_r are given per design;
  *                     instance i uses design design_of_instance[i] (host array,

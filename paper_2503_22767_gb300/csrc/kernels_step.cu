@@ -214,38 +214,54 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
 // ---------------------------------------------------------------------------
 // grid operation (Eq. 16-18)
 // ---------------------------------------------------------------------------
+// One block row per instance (blockIdx.y), so node indices stay 32-bit.
+// Nodes without mass (most of a 3D grid) take the short path: Eq. 16 gives
+// them no velocity, and the reverse gives them no gradient.
 template <int D>
 __global__ void __launch_bounds__(256) k_grid(Params P, float4* __restrict__ acc,
                                               float4* __restrict__ V, float4* __restrict__ acc_next,
-                                              bool clear_acc, long long total) {
+                                              bool clear_acc) {
     pdl_wait();
     pdl_trigger();
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    float4 g = acc[i];
+    const int local = blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= P.nodes) return;
+    const long long i = (long long)blockIdx.y * P.nodes + local;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 g = acc[i];
+    if (clear_acc) acc[i] = zero;
+    if (acc_next) acc_next[i] = zero;
+    if (!(g.x > 0.0f)) {
+        V[i] = zero;
+        return;
+    }
     int c[D];
-    node_coords<D>(i % P.nodes, P.res, c);
+    node_coords<D>(local, P.res, c);
     float mv[D], v[D];
     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
     grid_velocity<D>(P, c, g.x, mv, v);
     V[i] = make_float4(v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f, 0.0f);
-    if (clear_acc) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (acc_next) acc_next[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 template <int D>
 __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __restrict__ acc,
                                                       float4* __restrict__ Vbar,
-                                                      float4* __restrict__ gadj, long long total) {
+                                                      float4* __restrict__ gadj) {
     pdl_wait();
     pdl_trigger();
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    float4 g = acc[i];
-    float4 vb4 = Vbar[i];
-    Vbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int local = blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= P.nodes) return;
+    const long long i = (long long)blockIdx.y * P.nodes + local;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 g = acc[i];
+    if (!(g.x > 0.0f)) {
+        Vbar[i] = zero;
+        gadj[i] = zero;
+        return;
+    }
+    const float4 vb4 = Vbar[i];
+    Vbar[i] = zero;
     int c[D];
-    node_coords<D>(i % P.nodes, P.res, c);
+    node_coords<D>(local, P.res, c);
     float mv[D], vb[D], mvb[D], mb;
     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
     unpack3<D>(vb4, vb);
@@ -798,18 +814,16 @@ cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, bool fuse_v
 
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,
                         bool clear_acc, cudaStream_t st) {
-    long long total = P.nodes * P.n_inst;
-    dim3 grid(blocks_for(total, 256));
-    if (dim == 2) return launch_chain(P, k_grid<2>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc, total);
-    return launch_chain(P, k_grid<3>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc, total);
+    dim3 grid(blocks_for(P.nodes, 256), P.n_inst);
+    if (dim == 2) return launch_chain(P, k_grid<2>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc);
+    return launch_chain(P, k_grid<3>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc);
 }
 
 cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, float4* Vbar,
                                 float4* gadj, cudaStream_t st) {
-    long long total = P.nodes * P.n_inst;
-    dim3 grid(blocks_for(total, 256));
-    if (dim == 2) return launch_chain(P, k_grid_adjoint<2>, grid, dim3(256), st, P, acc, Vbar, gadj, total);
-    return launch_chain(P, k_grid_adjoint<3>, grid, dim3(256), st, P, acc, Vbar, gadj, total);
+    dim3 grid(blocks_for(P.nodes, 256), P.n_inst);
+    if (dim == 2) return launch_chain(P, k_grid_adjoint<2>, grid, dim3(256), st, P, acc, Vbar, gadj);
+    return launch_chain(P, k_grid_adjoint<3>, grid, dim3(256), st, P, acc, Vbar, gadj);
 }
 
 cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0, float* s,

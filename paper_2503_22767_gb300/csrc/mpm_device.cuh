@@ -327,10 +327,10 @@ __device__ __forceinline__ void piola_adjoint(const float (&E)[D][D], float phi,
 // projects it: Coulomb friction on the floor in wall mode 1, otherwise v = 0.
 // ---------------------------------------------------------------------------
 template <int D>
-__device__ __forceinline__ void node_coords(long long local, int res, int (&c)[D]) {
+__device__ __forceinline__ void node_coords(int local, int res, int (&c)[D]) {
 #pragma unroll
     for (int a = D - 1; a >= 0; --a) {
-        c[a] = (int)(local % res);
+        c[a] = local % res;
         local /= res;
     }
 }

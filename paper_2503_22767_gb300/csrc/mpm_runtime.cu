@@ -331,6 +331,7 @@ int validate(const mpm_config* c, std::string& why) {
     if (!(c->dt > 0.0) || !std::isfinite(c->dt)) { why = "dt must be > 0"; return MPM_ERR_ARG; }
     if (c->n_steps < 1) { why = "n_steps must be >= 1"; return MPM_ERR_ARG; }
     if (c->n_instances < 1 || !c->n_particles) { why = "need n_instances >= 1 and n_particles"; return MPM_ERR_ARG; }
+    if (c->n_instances > 65535) { why = "at most 65535 instances (one grid row of blocks each)"; return MPM_ERR_ARG; }
     if (!(c->E > 0.0) || !(c->nu >= 0.0 && c->nu < 0.5) || !(c->rho0 > 0.0) || !(c->p_vol > 0.0)) {
         why = "need E > 0, 0 <= nu < 0.5, rho0 > 0, p_vol > 0";
         return MPM_ERR_ARG;
