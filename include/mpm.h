@@ -226,6 +226,42 @@ int mpm_set_option(mpm_handle* h, int key, long long value);
 int mpm_get_option(const mpm_handle* h, int key, long long* value);
 
 /*
+ * Solid boundaries beyond the walls (Eq. 18 in general form): obstacles, and
+ * clamps or holders attached to the material, static or moving.  Each box is
+ * axis-aligned, given at t = 0 in domain units (lo <= hi on every used axis).
+ * A grid node inside a box lies on its nearest face, whose outward normal is
+ * n_b.  The box may move: motion gives per box and substep its offset from
+ * the t = 0 position and its velocity v_b.  Per kind:
+ *   MPM_BOUNDARY_COULOMB   when (v - v_b) . n_b < 0, the normal part of v
+ *                          becomes v_b's and the tangential part of v - v_b
+ *                          shrinks by mu |(v - v_b) . n_b|, to zero at most;
+ *   MPM_BOUNDARY_NONSLIP   when (v - v_b) . n_b < 0, v = v_b (mu -> infinity);
+ *   MPM_BOUNDARY_ATTACHED  v = v_b always (material attached to the box).
+ * Boxes act after the walls, in the given order.  The reverse mode replays
+ * them.  Components they overwrite pass no gradient.
+ */
+#define MPM_MAX_BOUNDARIES 8
+enum { MPM_BOUNDARY_COULOMB = 0, MPM_BOUNDARY_NONSLIP = 1, MPM_BOUNDARY_ATTACHED = 2 };
+typedef struct {
+    int kind;     /* MPM_BOUNDARY_* */
+    float mu;     /* friction coefficient (MPM_BOUNDARY_COULOMB) */
+    float lo[3];  /* box corners at t = 0 (entries past dim are ignored) */
+    float hi[3];
+} mpm_boundary;
+
+/*
+ * Replace the solid boxes with boxes[0 .. n) (host array, read during the
+ * call).  n = 0 removes them.  motion is a device array [n][n_steps][2][dim]
+ * (offset, then v_b, at t_n = n dt), or NULL for static boxes (offset and
+ * v_b zero).  It is copied into storage that mpm_create allocated.  The call
+ * synchronises cuda_stream.  A following mpm_backward needs a new
+ * mpm_forward first.
+ * Errors: MPM_ERR_ARG (n outside [0, MPM_MAX_BOUNDARIES], unknown kind,
+ * negative or non-finite mu, lo > hi), MPM_ERR_CUDA.
+ */
+int mpm_set_boundaries(mpm_handle* h, int n, const mpm_boundary* boxes, const float* motion, void* cuda_stream);
+
+/*
  * Autotuner (not in the paper; a launch-configuration search of this
  * library).  Times forward + backward passes over the first sample_substeps
  * substeps (0 = two checkpoint segments) of the inputs staged by the last

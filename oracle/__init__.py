@@ -38,6 +38,8 @@ class Params(ctypes.Structure):
         ("rho0", ctypes.c_double), ("p_vol", ctypes.c_double), ("simp_eps", ctypes.c_double),
         ("damping", ctypes.c_double), ("floor_mu", ctypes.c_double),
         ("gravity", ctypes.c_double * 3),
+        ("n_bnd", ctypes.c_int), ("pad2_", ctypes.c_int),
+        ("bnd", ctypes.c_void_p), ("bmotion", ctypes.c_void_p),
     ]
 
 
@@ -108,8 +110,10 @@ def _ip(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
 
 
-def params(cfg, n_steps=None) -> Params:
-    """Oracle parameter block from an ``MpmConfig``-like object."""
+def params(cfg, n_steps=None, w=None) -> Params:
+    """Oracle parameter block from an ``MpmConfig``-like object (and the
+    workload's box motion, if any).  The arrays the block points to are
+    kept on it."""
     p = Params()
     p.dim, p.res = int(cfg.dim), int(cfg.res)
     p.n_steps = int(cfg.n_steps if n_steps is None else n_steps)
@@ -121,6 +125,23 @@ def params(cfg, n_steps=None) -> Params:
     g = list(cfg.gravity) + [0.0] * 3
     for i in range(3):
         p.gravity[i] = float(g[i])
+    boxes = getattr(cfg, "boundaries", None) or []
+    p.n_bnd = len(boxes)
+    if boxes:
+        arr = np.zeros((len(boxes), 8))
+        for b, (kind, mu, lo, hi) in enumerate(boxes):
+            arr[b, 0], arr[b, 1] = kind, mu
+            arr[b, 2:2 + len(lo)] = lo
+            arr[b, 5:5 + len(hi)] = hi
+        p._bnd = arr
+        p.bnd = arr.ctypes.data
+        bm = getattr(w, "bmotion", None) if w is not None else None
+        if bm is not None:
+            T, d = p.n_steps, int(cfg.dim)
+            m = np.zeros((len(boxes), max(T, 1), 2, 3))
+            m[:, :T, :, :d] = np.asarray(bm, dtype=np.float64)[:, :T]
+            p._bm = m
+            p.bmotion = m.ctypes.data
     return p
 
 
@@ -205,7 +226,7 @@ def forward(w, n_steps=None, traj=False, C0=None, F0=None):
     tx = np.zeros((T + 1, n, 3)) if traj else None
     mom = np.zeros((max(T, 1), ni))
     fld = field_to3(w.field, ni, max(T, 1)) if T <= cfg.n_steps else None
-    p = params(cfg, T)
+    p = params(cfg, T, w)
     c0, f0 = _aos9(C0, n), _aos9(F0, n)
     if F0 is not None and d == 2:
         f0.reshape(n, 3, 3)[:, 2, 2] = 0.0
@@ -238,7 +259,7 @@ def backward(w, dloss=None, ckpt_every=0, n_steps=None, sum_designs=True):
     g_phi = np.zeros(n); g_mag = np.zeros((n, 3)); g_field = np.zeros((ni, max(T, 1), 3))
     g_x0 = np.zeros((n, 3)); g_v0 = np.zeros((n, 3))
     fld = field_to3(w.field, ni, max(T, 1))
-    p = params(cfg, T)
+    p = params(cfg, T, w)
     st = lib().orc_backward(ctypes.byref(p), ni, _ip(counts), _dp(inp["x0"]), _dp(inp["v0"]),
                             _dp(inp["phi"]), _dp(inp["mag"]), _dp(fld), _dp(inp["target"]),
                             _dp(dl), int(ckpt_every), _dp(g_phi), _dp(g_mag), _dp(g_field),

@@ -70,6 +70,14 @@ typedef struct {
     int pad_;
     double dt, E, nu, rho0, p_vol, simp_eps, damping, floor_mu;
     double gravity[3];
+    /* Solid boxes of Eq. 18 (reading R18): n_bnd entries of 8 doubles
+     * {kind, mu, lo[3], hi[3]} (kind 0 Coulomb, 1 non-slip, 2 attached),
+     * and optionally per substep and box the offset and velocity v_b,
+     * bmotion[((b * n_steps + n) * 2 + {0, 1}) * 3 + i]. */
+    int n_bnd;
+    int pad2_;
+    const double* bnd;
+    const double* bmotion;
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -358,12 +366,15 @@ static int p2g(const orc_params* P, int p0, int p1, const state_t* s, const doub
     return status;
 }
 
-/* Boundary projection trace of one node (reading R5/R6). */
+/* Boundary projection trace of one node (readings R5/R6/R18). */
+#define ORC_MAX_OPS (6 + 8)
 typedef struct {
     int n_ops;
-    int kind[6];     /* 1 = non-slip, 2 = Coulomb */
-    int axis[6];
-    double vin[6][3];
+    int kind[ORC_MAX_OPS];     /* 1 = velocity set (non-slip / attached), 2 = Coulomb */
+    int axis[ORC_MAX_OPS];
+    double sgn[ORC_MAX_OPS];   /* outward normal of the solid: sgn * e_axis */
+    double mu[ORC_MAX_OPS];
+    double vin[ORC_MAX_OPS][3]; /* velocity relative to the boundary before the op */
 } bc_trace;
 
 static void node_index_coords(const orc_params* P, long idx, int* c) {
@@ -374,8 +385,26 @@ static void node_index_coords(const orc_params* P, long idx, int* c) {
     }
 }
 
-/* Boundary conditions on velocity v (in place), recording what fired. */
-static void apply_bc(const orc_params* P, const int* c, double* v, bc_trace* tr) {
+/* Coulomb projection of Eq. 18 on velocity v relative to a boundary moving
+ * at vb, with outward normal sgn * e_a, when the relative velocity points
+ * into the solid (vn < 0): the normal part becomes vb's, the tangential
+ * part shrinks by mu |vn| (to zero at most). */
+static void coulomb(int d, int a, double sgn, double mu, const double* vb, double* v) {
+    double vr[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i) vr[i] = v[i] - vb[i];
+    double vn = sgn * vr[a];
+    double t2 = 0.0;
+    for (int i = 0; i < d; ++i)
+        if (i != a) t2 += vr[i] * vr[i];
+    double u = sqrt(t2);
+    double sp = u + mu * vn;
+    double f = (u > 0.0 && sp > 0.0) ? sp / u : 0.0;
+    for (int i = 0; i < d; ++i) v[i] = vb[i] + (i == a ? 0.0 : vr[i] * f);
+}
+
+/* Boundary conditions on velocity v (in place) at substep `step`, recording
+ * what fired: the walls (R5), then every solid box in order (R18). */
+static void apply_bc(const orc_params* P, const int* c, double* v, bc_trace* tr, int step) {
     int d = P->dim;
     tr->n_ops = 0;
     for (int a = 0; a < d; ++a) {
@@ -386,30 +415,61 @@ static void apply_bc(const orc_params* P, const int* c, double* v, bc_trace* tr)
             if (!(vn < 0.0)) continue;
             int op = tr->n_ops++;
             tr->axis[op] = a;
+            tr->sgn[op] = side == 0 ? 1.0 : -1.0;
+            tr->mu[op] = P->floor_mu;
             for (int i = 0; i < 3; ++i) tr->vin[op][i] = v[i];
             if (P->wall_mode == 1 && a == 1 && side == 0) {
                 /* Coulomb floor, Eq. 18 with v_b = 0, normal +e_1 */
+                static const double zero[3] = {0, 0, 0};
                 tr->kind[op] = 2;
-                double t2 = 0.0;
-                for (int i = 0; i < d; ++i)
-                    if (i != a) t2 += v[i] * v[i];
-                double u = sqrt(t2);
-                double sp = u + P->floor_mu * vn;
-                if (u > 0.0 && sp > 0.0) {
-                    for (int i = 0; i < d; ++i) v[i] = (i == a) ? 0.0 : v[i] * sp / u;
-                } else {
-                    for (int i = 0; i < d; ++i) v[i] = 0.0;
-                }
+                coulomb(d, a, 1.0, P->floor_mu, zero, v);
             } else {
                 tr->kind[op] = 1; /* non-slip, the mu -> infinity limit */
                 for (int i = 0; i < d; ++i) v[i] = 0.0;
             }
         }
     }
+    /* solid boxes: a node inside the (moved) box lies on its nearest face */
+    double dx = 1.0 / P->res;
+    for (int b = 0; b < P->n_bnd; ++b) {
+        const double* B = P->bnd + 8 * b;
+        int kind = (int)B[0];
+        double off[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+        if (P->bmotion) {
+            const double* m = P->bmotion + ((size_t)b * P->n_steps + step) * 6;
+            for (int i = 0; i < 3; ++i) {
+                off[i] = m[i];
+                vb[i] = m[3 + i];
+            }
+        }
+        int inside = 1, axis = 0;
+        double sgn = -1.0, best = 1e300;
+        for (int a = 0; a < d; ++a) {
+            double x = c[a] * dx, lo = B[2 + a] + off[a], hi = B[5 + a] + off[a];
+            if (x < lo || x > hi) inside = 0;
+            if (x - lo < best) { best = x - lo; axis = a; sgn = -1.0; }
+            if (hi - x < best) { best = hi - x; axis = a; sgn = 1.0; }
+        }
+        if (!inside) continue;
+        double vn = sgn * (v[axis] - vb[axis]);
+        if (kind != 2 && !(vn < 0.0)) continue; /* separating: free */
+        int op = tr->n_ops++;
+        tr->axis[op] = axis;
+        tr->sgn[op] = sgn;
+        tr->mu[op] = B[1];
+        for (int i = 0; i < 3; ++i) tr->vin[op][i] = v[i] - vb[i];
+        if (kind == 0) {
+            tr->kind[op] = 2;
+            coulomb(d, axis, sgn, B[1], vb, v);
+        } else { /* non-slip obstacle when moving into it; attached always */
+            tr->kind[op] = 1;
+            for (int i = 0; i < d; ++i) v[i] = vb[i];
+        }
+    }
 }
 
-/* Grid operation, Eq. 16-18, on every node of one grid. */
-static void grid_update(const orc_params* P, const double* gm, const double* gmv, double* gv) {
+/* Grid operation, Eq. 16-18, on every node of one grid at substep `step`. */
+static void grid_update(const orc_params* P, const double* gm, const double* gmv, double* gv, int step) {
     long G = grid_size(P);
     int d = P->dim;
     for (long n = 0; n < G; ++n) {
@@ -423,7 +483,7 @@ static void grid_update(const orc_params* P, const double* gm, const double* gmv
         int c[3];
         node_index_coords(P, n, c);
         bc_trace tr;
-        apply_bc(P, c, v, &tr);
+        apply_bc(P, c, v, &tr, step);
         for (int i = 0; i < d; ++i) gv[3 * n + i] = v[i];
     }
 }
@@ -484,7 +544,7 @@ typedef struct {
 
 static int sim_init(sim_t* S, const orc_params* P, int n_inst, const int* counts) {
     if (!P || !counts || n_inst <= 0 || (P->dim != 2 && P->dim != 3) || P->res < 2 * P->bound + 3 ||
-        P->n_steps < 0)
+        P->n_steps < 0 || P->n_bnd < 0 || P->n_bnd > 8 || (P->n_bnd > 0 && !P->bnd))
         return ORC_ERR_ARG;
     S->P = P;
     S->n_inst = n_inst;
@@ -566,7 +626,7 @@ static int substep(sim_t* S, int n, const state_t* si, const double* phi, const 
         int st = p2g(P, p0, p1, si, phi, mag, Ba, S->gm, S->gmv);
         if (st == ORC_ERR_DOMAIN) return st;
         if (st != ORC_OK) worst = st;
-        grid_update(P, S->gm, S->gmv, S->gv);
+        grid_update(P, S->gm, S->gmv, S->gv, n);
         st = g2p(P, p0, p1, si, S->gv, so);
         if (st == ORC_ERR_DOMAIN) return st;
         if (st != ORC_OK) worst = st;
@@ -689,7 +749,7 @@ int orc_p2g_grid(const orc_params* P, int n_inst, const int* counts, const doubl
         st = p2g(P, S.offs[inst], S.offs[inst + 1], &s, phi, mag, Ba + 3 * inst, gm, gmv);
         if (st == ORC_ERR_DOMAIN) { sim_free(&S); return st; }
         if (st != ORC_OK) worst = st;
-        grid_update(P, gm, gmv, gv);
+        grid_update(P, gm, gmv, gv, 0);
     }
     sim_free(&S);
     return worst;
@@ -701,7 +761,7 @@ int orc_p2g_grid(const orc_params* P, int n_inst, const int* counts, const doubl
 
 /* Reverse of the grid operation on one node: Vbar -> (mbar, mvbar). */
 static void grid_update_adjoint_node(const orc_params* P, long n, double m, const double* mv,
-                                     const double* Vbar, double* mbar, double* mvbar) {
+                                     const double* Vbar, double* mbar, double* mvbar, int step) {
     int d = P->dim;
     *mbar = 0.0;
     for (int i = 0; i < 3; ++i) mvbar[i] = 0.0;
@@ -716,34 +776,37 @@ static void grid_update_adjoint_node(const orc_params* P, long n, double m, cons
     node_index_coords(P, n, c);
     bc_trace tr;
     double v2[3] = {v1[0], v1[1], v1[2]};
-    apply_bc(P, c, v2, &tr);
+    apply_bc(P, c, v2, &tr, step);
     double vb[3] = {0, 0, 0};
     for (int i = 0; i < d; ++i) vb[i] = Vbar[i];
     for (int op = tr.n_ops - 1; op >= 0; --op) {
-        if (tr.kind[op] == 1) {
+        if (tr.kind[op] == 1) { /* output independent of the input */
             for (int i = 0; i < 3; ++i) vb[i] = 0.0;
             continue;
         }
-        /* Coulomb: v_out_t = t (1 + mu vn / u), v_out_n = 0 (when u > 0, u + mu vn > 0) */
+        /* Coulomb on the relative velocity r (the boundary velocity is a
+         * constant): out_t = r_t (1 + mu vn / u), out_n = 0, vn = sgn r_a,
+         * u = |r_t|, when u > 0 and u + mu vn > 0 */
         int a = tr.axis[op];
+        double sg = tr.sgn[op], mu = tr.mu[op];
         const double* vin = tr.vin[op];
-        double vn = vin[a];
+        double vn = sg * vin[a];
         double u2 = 0.0;
         for (int i = 0; i < d; ++i)
             if (i != a) u2 += vin[i] * vin[i];
         double u = sqrt(u2);
-        double sp = u + P->floor_mu * vn;
+        double sp = u + mu * vn;
         double out[3] = {0, 0, 0};
         if (u > 0.0 && sp > 0.0) {
-            double tdot = 0.0; /* vbar_out . t */
+            double tdot = 0.0; /* vbar_out . r_t */
             for (int i = 0; i < d; ++i)
                 if (i != a) tdot += vb[i] * vin[i];
-            double f = 1.0 + P->floor_mu * vn / u;
+            double f = 1.0 + mu * vn / u;
             for (int i = 0; i < d; ++i) {
                 if (i == a) continue;
-                out[i] = vb[i] * f - P->floor_mu * vn * vin[i] * tdot / (u * u * u);
+                out[i] = vb[i] * f - mu * vn * vin[i] * tdot / (u * u * u);
             }
-            out[a] = P->floor_mu * tdot / u;
+            out[a] = sg * mu * tdot / u;
         }
         for (int i = 0; i < 3; ++i) vb[i] = out[i];
     }
@@ -790,7 +853,7 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
         memset(S->gmv, 0, sizeof(double) * 3 * Gn);
         int st = p2g(P, p0, p1, sn, phi, mag, Ba, S->gm, S->gmv);
         if (st == ORC_ERR_DOMAIN) { free(Vbar); free(mbar); free(mvbar); return st; }
-        grid_update(P, S->gm, S->gmv, S->gv);
+        grid_update(P, S->gm, S->gmv, S->gv, n);
         memset(Vbar, 0, sizeof(double) * 3 * Gn);
 
         /* --- reverse of G2P (Eq. 19-22) --- */
@@ -860,7 +923,7 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
         /* --- reverse of the grid operation (Eq. 16-18) --- */
         for (long nd = 0; nd < Gn; ++nd)
             grid_update_adjoint_node(P, nd, S->gm[nd], S->gmv + 3 * nd, Vbar + 3 * nd, mbar + nd,
-                                     mvbar + 3 * nd);
+                                     mvbar + 3 * nd, n);
 
         /* --- reverse of P2G (Eq. 14-15, stress Eq. 7, SIMP Eq. 31-33) --- */
         for (int p = p0; p < p1; ++p) {

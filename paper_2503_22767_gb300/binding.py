@@ -28,11 +28,20 @@ STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_CUDA", -3: "MPM_ERR
 EXPORTS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_forward", "mpm_backward",
            "mpm_forward_host", "mpm_backward_host", "mpm_read_state", "mpm_sort_particles",
            "mpm_set_option", "mpm_get_option", "mpm_autotune", "mpm_get_stats", "mpm_reset_stats",
-           "mpm_substep_noalloc",
+           "mpm_substep_noalloc", "mpm_set_boundaries",
            # design maps and optimiser step (mpm_design.h)
            "mpm_design_create", "mpm_design_destroy", "mpm_design_last_error", "mpm_design_forward",
            "mpm_design_backward", "mpm_adam_step"]
 MPM_NOALLOC_MAX_NODES = 262144
+
+
+MPM_MAX_BOUNDARIES = 8
+MPM_BOUNDARY_COULOMB, MPM_BOUNDARY_NONSLIP, MPM_BOUNDARY_ATTACHED = 0, 1, 2
+
+
+class mpm_boundary(ctypes.Structure):
+    """Mirror of mpm_boundary (include/mpm.h)."""
+    _fields_ = [("kind", c_int), ("mu", ctypes.c_float), ("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
 
 
 class mpm_design_config(ctypes.Structure):
@@ -104,6 +113,7 @@ def load():
             "mpm_get_stats": ([H, ctypes.POINTER(mpm_stats)], c_int),
             "mpm_reset_stats": ([H], c_int),
             "mpm_substep_noalloc": ([ctypes.POINTER(mpm_config), c_int, pf, pf, pf, pf, pf, vp], c_int),
+            "mpm_set_boundaries": ([H, c_int, ctypes.POINTER(mpm_boundary), pf, vp], c_int),
             "mpm_design_create": ([ctypes.POINTER(mpm_design_config), pf, pi, ctypes.POINTER(c_void_p), vp],
                                   c_int),
             "mpm_design_destroy": ([H], c_int),

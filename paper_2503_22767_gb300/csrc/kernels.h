@@ -61,10 +61,10 @@ cudaError_t launch_adjoint_tiled(int dim, bool fuse, bool fuse_v, const Params& 
 // grid operation on every node of every instance: acc -> V; clears acc
 // (lean) or clears acc_next (store pass).
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,
-                        bool clear_acc, cudaStream_t st);
+                        bool clear_acc, int step, cudaStream_t st);
 // grid adjoint: Vbar -> gadj (clears Vbar).
 cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, float4* Vbar,
-                                float4* gadj, cudaStream_t st);
+                                float4* gadj, int step, cudaStream_t st);
 
 // initial state from x0 / v0 (input order): C = 0, F = I, id = p.
 cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0,

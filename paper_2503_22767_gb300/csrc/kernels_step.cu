@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
                 if (!FUSE) return g;
                 float mv[D], gv[D];
                 unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                grid_velocity<D>(P, c, g.x, mv, gv);  // Eq. 16-18 once per node
+                grid_velocity<D>(P, c, g.x, mv, gv, a.n_g2p);  // Eq. 16-18 once per node
                 return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
             });
         }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
                 if (box.use) {
                     unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
                 } else {
-                    node_velocity<D, FUSE>(Vi, t, P, gv);
+                    node_velocity<D, FUSE>(Vi, t, P, gv, a.n_g2p);
                 }
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
@@ -215,12 +215,12 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
 // grid operation (Eq. 16-18)
 // ---------------------------------------------------------------------------
 // One block row per instance (blockIdx.y), so node indices stay 32-bit.
-// Nodes without mass (most of a 3D grid) take the short path: Eq. 16 gives
-// them no velocity, and the reverse gives them no gradient.
+// Nodes without mass (most of a 3D grid) skip the node arithmetic: Eq. 16
+// gives them no velocity, and the reverse gives them no gradient.
 template <int D>
 __global__ void __launch_bounds__(256) k_grid(Params P, float4* __restrict__ acc,
                                               float4* __restrict__ V, float4* __restrict__ acc_next,
-                                              bool clear_acc) {
+                                              bool clear_acc, int step) {
     pdl_wait();
     pdl_trigger();
     const int local = blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,24 +228,24 @@ __global__ void __launch_bounds__(256) k_grid(Params P, float4* __restrict__ acc
     const long long i = (long long)blockIdx.y * P.nodes + local;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 g = acc[i];
+    float4 out = zero;
+    if (g.x > 0.0f) {
+        int c[D];
+        node_coords<D>(local, P.res, c);
+        float mv[D], v[D];
+        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+        grid_velocity<D>(P, c, g.x, mv, v, step);
+        out = make_float4(v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f, 0.0f);
+    }
+    V[i] = out;
     if (clear_acc) acc[i] = zero;
     if (acc_next) acc_next[i] = zero;
-    if (!(g.x > 0.0f)) {
-        V[i] = zero;
-        return;
-    }
-    int c[D];
-    node_coords<D>(local, P.res, c);
-    float mv[D], v[D];
-    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-    grid_velocity<D>(P, c, g.x, mv, v);
-    V[i] = make_float4(v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f, 0.0f);
 }
 
 template <int D>
 __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __restrict__ acc,
                                                       float4* __restrict__ Vbar,
-                                                      float4* __restrict__ gadj) {
+                                                      float4* __restrict__ gadj, int step) {
     pdl_wait();
     pdl_trigger();
     const int local = blockIdx.x * blockDim.x + threadIdx.x;
@@ -253,20 +253,19 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
     const long long i = (long long)blockIdx.y * P.nodes + local;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 g = acc[i];
-    if (!(g.x > 0.0f)) {
-        Vbar[i] = zero;
-        gadj[i] = zero;
-        return;
+    float4 out = zero;
+    if (g.x > 0.0f) {
+        const float4 vb4 = Vbar[i];
+        int c[D];
+        node_coords<D>(local, P.res, c);
+        float mv[D], vb[D], mvb[D], mb;
+        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+        unpack3<D>(vb4, vb);
+        grid_velocity_adjoint<D>(P, c, g.x, mv, vb, mb, mvb, step);
+        out = pack4<D>(mb, mvb);
     }
-    const float4 vb4 = Vbar[i];
     Vbar[i] = zero;
-    int c[D];
-    node_coords<D>(local, P.res, c);
-    float mv[D], vb[D], mvb[D], mb;
-    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-    unpack3<D>(vb4, vb);
-    grid_velocity_adjoint<D>(P, c, g.x, mv, vb, mb, mvb);
-    gadj[i] = pack4<D>(mb, mvb);
+    gadj[i] = out;
 }
 
 // ---------------------------------------------------------------------------
@@ -376,7 +375,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     float mv[D], vbv[D], mbv, mvb[D];
                     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
                     unpack3<D>(__ldg(vbi + node), vbv);
-                    grid_velocity_adjoint<D>(P, c, g.x, mv, vbv, mbv, mvb);
+                    grid_velocity_adjoint<D>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
                     return make_float4(mbv, mvb[0], mvb[1], D == 3 ? mvb[D - 1] : 0.0f);
                 });
 #pragma unroll
@@ -394,7 +393,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     float mv[D], vbv[D], mbv;
                     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
                     unpack3<D>(__ldg(vbi + t.node), vbv);
-                    grid_velocity_adjoint<D>(P, t.c, g.x, mv, vbv, mbv, mvb);
+                    grid_velocity_adjoint<D>(P, t.c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
                     g.x = mbv;
                 } else {
                     g = __ldg(gi + t.node);
@@ -526,7 +525,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                 if (!FUSE_V) return g;
                 float mv[D], gv[D];
                 unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                grid_velocity<D>(P, c, g.x, mv, gv);  // Eq. 16-18 once per node
+                grid_velocity<D>(P, c, g.x, mv, gv, a.n_p2g - 1);  // Eq. 16-18 once per node
                 return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
             });
         // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T), factored
@@ -547,7 +546,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
             node_term<D>(s, k, P, t);
             float gv[D];
             if (box.use) unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
-            else node_velocity<D, FUSE_V>(Vi, t, P, gv);
+            else node_velocity<D, FUSE_V>(Vi, t, P, gv, a.n_p2g - 1);
             float sv[D], dot = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
@@ -813,17 +812,17 @@ cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, bool fuse_v
 }
 
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,
-                        bool clear_acc, cudaStream_t st) {
+                        bool clear_acc, int step, cudaStream_t st) {
     dim3 grid(blocks_for(P.nodes, 256), P.n_inst);
-    if (dim == 2) return launch_chain(P, k_grid<2>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc);
-    return launch_chain(P, k_grid<3>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc);
+    if (dim == 2) return launch_chain(P, k_grid<2>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc, step);
+    return launch_chain(P, k_grid<3>, grid, dim3(256), st, P, acc, V, acc_next, clear_acc, step);
 }
 
 cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, float4* Vbar,
-                                float4* gadj, cudaStream_t st) {
+                                float4* gadj, int step, cudaStream_t st) {
     dim3 grid(blocks_for(P.nodes, 256), P.n_inst);
-    if (dim == 2) return launch_chain(P, k_grid_adjoint<2>, grid, dim3(256), st, P, acc, Vbar, gadj);
-    return launch_chain(P, k_grid_adjoint<3>, grid, dim3(256), st, P, acc, Vbar, gadj);
+    if (dim == 2) return launch_chain(P, k_grid_adjoint<2>, grid, dim3(256), st, P, acc, Vbar, gadj, step);
+    return launch_chain(P, k_grid_adjoint<3>, grid, dim3(256), st, P, acc, Vbar, gadj, step);
 }
 
 cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0, float* s,

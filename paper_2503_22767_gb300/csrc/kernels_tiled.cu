@@ -22,10 +22,10 @@ namespace {
 template <int D, bool FUSE>
 __device__ __forceinline__ float4 gather_node(const TileBox<D>& box, const float4* tile,
                                               const float4* __restrict__ direct,
-                                              const NodeTerm<D>& t, const Params& P) {
+                                              const NodeTerm<D>& t, const Params& P, int step) {
     if (box.use) return tile[box_index<D>(box, t.c)];
     float gv[D];
-    node_velocity<D, FUSE>(direct, t, P, gv);
+    node_velocity<D, FUSE>(direct, t, P, gv, step);
     return make_float4(gv[0], gv[1 % D], D == 3 ? gv[2 % D] : 0.0f, 0.0f);
 }
 
@@ -33,12 +33,12 @@ __device__ __forceinline__ float4 gather_node(const TileBox<D>& box, const float
 // grid operation applied to the accumulator (fused grid)
 template <int D, bool FUSE>
 __device__ __forceinline__ float4 stage_velocity(const float4* __restrict__ src, const int (&c)[D],
-                                                 const Params& P) {
+                                                 const Params& P, int step) {
     const float4 g = __ldg(src + grid_index<D>(c, P.res));
     if (!FUSE) return g;
     float mv[D], v[D];
     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-    grid_velocity<D>(P, c, g.x, mv, v);
+    grid_velocity<D>(P, c, g.x, mv, v, step);
     return make_float4(v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f, 0.0f);
 }
 
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_forward_tiled(Params P, StepArgs a) {
         for (int t = threadIdx.x; t < box.n; t += blockDim.x) {
             int c[D];
             box_coords<D>(box, t, c);
-            tileV[t] = stage_velocity<D, FUSE>(src, c, P);
+            tileV[t] = stage_velocity<D, FUSE>(src, c, P, a.n_g2p);
         }
     }
     __syncthreads();
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_forward_tiled(Params P, StepArgs a) {
             NodeTerm<D> t;
             node_term<D>(s, k, P, t);
             float gv[D];
-            unpack3<D>(gather_node<D, FUSE>(box, tileV, direct, t, P), gv);
+            unpack3<D>(gather_node<D, FUSE>(box, tileV, direct, t, P, a.n_g2p), gv);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 v[i] += t.w * gv[i];  // Eq. 19
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
                 float mv[D], vbv[D], mvb[D], mbv;
                 unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
                 unpack3<D>(__ldg(a.VbarIn + gi), vbv);
-                grid_velocity_adjoint<D>(P, c, g.x, mv, vbv, mbv, mvb);
+                grid_velocity_adjoint<D>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
                 tileG[t] = pack4<D>(mbv, mvb);
             } else {
                 tileG[t] = __ldg(a.gadj + gi);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
                 float mv[D], vbv[D], mvb[D], mbv;
                 unpack3<D>(make_float4(g4.y, g4.z, g4.w, 0.0f), mv);
                 unpack3<D>(__ldg(a.VbarIn + off + t.node), vbv);
-                grid_velocity_adjoint<D>(P, t.c, g4.x, mv, vbv, mbv, mvb);
+                grid_velocity_adjoint<D>(P, t.c, g4.x, mv, vbv, mbv, mvb, a.n_p2g);
                 g = pack4<D>(mbv, mvb);
             } else {
                 g = __ldg(a.gadj + off + t.node);
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
         for (int t = threadIdx.x; t < box2.n; t += blockDim.x) {
             int c[D];
             box_coords<D>(box2, t, c);
-            tileG[t] = stage_velocity<D, FUSE_V>(src, c, P);
+            tileG[t] = stage_velocity<D, FUSE_V>(src, c, P, a.n_p2g - 1);
         }
     }
     __syncthreads();
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
         if (active) {
             node_term<D>(s2, k, P, t);
             float gv[D];
-            unpack3<D>(gather_node<D, FUSE_V>(box2, tileG, direct, t, P), gv);
+            unpack3<D>(gather_node<D, FUSE_V>(box2, tileG, direct, t, P, a.n_p2g - 1), gv);
             float vdot = 0.0f, vcd = 0.0f, cd[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {

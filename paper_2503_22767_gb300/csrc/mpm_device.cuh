@@ -32,6 +32,26 @@ struct Params {
     int pdl;  // per-substep kernels launched with programmatic dependent launch
     int adj_blocks;  // register budget of the adjoint particle kernel: 256-thread blocks per SM (2 or 3)
     int box;         // 1: warps stage their stencil nodes in shared memory before gathering
+    // solid boxes of Eq. 18 beyond the walls (device memory), or null.  One
+    // pointer keeps the parameter block (and the transfer kernels' register
+    // allocation) as small as without boxes.
+    const struct BoundarySet* bset;
+};
+
+constexpr int kMaxBoundaries = 8;
+constexpr int kBoundaryCoulomb = 0, kBoundaryNonSlip = 1, kBoundaryAttached = 2;
+
+struct Boundary {
+    int kind;  // kBoundary*
+    float mu;  // friction coefficient (Coulomb)
+    float lo[3], hi[3];  // axis-aligned box at t = 0
+};
+
+struct BoundarySet {
+    int n;                        // boxes in use (<= kMaxBoundaries)
+    Boundary box[kMaxBoundaries];
+    const float* motion;          // per box and substep: offset, velocity v_b
+                                  // ([b][n_steps][2][D]), or null for static boxes
 };
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
@@ -335,9 +355,60 @@ __device__ __forceinline__ void node_coords(int local, int res, int (&c)[D]) {
     }
 }
 
+// Solid box b at substep `step` and node c: true when the node lies inside
+// the (moved) box, with the box velocity vb and the outward normal sgn e_axis
+// of the face nearest to the node (ties: lowest axis, low face first).
+template <int D>
+__device__ __forceinline__ bool box_contact(const Params& P, int b, int step, const int (&c)[D],
+                                            float (&vb)[D], int& axis, float& sgn) {
+    const Boundary B = P.bset->box[b];
+    const float* mo = P.bset->motion ? P.bset->motion + ((long long)b * P.n_steps + step) * 2 * D : nullptr;
+    bool inside = true;
+    float best = 3.0e38f;
+    axis = 0;
+    sgn = -1.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float off = mo ? mo[a] : 0.0f;
+        vb[a] = mo ? mo[D + a] : 0.0f;
+        const float x = (float)c[a] * P.dx, lo = B.lo[a] + off, hi = B.hi[a] + off;
+        if (x < lo || x > hi) inside = false;
+        if (x - lo < best) {
+            best = x - lo;
+            axis = a;
+            sgn = -1.0f;
+        }
+        if (hi - x < best) {
+            best = hi - x;
+            axis = a;
+            sgn = 1.0f;
+        }
+    }
+    return inside;
+}
+
+// Eq. 18 on the velocity relative to a boundary moving at vb, outward
+// normal sgn e_a: the normal part becomes vb's, the tangential part shrinks
+// by mu |vn| (to zero at most).
+template <int D>
+__device__ __forceinline__ void coulomb_project(int a, float sgn, float mu, const float (&vb)[D], float (&v)[D]) {
+    float vr[D], t2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        vr[i] = v[i] - vb[i];
+        if (i != a) t2 += vr[i] * vr[i];
+    }
+    const float vn = sgn * vr[a];
+    const float u = sqrtf(t2);
+    const float sp = u + mu * vn;
+    const float f = (u > 0.0f && sp > 0.0f) ? sp / u : 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = vb[i] + (i == a ? 0.0f : vr[i] * f);
+}
+
 template <int D>
 __device__ __forceinline__ void grid_velocity(const Params& P, const int (&c)[D], float m,
-                                              const float (&mv)[D], float (&v)[D]) {
+                                              const float (&mv)[D], float (&v)[D], int step) {
     if (!(m > 0.0f)) {
 #pragma unroll
         for (int i = 0; i < D; ++i) v[i] = 0.0f;
@@ -370,6 +441,22 @@ __device__ __forceinline__ void grid_velocity(const Params& P, const int (&c)[D]
             }
         }
     }
+    // solid boxes after the walls, in order: attached boxes set v = v_b; the
+    // others act when the velocity relative to the box points into it
+    const int nbox = P.bset ? P.bset->n : 0;
+    for (int b = 0; b < nbox; ++b) {
+        float vb[D], sgn;
+        int axis;
+        if (!box_contact<D>(P, b, step, c, vb, axis, sgn)) continue;
+        const int kind = P.bset->box[b].kind;
+        if (kind != kBoundaryAttached && !(sgn * (v[axis] - vb[axis]) < 0.0f)) continue;
+        if (kind == kBoundaryCoulomb) {
+            coulomb_project<D>(axis, sgn, P.bset->box[b].mu, vb, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) v[i] = vb[i];
+        }
+    }
 }
 
 // Reverse of grid_velocity: Vbar -> (mbar, mvbar).  The forward branches are
@@ -377,7 +464,7 @@ __device__ __forceinline__ void grid_velocity(const Params& P, const int (&c)[D]
 template <int D>
 __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int (&c)[D], float m,
                                                       const float (&mv)[D], const float (&Vbar)[D],
-                                                      float& mbar, float (&mvbar)[D]) {
+                                                      float& mbar, float (&mvbar)[D], int step) {
     mbar = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i) mvbar[i] = 0.0f;
@@ -424,9 +511,66 @@ __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int
             }
         }
     }
+    // replay the solid boxes, remembering the relative velocity entering
+    // each projection that fired (kind 1: set, 2: Coulomb)
+    int bkind[kMaxBoundaries], baxis[kMaxBoundaries];
+    float bsgn[kMaxBoundaries], bmu[kMaxBoundaries], bvin[kMaxBoundaries][D];
+    const int nb = P.bset ? min(P.bset->n, kMaxBoundaries) : 0;
+    for (int b = 0; b < nb; ++b) {
+        float vbx[D], sgn;
+        int axis;
+        bkind[b] = 0;
+        if (!box_contact<D>(P, b, step, c, vbx, axis, sgn)) continue;
+        const int kind = P.bset->box[b].kind;
+        if (kind != kBoundaryAttached && !(sgn * (v[axis] - vbx[axis]) < 0.0f)) continue;
+        baxis[b] = axis;
+        bsgn[b] = sgn;
+        bmu[b] = P.bset->box[b].mu;
+#pragma unroll
+        for (int i = 0; i < D; ++i) bvin[b][i] = v[i] - vbx[i];
+        if (kind == kBoundaryCoulomb) {
+            bkind[b] = 2;
+            coulomb_project<D>(axis, sgn, bmu[b], vbx, v);
+        } else {
+            bkind[b] = 1;
+#pragma unroll
+            for (int i = 0; i < D; ++i) v[i] = vbx[i];
+        }
+    }
     float vb[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) vb[i] = Vbar[i];
+    // reverse of the boxes (last first); the box velocity is a constant, so
+    // the Coulomb Jacobian acts on the relative velocity r = v - v_b:
+    // out_t = r_t (1 + mu vn / u), out_n = 0, vn = sgn r_a, u = |r_t|
+    for (int b = nb - 1; b >= 0; --b) {
+        if (bkind[b] == 1) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) vb[i] = 0.0f;
+        } else if (bkind[b] == 2) {
+            const int a = baxis[b];
+            const float mu = bmu[b], vn = bsgn[b] * bvin[b][a];
+            float t2 = 0.0f, tdot = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+                if (i != a) {
+                    t2 += bvin[b][i] * bvin[b][i];
+                    tdot += vb[i] * bvin[b][i];
+                }
+            const float u = sqrtf(t2);
+            if (u > 0.0f && u + mu * vn > 0.0f) {
+                const float ru = 1.0f / u;
+                const float f = 1.0f + mu * vn * ru;
+                const float g = mu * vn * tdot * ru * ru * ru;
+                const float out_n = bsgn[b] * mu * tdot * ru;
+#pragma unroll
+                for (int i = 0; i < D; ++i) vb[i] = (i == a) ? out_n : vb[i] * f - g * bvin[b][i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < D; ++i) vb[i] = 0.0f;
+            }
+        }
+    }
     if (nops > 0) {
 #pragma unroll
         for (int op = 2 * D - 1; op >= 0; --op) {

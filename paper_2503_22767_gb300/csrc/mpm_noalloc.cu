@@ -158,7 +158,7 @@ extern "C" int mpm_substep_noalloc(const mpm_config* cfg, int substep, const flo
     a.n_p2g = substep;
     if ((e = mpm::launch_forward(d, false, true, false, false, P, a, 128, st)) != cudaSuccess)
         return report(MPM_ERR_CUDA, cudaGetErrorString(e));
-    if ((e = mpm::launch_grid(d, P, acc, V, nullptr, false, st)) != cudaSuccess)
+    if ((e = mpm::launch_grid(d, P, acc, V, nullptr, false, substep, st)) != cudaSuccess)
         return report(MPM_ERR_CUDA, cudaGetErrorString(e));
     mpm::StepArgs g = a;
     g.acc = nullptr;

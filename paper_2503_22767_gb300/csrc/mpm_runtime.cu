@@ -109,6 +109,8 @@ struct mpm_handle {
 
     float4* acc3 = nullptr;   // fused mode: three rotating P2G accumulators
     float4* Vbar3 = nullptr;  // fused mode: three rotating G2P^T scatter targets
+    mpm::BoundarySet* d_bset = nullptr;  // solid boxes (Eq. 18) read by the grid operation
+    float* d_bmotion = nullptr;          // their offsets and velocities per substep
 
     // --- options ---
     bool fuse_fwd = true;   // grid operation folded into the forward particle kernels
@@ -468,6 +470,8 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->gphi_d, h->Nd);
     ALLOC(h->gmag_d, d * h->Nd);
     ALLOC(h->gfield_d, (long long)h->n_inst * h->T * d);
+    ALLOC(h->d_bset, 1);
+    ALLOC(h->d_bmotion, (long long)mpm::kMaxBoundaries * h->T * 2 * d);
     ALLOC(h->st_x0, d * h->N);
     ALLOC(h->st_v0, d * h->N);
     ALLOC(h->st_xout, d * h->N);
@@ -583,7 +587,7 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
         }
         for (int n = s0; n < s1; ++n) {
             if (!fuse && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
-                              return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, st);
+                              return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, n, st);
                           })))
                 return rc;
             const bool p2g = n + 1 < T;
@@ -682,7 +686,7 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
         const bool p2g = k + 1 < Ks;
         float4* next_acc = p2g ? gacc(k + 1) : nullptr;
         if (!fuse_rec && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
-                          return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, st);
+                          return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, n, st);
                       })))
             return rc;
         a = base_args(h);
@@ -770,7 +774,7 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
     for (int k = Ks - 1; k >= 1; --k) {
         const int n = s0 + k;
         if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
-                          return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, st);
+                          return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, n, st);
                       })))
             return rc;
         a = args();
@@ -796,7 +800,7 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
             return rc;
     }
     if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
-                      return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, st);
+                      return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, s0, st);
                   })))
         return rc;
     a = args();
@@ -1252,6 +1256,40 @@ int mpm_sort_particles(mpm_handle* h, const float* x, int* keys, int* perm, void
     if (h->N > 0)
         MPM_CUDA(h, cudaMemcpyAsync(keys, h->sb.keys, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, st));
     MPM_CUDA(h, cudaStreamSynchronize(st));
+    return MPM_OK;
+}
+
+int mpm_set_boundaries(mpm_handle* h, int n, const mpm_boundary* boxes, const float* motion, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    if (n < 0 || n > MPM_MAX_BOUNDARIES) return fail(h, MPM_ERR_ARG, "n must be in [0, MPM_MAX_BOUNDARIES]");
+    if (n > 0 && !boxes) return fail(h, MPM_ERR_ARG, "boxes is NULL");
+    mpm::BoundarySet hs{};
+    hs.n = n;
+    for (int b = 0; b < n; ++b) {
+        const mpm_boundary& B = boxes[b];
+        if (B.kind < MPM_BOUNDARY_COULOMB || B.kind > MPM_BOUNDARY_ATTACHED)
+            return fail(h, MPM_ERR_ARG, "unknown boundary kind");
+        if (!(B.mu >= 0.0f) || !std::isfinite(B.mu)) return fail(h, MPM_ERR_ARG, "mu must be finite and >= 0");
+        for (int a = 0; a < h->dim; ++a)
+            if (!(B.lo[a] <= B.hi[a]) || !std::isfinite(B.lo[a]) || !std::isfinite(B.hi[a]))
+                return fail(h, MPM_ERR_ARG, "a box needs finite lo <= hi on every axis");
+        hs.box[b].kind = B.kind;
+        hs.box[b].mu = B.mu;
+        for (int a = 0; a < 3; ++a) {
+            hs.box[b].lo[a] = B.lo[a];
+            hs.box[b].hi[a] = B.hi[a];
+        }
+    }
+    hs.motion = (n > 0 && motion) ? h->d_bmotion : nullptr;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (hs.motion)
+        MPM_CUDA(h, cudaMemcpyAsync(h->d_bmotion, motion, sizeof(float) * (size_t)n * h->T * 2 * h->dim,
+                                    cudaMemcpyDeviceToDevice, st));
+    MPM_CUDA(h, cudaMemcpyAsync(h->d_bset, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    MPM_CUDA(h, cudaStreamSynchronize(st));  // hs lives on this stack frame
+    drop_graphs(h);
+    h->P.bset = n > 0 ? h->d_bset : nullptr;
+    h->forward_done = false;  // a backward must replay the forward's boundaries
     return MPM_OK;
 }
 

@@ -79,6 +79,8 @@ class Simulator:
             self.set_option(B.MPM_OPT_BLOCK, block)
         for key, value in (options or {}).items():
             self.set_option(key, value)
+        if getattr(cfg, "boundaries", None):
+            self.set_boundaries(cfg.boundaries)
 
     # -- lifetime -------------------------------------------------------------
     def close(self):
@@ -164,6 +166,23 @@ class Simulator:
                                          _stream())
         self._check(st, "mpm_sort_particles")
         return keys, perm
+
+    def set_boundaries(self, boxes, motion=None):
+        """Solid boxes of Eq. 18 beyond the walls (see mpm_set_boundaries):
+        boxes is a list of (kind, mu, lo, hi) with kind 0 Coulomb, 1
+        non-slip, 2 attached; motion a CUDA tensor [n][n_steps][2][d]
+        (offset, velocity per substep) or None for static boxes."""
+        n = len(boxes)
+        arr = (B.mpm_boundary * max(n, 1))()
+        for b, (kind, mu, lo, hi) in enumerate(boxes):
+            arr[b].kind, arr[b].mu = int(kind), float(mu)
+            lo3, hi3 = list(lo) + [0.0] * 3, list(hi) + [0.0] * 3
+            for a in range(3):
+                arr[b].lo[a], arr[b].hi[a] = float(lo3[a]), float(hi3[a])
+        motion = _dev(motion, (n, self.T, 2, self.d), "motion")
+        st = self.lib.mpm_set_boundaries(self.handle, n, arr, B.fptr(motion), _stream())
+        self._check(st, "mpm_set_boundaries")
+        self.generation += 1
 
     def autotune(self, cache_path=None, sample_substeps=0):
         """Pick block size, grid fusion, the adjoint register budget and warp-staged gathers by timing them on the inputs

@@ -55,6 +55,9 @@ class MpmConfig:
     floor_mu: float = 0.0
     loss_kind: int = 0  # 0: final-position MSE (Eq. 38); 1: locomotion (Eq. 40)
     checkpoint_every: int = 0  # 0 = store every substep
+    # solid boxes of Eq. 18 beyond the walls: (kind, mu, lo, hi) with kind
+    # 0 Coulomb, 1 non-slip, 2 attached; their motion is Workload.bmotion
+    boundaries: Optional[List[tuple]] = None
 
     @property
     def n_instances(self) -> int:
@@ -102,6 +105,9 @@ class Workload:
     field: np.ndarray
     target: Optional[np.ndarray]
     meta: dict = field(default_factory=dict)
+    # per box and substep: offset from the t = 0 box and velocity v_b,
+    # [n_boxes][n_steps][2][d]; None for static boxes
+    bmotion: Optional[np.ndarray] = None
 
 
 # ---------------------------------------------------------------------------
@@ -387,7 +393,7 @@ def batch(parts, design_of_instance: Optional[List[int]] = None, name: str = "ba
     cfg = MpmConfig(**{**parts[0].cfg.as_dict(), "counts": counts,
                        "design_of_instance": list(design_of_instance) if design_of_instance is not None else None})
     return Workload(name, cfg, np.concatenate([p.x0 for p in parts], axis=1), v0, phi, mag,
-                    np.concatenate([p.field for p in parts], axis=0), target)
+                    np.concatenate([p.field for p in parts], axis=0), target, bmotion=parts[0].bmotion)
 
 
 def tiny_2d(seed: int = 0, n_steps: int = 20, res: int = 16, per_axis: int = 2, cells=(4, 2),
@@ -445,8 +451,9 @@ def with_steps(w: Workload, n_steps: int, checkpoint_every: Optional[int] = None
     cfg = MpmConfig(**{**w.cfg.as_dict(), "n_steps": n_steps})
     if checkpoint_every is not None:
         cfg.checkpoint_every = checkpoint_every
+    bm = None if w.bmotion is None else np.ascontiguousarray(w.bmotion[:, :n_steps])
     return Workload(w.name, cfg, w.x0, w.v0, w.phi, w.mag,
-                    np.ascontiguousarray(w.field[:, :n_steps]), w.target, dict(w.meta))
+                    np.ascontiguousarray(w.field[:, :n_steps]), w.target, dict(w.meta), bm)
 
 
 def expand_design(w: Workload, name: str) -> np.ndarray:

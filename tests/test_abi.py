@@ -48,13 +48,16 @@ def test_struct_layout_matches_header(tmp_path):
     fields = [f[0] for f in B.mpm_config._fields_]
     sfields = [f[0] for f in B.mpm_stats._fields_]
     dfields = [f[0] for f in B.mpm_design_config._fields_]
+    bfields = [f[0] for f in B.mpm_boundary._fields_]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpm_design.h"', "int main(void) {"]
     lines += [f'printf("%zu\\n", offsetof(mpm_config, {f}));' for f in fields]
     lines += ['printf("%zu\\n", sizeof(mpm_config));']
     lines += [f'printf("%zu\\n", offsetof(mpm_stats, {f}));' for f in sfields]
     lines += ['printf("%zu\\n", sizeof(mpm_stats));']
     lines += [f'printf("%zu\\n", offsetof(mpm_design_config, {f}));' for f in dfields]
-    lines += ['printf("%zu\\n", sizeof(mpm_design_config));', "return 0; }"]
+    lines += ['printf("%zu\\n", sizeof(mpm_design_config));']
+    lines += [f'printf("%zu\\n", offsetof(mpm_boundary, {f}));' for f in bfields]
+    lines += ['printf("%zu\\n", sizeof(mpm_boundary));', "return 0; }"]
     src.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     assert os.system(f"gcc -I {ROOT}/include -o {exe} {src}") == 0
@@ -62,6 +65,7 @@ def test_struct_layout_matches_header(tmp_path):
     want = [getattr(B.mpm_config, f).offset for f in fields] + [ctypes.sizeof(B.mpm_config)]
     want += [getattr(B.mpm_stats, f).offset for f in sfields] + [ctypes.sizeof(B.mpm_stats)]
     want += [getattr(B.mpm_design_config, f).offset for f in dfields] + [ctypes.sizeof(B.mpm_design_config)]
+    want += [getattr(B.mpm_boundary, f).offset for f in bfields] + [ctypes.sizeof(B.mpm_boundary)]
     assert got == want
 
 
@@ -137,6 +141,11 @@ def test_design_create_needs_region_exactly_with_regions(lib):
     h = ctypes.c_void_p()
     c = _dcfg(n_regions=4)
     assert lib.mpm_design_create(ctypes.byref(c), None, None, ctypes.byref(h), None) == B.MPM_ERR_ARG
+
+
+def test_set_boundaries_null_handle_fails_cleanly(lib):
+    assert lib.mpm_set_boundaries(None, 0, None, None, None) == B.MPM_ERR_ARG
+    assert B.MPM_MAX_BOUNDARIES == 8
 
 
 def test_design_and_adam_null_arguments_fail_cleanly(lib):
