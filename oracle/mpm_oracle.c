@@ -41,6 +41,12 @@
  *       total mass has zero loss.
  *   R10 Shape MSE is the mean over the instance's particles of |x_p(T) - xbar_p|^2.
  *   R11 Derivatives through floor() are zero (the weights are C1 across cells).
+ *   R18 Solid boxes beyond the walls (Eq. 18 in general form): every node
+ *       inside an axis-aligned box, faces included, is "on" it with the
+ *       outward normal of the nearest face (ties: lowest axis, low face
+ *       first); Coulomb and non-slip boxes act when (v - v_b) . n_b < 0,
+ *       attached boxes always set v = v_b; boxes act after the walls, in
+ *       order; a box's offset and v_b are given per substep.
  *
  * Layout: per particle x[3], v[3], C[9], F[9] (row-major 3x3; in 2D only the
  * leading 2 components / 2x2 block are used and the rest stay zero).
