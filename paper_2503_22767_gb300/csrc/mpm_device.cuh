@@ -511,60 +511,60 @@ __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int
             }
         }
     }
-    // replay the solid boxes, remembering the relative velocity entering
-    // each projection that fired (kind 1: set, 2: Coulomb)
-    int bkind[kMaxBoundaries], baxis[kMaxBoundaries];
-    float bsgn[kMaxBoundaries], bmu[kMaxBoundaries], bvin[kMaxBoundaries][D];
-    const int nb = P.bset ? min(P.bset->n, kMaxBoundaries) : 0;
-    for (int b = 0; b < nb; ++b) {
-        float vbx[D], sgn;
-        int axis;
-        bkind[b] = 0;
-        if (!box_contact<D>(P, b, step, c, vbx, axis, sgn)) continue;
-        const int kind = P.bset->box[b].kind;
-        if (kind != kBoundaryAttached && !(sgn * (v[axis] - vbx[axis]) < 0.0f)) continue;
-        baxis[b] = axis;
-        bsgn[b] = sgn;
-        bmu[b] = P.bset->box[b].mu;
-#pragma unroll
-        for (int i = 0; i < D; ++i) bvin[b][i] = v[i] - vbx[i];
-        if (kind == kBoundaryCoulomb) {
-            bkind[b] = 2;
-            coulomb_project<D>(axis, sgn, bmu[b], vbx, v);
-        } else {
-            bkind[b] = 1;
-#pragma unroll
-            for (int i = 0; i < D; ++i) v[i] = vbx[i];
-        }
-    }
+    // Reverse of the solid boxes, last first.  The velocity entering box b is
+    // recomputed by replaying boxes 0..b-1 from the walls' output (at most 8
+    // boxes, so no per-box arrays; nothing runs without boxes).  The box
+    // velocity is a constant, so the Coulomb Jacobian acts on the relative
+    // velocity r = v - v_b: out_t = r_t (1 + mu vn / u), out_n = 0,
+    // vn = sgn r_a, u = |r_t|.
     float vb[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) vb[i] = Vbar[i];
-    // reverse of the boxes (last first); the box velocity is a constant, so
-    // the Coulomb Jacobian acts on the relative velocity r = v - v_b:
-    // out_t = r_t (1 + mu vn / u), out_n = 0, vn = sgn r_a, u = |r_t|
+    const int nb = P.bset ? min(P.bset->n, kMaxBoundaries) : 0;
     for (int b = nb - 1; b >= 0; --b) {
-        if (bkind[b] == 1) {
+        float ve[D];
 #pragma unroll
-            for (int i = 0; i < D; ++i) vb[i] = 0.0f;
-        } else if (bkind[b] == 2) {
-            const int a = baxis[b];
-            const float mu = bmu[b], vn = bsgn[b] * bvin[b][a];
-            float t2 = 0.0f, tdot = 0.0f;
+        for (int i = 0; i < D; ++i) ve[i] = v[i];
+        for (int e = 0; e <= b; ++e) {
+            float vbx[D], sgn;
+            int axis;
+            if (!box_contact<D>(P, e, step, c, vbx, axis, sgn)) continue;
+            const int kind = P.bset->box[e].kind;
+            if (kind != kBoundaryAttached && !(sgn * (ve[axis] - vbx[axis]) < 0.0f)) continue;
+            if (e < b) {  // replay an earlier box
+                if (kind == kBoundaryCoulomb) {
+                    coulomb_project<D>(axis, sgn, P.bset->box[e].mu, vbx, ve);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) ve[i] = vbx[i];
+                }
+                continue;
+            }
+            // box b fired on the entering velocity ve
+            if (kind != kBoundaryCoulomb) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) vb[i] = 0.0f;
+                continue;
+            }
+            const float mu = P.bset->box[e].mu;
+            float r[D], t2 = 0.0f, tdot = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) r[i] = ve[i] - vbx[i];
+            const float vn = sgn * r[axis];
 #pragma unroll
             for (int i = 0; i < D; ++i)
-                if (i != a) {
-                    t2 += bvin[b][i] * bvin[b][i];
-                    tdot += vb[i] * bvin[b][i];
+                if (i != axis) {
+                    t2 += r[i] * r[i];
+                    tdot += vb[i] * r[i];
                 }
             const float u = sqrtf(t2);
             if (u > 0.0f && u + mu * vn > 0.0f) {
                 const float ru = 1.0f / u;
                 const float f = 1.0f + mu * vn * ru;
                 const float g = mu * vn * tdot * ru * ru * ru;
-                const float out_n = bsgn[b] * mu * tdot * ru;
+                const float out_n = sgn * mu * tdot * ru;
 #pragma unroll
-                for (int i = 0; i < D; ++i) vb[i] = (i == a) ? out_n : vb[i] * f - g * bvin[b][i];
+                for (int i = 0; i < D; ++i) vb[i] = (i == axis) ? out_n : vb[i] * f - g * r[i];
             } else {
 #pragma unroll
                 for (int i = 0; i < D; ++i) vb[i] = 0.0f;
