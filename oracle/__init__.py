@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("gravity", ctypes.c_double * 3),
         ("n_bnd", ctypes.c_int), ("pad2_", ctypes.c_int),
         ("bnd", ctypes.c_void_p), ("bmotion", ctypes.c_void_p),
+        ("fgrad", ctypes.c_void_p), ("g_fgrad", ctypes.c_void_p),
     ]
 
 
@@ -142,6 +143,13 @@ def params(cfg, n_steps=None, w=None) -> Params:
             m[:, :T, :, :d] = np.asarray(bm, dtype=np.float64)[:, :T]
             p._bm = m
             p.bmotion = m.ctypes.data
+    fg = getattr(w, "fgrad", None) if w is not None else None
+    if fg is not None:
+        T, d, ni = p.n_steps, int(cfg.dim), int(cfg.n_instances)
+        g = np.zeros((ni, max(T, 1), 3, 3))
+        g[:, :T, :d, :d] = np.asarray(fg, dtype=np.float64)[:, :T]
+        p._fg = g
+        p.fgrad = g.ctypes.data
     return p
 
 
@@ -260,6 +268,10 @@ def backward(w, dloss=None, ckpt_every=0, n_steps=None, sum_designs=True):
     g_x0 = np.zeros((n, 3)); g_v0 = np.zeros((n, 3))
     fld = field_to3(w.field, ni, max(T, 1))
     p = params(cfg, T, w)
+    g_fgrad = None
+    if getattr(w, "fgrad", None) is not None:
+        g_fgrad = np.zeros((ni, max(T, 1), 3, 3))
+        p.g_fgrad = g_fgrad.ctypes.data
     st = lib().orc_backward(ctypes.byref(p), ni, _ip(counts), _dp(inp["x0"]), _dp(inp["v0"]),
                             _dp(inp["phi"]), _dp(inp["mag"]), _dp(fld), _dp(inp["target"]),
                             _dp(dl), int(ckpt_every), _dp(g_phi), _dp(g_mag), _dp(g_field),
@@ -267,6 +279,7 @@ def backward(w, dloss=None, ckpt_every=0, n_steps=None, sum_designs=True):
     _check(st, "backward")
     g_mag_s = np.ascontiguousarray(g_mag[:, :d].T)
     out = dict(g_field=np.ascontiguousarray(g_field[:, :T, :d]),
+               g_fgrad=None if g_fgrad is None else np.ascontiguousarray(g_fgrad[:, :T, :d, :d]),
                g_x0=np.ascontiguousarray(g_x0[:, :d].T), g_v0=np.ascontiguousarray(g_v0[:, :d].T),
                status=st)
     if sum_designs:

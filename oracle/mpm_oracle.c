@@ -47,6 +47,12 @@
  *       first); Coulomb and non-slip boxes act when (v - v_b) . n_b < 0,
  *       attached boxes always set v = v_b; boxes act after the walls, in
  *       order; a box's offset and v_b are given per substep.
+ *   R19 Non-uniform applied field (the paper assumes a uniform one and notes
+ *       that non-uniform fields fit the framework): a linear field about the
+ *       domain centre, B(x) = B_a + G (x - x_c).  Eq. 7 / 31 use B at the
+ *       particle; the SIMP-scaled energy of Eq. 32 then depends on x, and
+ *       its negative x-derivative f = (phi^q V / mu0) G^T (F B~_r) enters the
+ *       particle's momentum in P2G.
  *
  * Layout: per particle x[3], v[3], C[9], F[9] (row-major 3x3; in 2D only the
  * leading 2 components / 2x2 block are used and the rest stay zero).
@@ -84,6 +90,12 @@ typedef struct {
     int pad2_;
     const double* bnd;
     const double* bmotion;
+    /* Non-uniform applied field (reading R19): B(x, t_n) = B_a[n] + G[n] (x - x_c),
+     * x_c the domain centre, G[n] = fgrad[(inst * n_steps + n) * 9 + 3 i + j]
+     * = dB_i/dx_j (row-major 3x3, d x d used), or NULL for a uniform field.
+     * The reverse writes dL/dG to g_fgrad (same layout) when it is given. */
+    const double* fgrad;
+    double* g_fgrad;
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -332,9 +344,34 @@ typedef struct {
 
 static double particle_mass(const orc_params* P, double phi) { return phi * P->rho0 * P->p_vol; } /* Eq. 33 */
 
-/* P2G (Eq. 14-15 with reading R1) for the particles [p0, p1) into one grid. */
+/* Field at a particle (R19): B_a + G (x - x_c), or B_a when Gn is NULL. */
+static void field_at(int d, const double* Ba, const double* Gn, const double* x, double* B) {
+    for (int i = 0; i < 3; ++i) B[i] = Ba[i];
+    if (!Gn) return;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) B[i] += Gn[3 * i + j] * (x[j] - 0.5);
+}
+
+/* Body force of a non-uniform field (R19): minus the position derivative of
+ * the SIMP-scaled magnetic energy of Eq. 31-32,
+ *   f = (phi^q V / mu0) G^T (F B~_r). */
+static void magnetic_force(const orc_params* P, const double* Gn, const double* F, const double* Br,
+                           double phi, double* f) {
+    int d = P->dim;
+    for (int i = 0; i < 3; ++i) f[i] = 0.0;
+    if (!Gn) return;
+    double c = ipow(phi, P->simp_q) * P->p_vol / MU0;
+    double FB[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i)
+        for (int k = 0; k < d; ++k) FB[i] += F[3 * i + k] * Br[k];
+    for (int j = 0; j < d; ++j)
+        for (int i = 0; i < d; ++i) f[j] += c * Gn[3 * i + j] * FB[i];
+}
+
+/* P2G (Eq. 14-15 with reading R1) for the particles [p0, p1) into one grid;
+ * Gn is the field gradient of this instance and substep, or NULL. */
 static int p2g(const orc_params* P, int p0, int p1, const state_t* s, const double* phi,
-               const double* mag, const double* Ba, double* gm, double* gmv) {
+               const double* mag, const double* Ba, const double* Gn, double* gm, double* gmv) {
     int d = P->dim;
     double G, K;
     lame(P, &G, &K);
@@ -344,11 +381,13 @@ static int p2g(const orc_params* P, int p0, int p1, const state_t* s, const doub
     for (int p = p0; p < p1; ++p) {
         stencil_t S;
         if (!make_stencil(P, s->x + 3 * p, &S)) return ORC_ERR_DOMAIN;
-        double Pst[9];
-        double J = orc_stress(d, G, K, s->F + 9 * p, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Ba, Pst);
+        double Pst[9], Bp[3], fp[3];
+        field_at(d, Ba, Gn, s->x + 3 * p, Bp);
+        double J = orc_stress(d, G, K, s->F + 9 * p, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Bp, Pst);
         if (!(J > 0.0)) status = ORC_ERR_NUMERIC;
         double mp = particle_mass(P, phi[p]);
         const double* F = s->F + 9 * p;
+        magnetic_force(P, Gn, F, mag + 3 * p, phi[p], fp);
         const double* C = s->C + 9 * p;
         double A[9] = {0};
         for (int i = 0; i < d; ++i)
@@ -365,7 +404,7 @@ static int p2g(const orc_params* P, int p0, int p1, const state_t* s, const doub
             for (int i = 0; i < d; ++i) {
                 double Ad = 0.0;
                 for (int j = 0; j < d; ++j) Ad += A[i * 3 + j] * dpos[j];
-                gmv[3 * node + i] += w * (mp * s->v[3 * p + i] + Ad);
+                gmv[3 * node + i] += w * (mp * s->v[3 * p + i] + P->dt * fp[i] + Ad);
             }
         }
     }
@@ -629,7 +668,8 @@ static int substep(sim_t* S, int n, const state_t* si, const double* phi, const 
         const double* Ba = field + ((size_t)inst * P->n_steps + n) * 3;
         memset(S->gm, 0, sizeof(double) * S->G);
         memset(S->gmv, 0, sizeof(double) * 3 * S->G);
-        int st = p2g(P, p0, p1, si, phi, mag, Ba, S->gm, S->gmv);
+        const double* Gn = P->fgrad ? P->fgrad + ((size_t)inst * P->n_steps + n) * 9 : NULL;
+        int st = p2g(P, p0, p1, si, phi, mag, Ba, Gn, S->gm, S->gmv);
         if (st == ORC_ERR_DOMAIN) return st;
         if (st != ORC_OK) worst = st;
         grid_update(P, S->gm, S->gmv, S->gv, n);
@@ -752,7 +792,8 @@ int orc_p2g_grid(const orc_params* P, int n_inst, const int* counts, const doubl
         double* gv = gv_out + (size_t)inst * 3 * S.G;
         memset(gm, 0, sizeof(double) * S.G);
         memset(gmv, 0, sizeof(double) * 3 * S.G);
-        st = p2g(P, S.offs[inst], S.offs[inst + 1], &s, phi, mag, Ba + 3 * inst, gm, gmv);
+        const double* Gn = P->fgrad ? P->fgrad + (size_t)inst * P->n_steps * 9 : NULL;
+        st = p2g(P, S.offs[inst], S.offs[inst + 1], &s, phi, mag, Ba + 3 * inst, Gn, gm, gmv);
         if (st == ORC_ERR_DOMAIN) { sim_free(&S); return st; }
         if (st != ORC_OK) worst = st;
         grid_update(P, gm, gmv, gv, 0);
@@ -857,7 +898,9 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
         /* recompute the forward grid of this substep */
         memset(S->gm, 0, sizeof(double) * Gn);
         memset(S->gmv, 0, sizeof(double) * 3 * Gn);
-        int st = p2g(P, p0, p1, sn, phi, mag, Ba, S->gm, S->gmv);
+        const double* Gf = P->fgrad ? P->fgrad + ((size_t)inst * P->n_steps + n) * 9 : NULL;
+        double* gGf = (P->fgrad && P->g_fgrad) ? P->g_fgrad + ((size_t)inst * P->n_steps + n) * 9 : NULL;
+        int st = p2g(P, p0, p1, sn, phi, mag, Ba, Gf, S->gm, S->gmv);
         if (st == ORC_ERR_DOMAIN) { free(Vbar); free(mbar); free(mvbar); return st; }
         grid_update(P, S->gm, S->gmv, S->gv, n);
         memset(Vbar, 0, sizeof(double) * 3 * Gn);
@@ -938,9 +981,11 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
             const double* F = sn->F + 9 * p;
             const double* C = sn->C + 9 * p;
             const double* v = sn->v + 3 * p;
-            double Pst[9];
-            orc_stress(d, G, K, F, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Ba, Pst);
+            double Pst[9], Bp[3], fp[3];
+            field_at(d, Ba, Gf, sn->x + 3 * p, Bp);
+            orc_stress(d, G, K, F, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Bp, Pst);
             double mp = particle_mass(P, phi[p]);
+            magnetic_force(P, Gf, F, mag + 3 * p, phi[p], fp);
             double A[9] = {0};
             for (int i = 0; i < d; ++i)
                 for (int j = 0; j < d; ++j) {
@@ -948,7 +993,7 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
                     for (int k = 0; k < d; ++k) PFt += Pst[i * 3 + k] * F[j * 3 + k];
                     A[i * 3 + j] = mp * C[i * 3 + j] - P->dt * kappa * P->p_vol * PFt;
                 }
-            double mpbar = 0.0, Abar[9] = {0};
+            double mpbar = 0.0, Abar[9] = {0}, fbar[3] = {0, 0, 0};
             double* xbn = an->x + 3 * p;
             double* vbn = an->v + 3 * p;
             for (int k = 0; k < n_offsets(d); ++k) {
@@ -957,8 +1002,12 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
                 stencil_node(P, &Sp, k, &node, &w, gw, dpos);
                 const double* mvb = mvbar + 3 * node;
                 double mb = mbar[node];
-                /* contribution value: w * (mb * mp + mvb . (mp v + A dpos)) */
+                /* contribution value: w * (mb * mp + mvb . (mp v + dt f + A dpos)) */
                 double inner = mb * mp;
+                for (int i = 0; i < d; ++i) {
+                    inner += mvb[i] * P->dt * fp[i];
+                    fbar[i] += w * P->dt * mvb[i];
+                }
                 double vcd = 0.0;
                 for (int i = 0; i < d; ++i) {
                     double Ad = 0.0, Cd = 0.0;
@@ -999,9 +1048,37 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
                     Pbar[i * 3 + j] = pb;
                     Fbn[i * 3 + j] += fb;
                 }
-            double phib = 0.0;
-            orc_stress_adjoint(d, G, K, F, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Ba, Pbar, Fbn,
-                               &phib, g_mag + 3 * p, gBa);
+            double phib = 0.0, Bpb[3] = {0, 0, 0};
+            orc_stress_adjoint(d, G, K, F, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Bp, Pbar, Fbn,
+                               &phib, g_mag + 3 * p, Bpb);
+            /* B_p = B_a + G (x_p - x_c): dL/dB_a, dL/dG and the x_p term */
+            for (int i = 0; i < d; ++i) gBa[i] += Bpb[i];
+            if (Gf) {
+                for (int i = 0; i < d; ++i)
+                    for (int j = 0; j < d; ++j) {
+                        if (gGf) gGf[3 * i + j] += Bpb[i] * (sn->x[3 * p + j] - 0.5);
+                        xbn[j] += Gf[3 * i + j] * Bpb[i];
+                    }
+                /* f = c G^T (F B~_r), c = phi^q V / mu0 */
+                const double* Br = mag + 3 * p;
+                double c = ipow(phi[p], P->simp_q) * P->p_vol / MU0;
+                double FB[3] = {0, 0, 0}, Gfb[3] = {0, 0, 0}, fraw = 0.0;
+                for (int i = 0; i < d; ++i)
+                    for (int k = 0; k < d; ++k) FB[i] += F[3 * i + k] * Br[k];
+                for (int i = 0; i < d; ++i)
+                    for (int j = 0; j < d; ++j) Gfb[i] += Gf[3 * i + j] * fbar[j]; /* G fbar */
+                for (int i = 0; i < d; ++i) {
+                    fraw += Gfb[i] * FB[i]; /* fbar . G^T F B~_r */
+                    for (int k = 0; k < d; ++k) {
+                        Fbn[3 * i + k] += c * Gfb[i] * Br[k];
+                        g_mag[3 * p + k] += c * Gfb[i] * F[3 * i + k];
+                    }
+                    if (gGf)
+                        for (int j = 0; j < d; ++j) gGf[3 * i + j] += c * FB[i] * fbar[j];
+                }
+                double dsdphi = P->simp_q > 0 ? P->simp_q * ipow(phi[p], P->simp_q - 1) : 0.0;
+                phib += dsdphi * P->p_vol / MU0 * fraw;
+            }
             g_phi[p] += phib + mpbar * P->rho0 * P->p_vol;
         }
     }

@@ -108,6 +108,10 @@ class Workload:
     # per box and substep: offset from the t = 0 box and velocity v_b,
     # [n_boxes][n_steps][2][d]; None for static boxes
     bmotion: Optional[np.ndarray] = None
+    # gradient of a non-uniform applied field, dB_i/dx_j per instance and
+    # substep about the domain centre, [n_instances][n_steps][d][d]; None for
+    # a uniform field
+    fgrad: Optional[np.ndarray] = None
 
 
 # ---------------------------------------------------------------------------
@@ -393,7 +397,9 @@ def batch(parts, design_of_instance: Optional[List[int]] = None, name: str = "ba
     cfg = MpmConfig(**{**parts[0].cfg.as_dict(), "counts": counts,
                        "design_of_instance": list(design_of_instance) if design_of_instance is not None else None})
     return Workload(name, cfg, np.concatenate([p.x0 for p in parts], axis=1), v0, phi, mag,
-                    np.concatenate([p.field for p in parts], axis=0), target, bmotion=parts[0].bmotion)
+                    np.concatenate([p.field for p in parts], axis=0), target, bmotion=parts[0].bmotion,
+                    fgrad=(np.concatenate([p.fgrad for p in parts], axis=0)
+                           if all(p.fgrad is not None for p in parts) else None))
 
 
 def tiny_2d(seed: int = 0, n_steps: int = 20, res: int = 16, per_axis: int = 2, cells=(4, 2),
@@ -452,8 +458,9 @@ def with_steps(w: Workload, n_steps: int, checkpoint_every: Optional[int] = None
     if checkpoint_every is not None:
         cfg.checkpoint_every = checkpoint_every
     bm = None if w.bmotion is None else np.ascontiguousarray(w.bmotion[:, :n_steps])
+    fg = None if w.fgrad is None else np.ascontiguousarray(w.fgrad[:, :n_steps])
     return Workload(w.name, cfg, w.x0, w.v0, w.phi, w.mag,
-                    np.ascontiguousarray(w.field[:, :n_steps]), w.target, dict(w.meta), bm)
+                    np.ascontiguousarray(w.field[:, :n_steps]), w.target, dict(w.meta), bm, fg)
 
 
 def expand_design(w: Workload, name: str) -> np.ndarray:
