@@ -262,6 +262,30 @@ typedef struct {
 int mpm_set_boundaries(mpm_handle* h, int n, const mpm_boundary* boxes, const float* motion, void* cuda_stream);
 
 /*
+ * Non-uniform applied field.  The paper assumes a uniform field and notes that
+ * non-uniform fields (e.g. from permanent magnets) fit the same framework
+ * (Section 5).  Here the field is linear about the domain centre x_c:
+ *   B(x, t_n) = field[inst][n] + G[inst][n] (x - x_c),
+ * with G = dB_i/dx_j.  Eq. 7 / 31 then use B at the particle, and the
+ * SIMP-scaled energy of Eq. 32 depends on position.  Its negative gradient is
+ * a body force on every particle,
+ *   f_p = (phi_bar_p^q V_p / mu0) G^T (F_p B~_r,p),
+ * added to the particle's momentum in P2G (Eq. 15).  The reverse mode gives
+ * dL/dG besides the other gradients.
+ *
+ * mpm_set_field_gradient copies grad (device, [n_instances][n_steps][dim][dim],
+ * row-major per substep) into storage from mpm_create, or removes it (NULL).
+ * It synchronises cuda_stream, and a following mpm_backward needs a new
+ * mpm_forward.  With a gradient set, the shared-memory tiles
+ * (MPM_OPT_TILE) are not used, and mpm_substep_noalloc stays uniform.
+ * mpm_field_gradient_grad copies dL/dG (same layout) after mpm_backward.
+ * Errors: MPM_ERR_ARG, MPM_ERR_STATE (no gradient set, or no backward yet),
+ * MPM_ERR_CUDA.
+ */
+int mpm_set_field_gradient(mpm_handle* h, const float* grad, void* cuda_stream);
+int mpm_field_gradient_grad(mpm_handle* h, float* g_grad, void* cuda_stream);
+
+/*
  * Autotuner (not in the paper; a launch-configuration search of this
  * library).  Times forward + backward passes over the first sample_substeps
  * substeps (0 = two checkpoint segments) of the inputs staged by the last

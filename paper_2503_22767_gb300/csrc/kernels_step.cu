@@ -30,7 +30,9 @@ constexpr int kMinBlocksForward3 = 4;
 namespace {
 
 // 3D: at most 64 registers (32 warps per SM) to keep more gathers in flight
-template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE>
+// EXT: P.ext is set (solid boxes or a non-uniform field); without it the
+// kernel carries no code for the field gradient.
+template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT>
 __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
     // Early loads: with the grid operation in its own kernel, this kernel's
@@ -161,6 +163,18 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
         for (int i = 0; i < D; ++i) {
             Br[i] = a.mag[(long long)i * np + p];
             Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
+        }
+        if (EXT && P.ext->fgrad) {
+            const float* Gn = P.ext->fgrad + ((long long)inst * P.n_steps + a.n_p2g) * D * D;
+            field_at_particle<D>(Gn, x, Ba);
+            // body force of the non-uniform field, folded into the momentum
+            // m v (f and m both vanish with phi, so m > 0 whenever f != 0)
+            float f[D];
+            magnetic_force<D>(Gn, F, Br, S.s, P, f);
+            if (mp > 0.0f) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[i] += P.dt * f[i] / mp;
+            }
         }
         piola<D>(S, Br, Ba, Pk);
         const float sc = P.dt * P.kappa * P.p_vol;
@@ -316,9 +330,16 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     float bab[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) bab[i] = 0.0f;
+    // non-uniform field: G of this substep (uniform over the launch), and the
+    // particle's contribution to dL/dG
+    const bool has_fgrad = P2GT && P.ext && P.ext->fgrad;
+    float gG[D * D];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) gG[i] = 0.0f;
     if (P2GT) {
         if (active) {
             const int n = a.n_p2g;
+            const float* Gn = has_fgrad ? P.ext->fgrad + ((long long)inst * P.n_steps + n) * D * D : nullptr;
             float(&x)[D] = x_n;
             float(&v)[D] = v_n;
             float(&F)[D][D] = F_n;
@@ -330,6 +351,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                 Br[i] = a.mag[(long long)i * np + p];
                 Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + n) * D + i);
             }
+            if (Gn) field_at_particle<D>(Gn, x, Ba);
             Stencil<D> s;
             if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
             StressParts<D> S;
@@ -363,6 +385,12 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     ar += A[i][j] * s.r[j];
                 }
                 u[i] = mp * v[i] - P.dx * ar;
+            }
+            if (Gn) {  // the body force is part of the particle's momentum term
+                float f[D];
+                magnetic_force<D>(Gn, F, Br, S.s, P, f);
+#pragma unroll
+                for (int i = 0; i < D; ++i) u[i] += P.dt * f[i];
             }
             const float4* __restrict__ gi = (FUSE ? a.accP : a.gadj) + (long long)inst * P.nodes;
             const float4* __restrict__ vbi = FUSE ? a.VbarIn + (long long)inst * P.nodes : nullptr;
@@ -461,6 +489,43 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
             for (int i = 0; i < D; ++i) brb[i] = 0.0f;
             piola_adjoint<D>(F, phi, S, Br, Ba, Pb, P, Fb, phib, brb, bab);
             float gph = phib + mpb * P.rho0 * P.p_vol;
+            if (Gn) {
+                // B at the particle = B_a + G (x - x_c): dL/dB_a stays in bab,
+                // dL/dG += bab (x - x_c)^T, xbar += G^T bab
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        gG[i * D + j] += bab[i] * (x[j] - 0.5f);
+                        xb[j] += __ldg(Gn + i * D + j) * bab[i];
+                    }
+                // body force f = c G^T (F B~_r), c = s V / mu0, whose adjoint is
+                // fbar = dt sum_i w mvb_i = dt S0
+                const float c = S.s * P.p_vol * (1.0f / kMu0);
+                float FB[D], Gfb[D], fraw = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    FB[i] = Br[i];
+                    Gfb[i] = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        FB[i] += F[i][k] * Br[k];
+                        Gfb[i] += __ldg(Gn + i * D + k) * (P.dt * S0[k]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    fraw += Gfb[i] * FB[i];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        Fb[i][k] += c * Gfb[i] * Br[k];
+                        brb[k] += c * Gfb[i] * ((i == k ? 1.0f : 0.0f) + F[i][k]);
+                        gG[i * D + k] += c * FB[i] * (P.dt * S0[k]);
+                    }
+                }
+                const float ds = P.simp_q > 0 ? (float)P.simp_q * int_pow(phi, P.simp_q - 1) : 0.0f;
+                gph += ds * P.p_vol * (1.0f / kMu0) * fraw;
+            }
             // locomotion seed on state n (n >= 1), Eq. 40
             if (P.loss_kind == 1 && n >= 1) {
                 const float M = a.Minst[inst];
@@ -478,6 +543,9 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
         }
         warp_add_per_instance<D>(bab, inst, a.gfield + (long long)a.n_p2g * D,
                                  (long long)P.n_steps * D);
+        if (has_fgrad)  // uniform over the launch: every lane takes part
+            warp_add_per_instance<D * D>(gG, inst, P.ext->gfgrad + (long long)a.n_p2g * D * D,
+                                         (long long)P.n_steps * D * D);
         if (!G2PT && active) {
             store_vec<D>(a.adj, L::X, np, p, xb);
             store_vec<D>(a.adj, L::V, np, p, vb);
@@ -761,14 +829,20 @@ static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, cons
     if (P.n_total == 0 && !(FUSE && a.zero4)) return cudaSuccess;
     long long threads = P.n_total > 0 ? P.n_total : block;
     dim3 grid(blocks_for(threads, block));
+    const bool ext = P.ext != nullptr;
     if (g2p && p2g) {
-        if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE>, grid, block, st, P, a);
-        return launch_chain(P, k_forward<D, true, true, false, FUSE>, grid, block, st, P, a);
+        if (ext) {
+            if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE, true>, grid, block, st, P, a);
+            return launch_chain(P, k_forward<D, true, true, false, FUSE, true>, grid, block, st, P, a);
+        }
+        if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE, false>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, true, true, false, FUSE, false>, grid, block, st, P, a);
     } else if (g2p) {
-        if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE>, grid, block, st, P, a);
-        return launch_chain(P, k_forward<D, true, false, false, FUSE>, grid, block, st, P, a);
+        if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE, false>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, true, false, false, FUSE, false>, grid, block, st, P, a);
     } else {
-        return launch_chain(P, k_forward<D, false, true, false, FUSE>, grid, block, st, P, a);
+        if (ext) return launch_chain(P, k_forward<D, false, true, false, FUSE, true>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, false, true, false, FUSE, false>, grid, block, st, P, a);
     }
     return cudaGetLastError();
 }

@@ -32,10 +32,11 @@ struct Params {
     int pdl;  // per-substep kernels launched with programmatic dependent launch
     int adj_blocks;  // register budget of the adjoint particle kernel: 256-thread blocks per SM (2 or 3)
     int box;         // 1: warps stage their stencil nodes in shared memory before gathering
-    // solid boxes of Eq. 18 beyond the walls (device memory), or null.  One
-    // pointer keeps the parameter block (and the transfer kernels' register
-    // allocation) as small as without boxes.
-    const struct BoundarySet* bset;
+    // solid boxes of Eq. 18 beyond the walls and a non-uniform applied field
+    // (device memory), or null for neither.  One pointer keeps the parameter
+    // block (and the transfer kernels' register allocation) as small as
+    // without them.
+    const struct Extras* ext;
 };
 
 constexpr int kMaxBoundaries = 8;
@@ -47,11 +48,16 @@ struct Boundary {
     float lo[3], hi[3];  // axis-aligned box at t = 0
 };
 
-struct BoundarySet {
+struct Extras {
     int n;                        // boxes in use (<= kMaxBoundaries)
     Boundary box[kMaxBoundaries];
     const float* motion;          // per box and substep: offset, velocity v_b
                                   // ([b][n_steps][2][D]), or null for static boxes
+    // non-uniform applied field B(x, t_n) = B_a[n] + G[n] (x - x_c), x_c the
+    // domain centre: G per instance and substep, [inst][n_steps][D][D]
+    // (dB_i/dx_j), or null for a uniform field; gfgrad receives dL/dG
+    const float* fgrad;
+    float* gfgrad;
 };
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
@@ -355,14 +361,48 @@ __device__ __forceinline__ void node_coords(int local, int res, int (&c)[D]) {
     }
 }
 
+// Non-uniform applied field, linear about the domain centre x_c = (1/2, ...):
+// B at the particle is B_a + G (x - x_c), with G row-major dB_i/dx_j.
+template <int D>
+__device__ __forceinline__ void field_at_particle(const float* __restrict__ Gn, const float (&x)[D],
+                                                  float (&B)[D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) B[i] += __ldg(Gn + i * D + j) * (x[j] - 0.5f);
+}
+
+// Body force of the non-uniform field: minus the position derivative of the
+// SIMP-scaled magnetic energy (Eq. 31-32), f = (s V / mu0) G^T (F B~_r), with
+// F = I + E and s = phi^q.
+template <int D>
+__device__ __forceinline__ void magnetic_force(const float* __restrict__ Gn, const float (&E)[D][D],
+                                               const float (&Br)[D], float s, const Params& P, float (&f)[D]) {
+    float FB[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        FB[i] = Br[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) FB[i] += E[i][k] * Br[k];
+    }
+    const float c = s * P.p_vol * (1.0f / kMu0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += __ldg(Gn + i * D + j) * FB[i];
+        f[j] = c * acc;
+    }
+}
+
 // Solid box b at substep `step` and node c: true when the node lies inside
 // the (moved) box, with the box velocity vb and the outward normal sgn e_axis
 // of the face nearest to the node (ties: lowest axis, low face first).
 template <int D>
 __device__ __forceinline__ bool box_contact(const Params& P, int b, int step, const int (&c)[D],
                                             float (&vb)[D], int& axis, float& sgn) {
-    const Boundary B = P.bset->box[b];
-    const float* mo = P.bset->motion ? P.bset->motion + ((long long)b * P.n_steps + step) * 2 * D : nullptr;
+    const Boundary B = P.ext->box[b];
+    const float* mo = P.ext->motion ? P.ext->motion + ((long long)b * P.n_steps + step) * 2 * D : nullptr;
     bool inside = true;
     float best = 3.0e38f;
     axis = 0;
@@ -443,15 +483,15 @@ __device__ __forceinline__ void grid_velocity(const Params& P, const int (&c)[D]
     }
     // solid boxes after the walls, in order: attached boxes set v = v_b; the
     // others act when the velocity relative to the box points into it
-    const int nbox = P.bset ? P.bset->n : 0;
+    const int nbox = P.ext ? P.ext->n : 0;
     for (int b = 0; b < nbox; ++b) {
         float vb[D], sgn;
         int axis;
         if (!box_contact<D>(P, b, step, c, vb, axis, sgn)) continue;
-        const int kind = P.bset->box[b].kind;
+        const int kind = P.ext->box[b].kind;
         if (kind != kBoundaryAttached && !(sgn * (v[axis] - vb[axis]) < 0.0f)) continue;
         if (kind == kBoundaryCoulomb) {
-            coulomb_project<D>(axis, sgn, P.bset->box[b].mu, vb, v);
+            coulomb_project<D>(axis, sgn, P.ext->box[b].mu, vb, v);
         } else {
 #pragma unroll
             for (int i = 0; i < D; ++i) v[i] = vb[i];
@@ -520,7 +560,7 @@ __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int
     float vb[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) vb[i] = Vbar[i];
-    const int nb = P.bset ? min(P.bset->n, kMaxBoundaries) : 0;
+    const int nb = P.ext ? min(P.ext->n, kMaxBoundaries) : 0;
     for (int b = nb - 1; b >= 0; --b) {
         float ve[D];
 #pragma unroll
@@ -529,11 +569,11 @@ __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int
             float vbx[D], sgn;
             int axis;
             if (!box_contact<D>(P, e, step, c, vbx, axis, sgn)) continue;
-            const int kind = P.bset->box[e].kind;
+            const int kind = P.ext->box[e].kind;
             if (kind != kBoundaryAttached && !(sgn * (ve[axis] - vbx[axis]) < 0.0f)) continue;
             if (e < b) {  // replay an earlier box
                 if (kind == kBoundaryCoulomb) {
-                    coulomb_project<D>(axis, sgn, P.bset->box[e].mu, vbx, ve);
+                    coulomb_project<D>(axis, sgn, P.ext->box[e].mu, vbx, ve);
                 } else {
 #pragma unroll
                     for (int i = 0; i < D; ++i) ve[i] = vbx[i];
@@ -546,7 +586,7 @@ __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int
                 for (int i = 0; i < D; ++i) vb[i] = 0.0f;
                 continue;
             }
-            const float mu = P.bset->box[e].mu;
+            const float mu = P.ext->box[e].mu;
             float r[D], t2 = 0.0f, tdot = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; ++i) r[i] = ve[i] - vbx[i];

@@ -109,7 +109,11 @@ struct mpm_handle {
 
     float4* acc3 = nullptr;   // fused mode: three rotating P2G accumulators
     float4* Vbar3 = nullptr;  // fused mode: three rotating G2P^T scatter targets
-    mpm::BoundarySet* d_bset = nullptr;  // solid boxes (Eq. 18) read by the grid operation
+    mpm::Extras* d_ext = nullptr;        // solid boxes (Eq. 18) and the field gradient
+    mpm::Extras ext_host{};              // host copy of *d_ext
+    float* d_fgrad = nullptr;            // dB/dx per instance and substep
+    float* d_gfgrad = nullptr;           // its gradient, filled by the backward pass
+    bool backward_done = false;
     float* d_bmotion = nullptr;          // their offsets and velocities per substep
 
     // --- options ---
@@ -470,7 +474,9 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->gphi_d, h->Nd);
     ALLOC(h->gmag_d, d * h->Nd);
     ALLOC(h->gfield_d, (long long)h->n_inst * h->T * d);
-    ALLOC(h->d_bset, 1);
+    ALLOC(h->d_ext, 1);
+    ALLOC(h->d_fgrad, (long long)h->n_inst * h->T * d * d);
+    ALLOC(h->d_gfgrad, (long long)h->n_inst * h->T * d * d);
     ALLOC(h->d_bmotion, (long long)mpm::kMaxBoundaries * h->T * 2 * d);
     ALLOC(h->st_x0, d * h->N);
     ALLOC(h->st_v0, d * h->N);
@@ -499,6 +505,10 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
         MPM_CUDA(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return MPM_OK;
 }
+
+// The tiled kernels take the uniform field only; a field gradient uses the
+// direct kernels.
+bool use_tiles(const mpm_handle* h) { return h->tile && !h->ext_host.fgrad; }
 
 StepArgs base_args(mpm_handle* h) {
     StepArgs a;
@@ -607,7 +617,7 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
             }
             if (!p2g) a.acc = nullptr;
             if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, all ? kFusedStore : kFused), st, [&] {
-                     return h->tile ? mpm::launch_forward_tiled(d, all, fuse, P, a, h->block, st)
+                     return use_tiles(h) ? mpm::launch_forward_tiled(d, all, fuse, P, a, h->block, st)
                                     : mpm::launch_forward(d, true, p2g, all, fuse, P, a, h->block, st);
                  })))
                 return rc;
@@ -705,7 +715,7 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
             a.V = gV(k);
         }
         if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
-                 return h->tile ? mpm::launch_forward_tiled(d, true, fuse_rec, P, a, h->block, st)
+                 return use_tiles(h) ? mpm::launch_forward_tiled(d, true, fuse_rec, P, a, h->block, st)
                                 : mpm::launch_forward(d, true, p2g, true, fuse_rec, P, a, h->block, st);
              })))
             return rc;
@@ -794,7 +804,7 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
         if (fuse_v) a.accG = gacc(k - 1);
         else a.V = gV(k - 1);
         if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
-                 return h->tile ? mpm::launch_adjoint_tiled(d, fuse, fuse_v, P, a, h->block, st)
+                 return use_tiles(h) ? mpm::launch_adjoint_tiled(d, fuse, fuse_v, P, a, h->block, st)
                                 : mpm::launch_adjoint(d, true, true, fuse, fuse_v, P, a, h->block, st);
              })))
             return rc;
@@ -832,6 +842,8 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
     MPM_CUDA(h, cudaMemsetAsync(h->gphi_d, 0, sizeof(float) * h->Nd, st));
     MPM_CUDA(h, cudaMemsetAsync(h->gmag_d, 0, sizeof(float) * d * h->Nd, st));
     MPM_CUDA(h, cudaMemsetAsync(h->gfield_d, 0, sizeof(float) * h->n_inst * h->T * d, st));
+    if (h->ext_host.fgrad)
+        MPM_CUDA(h, cudaMemsetAsync(h->d_gfgrad, 0, sizeof(float) * h->n_inst * h->T * d * d, st));
     if (h->fuse_adj) MPM_CUDA(h, cudaMemsetAsync(h->Vbar3, 0, sizeof(float4) * 3 * G, st));
     else MPM_CUDA(h, cudaMemsetAsync(h->Vbar, 0, sizeof(float4) * G, st));
     const int T = h->tune_T > 0 ? std::min(h->T, h->tune_T) : h->T;
@@ -922,6 +934,7 @@ int forward_impl(mpm_handle* h, const float* x0, const float* v0, const float* p
     if (!field) return fail(h, MPM_ERR_ARG, "field is required");
     if (h->N > 0 && P.loss_kind == 0 && !target) return fail(h, MPM_ERR_ARG, "target is required for loss_kind 0");
     h->forward_done = false;
+    h->backward_done = false;
     int rc;
     // stage the inputs into library-owned buffers (the passes read only those)
     if ((rc = dcopy(h, h->st_x0, x0, sizeof(float) * d * h->N, st))) return rc;
@@ -958,7 +971,9 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
     if (g_mag && (rc = dcopy(h, g_mag, h->gmag_d, sizeof(float) * d * h->Nd, st))) return rc;
     if (g_field && (rc = dcopy(h, g_field, h->gfield_d, sizeof(float) * h->n_inst * h->T * d, st)))
         return rc;
-    return finish(h, 1, st);
+    int rc2 = finish(h, 1, st);
+    if (rc2 == MPM_OK) h->backward_done = true;
+    return rc2;
 }
 
 // ---------------------------------------------------------------------------
@@ -1259,11 +1274,24 @@ int mpm_sort_particles(mpm_handle* h, const float* x, int* keys, int* perm, void
     return MPM_OK;
 }
 
+// Copy the host mirror of the boxes / field gradient to the device and point
+// the parameter block at it (or at nothing).  Captured graphs hold the old
+// parameter block and are dropped; a backward needs a new forward.
+static int upload_extras(mpm_handle* h, cudaStream_t st) {
+    MPM_CUDA(h, cudaMemcpyAsync(h->d_ext, &h->ext_host, sizeof(mpm::Extras), cudaMemcpyHostToDevice, st));
+    MPM_CUDA(h, cudaStreamSynchronize(st));
+    drop_graphs(h);
+    h->P.ext = (h->ext_host.n > 0 || h->ext_host.fgrad) ? h->d_ext : nullptr;
+    h->forward_done = false;
+    h->backward_done = false;
+    return MPM_OK;
+}
+
 int mpm_set_boundaries(mpm_handle* h, int n, const mpm_boundary* boxes, const float* motion, void* cuda_stream) {
     if (!h) return MPM_ERR_ARG;
     if (n < 0 || n > MPM_MAX_BOUNDARIES) return fail(h, MPM_ERR_ARG, "n must be in [0, MPM_MAX_BOUNDARIES]");
     if (n > 0 && !boxes) return fail(h, MPM_ERR_ARG, "boxes is NULL");
-    mpm::BoundarySet hs{};
+    mpm::Extras hs = h->ext_host;
     hs.n = n;
     for (int b = 0; b < n; ++b) {
         const mpm_boundary& B = boxes[b];
@@ -1281,15 +1309,33 @@ int mpm_set_boundaries(mpm_handle* h, int n, const mpm_boundary* boxes, const fl
         }
     }
     hs.motion = (n > 0 && motion) ? h->d_bmotion : nullptr;
+    for (int b = n; b < mpm::kMaxBoundaries; ++b) hs.box[b] = mpm::Boundary{};
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (hs.motion)
         MPM_CUDA(h, cudaMemcpyAsync(h->d_bmotion, motion, sizeof(float) * (size_t)n * h->T * 2 * h->dim,
                                     cudaMemcpyDeviceToDevice, st));
-    MPM_CUDA(h, cudaMemcpyAsync(h->d_bset, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
-    MPM_CUDA(h, cudaStreamSynchronize(st));  // hs lives on this stack frame
-    drop_graphs(h);
-    h->P.bset = n > 0 ? h->d_bset : nullptr;
-    h->forward_done = false;  // a backward must replay the forward's boundaries
+    h->ext_host = hs;
+    return upload_extras(h, st);
+}
+
+int mpm_set_field_gradient(mpm_handle* h, const float* grad, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t n = (size_t)h->n_inst * h->T * h->dim * h->dim;
+    if (grad) MPM_CUDA(h, cudaMemcpyAsync(h->d_fgrad, grad, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    h->ext_host.fgrad = grad ? h->d_fgrad : nullptr;
+    h->ext_host.gfgrad = grad ? h->d_gfgrad : nullptr;
+    return upload_extras(h, st);
+}
+
+int mpm_field_gradient_grad(mpm_handle* h, float* g_grad, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    if (!g_grad) return fail(h, MPM_ERR_ARG, "g_grad is NULL");
+    if (!h->ext_host.fgrad) return fail(h, MPM_ERR_STATE, "no field gradient is set");
+    if (!h->backward_done) return fail(h, MPM_ERR_STATE, "mpm_field_gradient_grad needs a successful mpm_backward");
+    const size_t n = (size_t)h->n_inst * h->T * h->dim * h->dim;
+    MPM_CUDA(h, cudaMemcpyAsync(g_grad, h->d_gfgrad, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)cuda_stream));
     return MPM_OK;
 }
 

@@ -184,6 +184,23 @@ class Simulator:
         self._check(st, "mpm_set_boundaries")
         self.generation += 1
 
+    def set_field_gradient(self, grad):
+        """Non-uniform applied field (see mpm_set_field_gradient): grad is a
+        CUDA tensor [n_instances][n_steps][d][d] of dB_i/dx_j about the
+        domain centre, or None for a uniform field."""
+        grad = _dev(grad, (self.n_inst, self.T, self.d, self.d), "grad")
+        self._check(self.lib.mpm_set_field_gradient(self.handle, B.fptr(grad), _stream()),
+                    "mpm_set_field_gradient")
+        self.generation += 1
+
+    def field_gradient_grad(self):
+        """dL/dG of the last backward, [n_instances][n_steps][d][d]."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        g = torch.empty((self.n_inst, self.T, self.d, self.d), device=dev)
+        self._check(self.lib.mpm_field_gradient_grad(self.handle, B.fptr(g), _stream()),
+                    "mpm_field_gradient_grad")
+        return g
+
     def autotune(self, cache_path=None, sample_substeps=0):
         """Pick block size, grid fusion, the adjoint register budget and warp-staged gathers by timing them on the inputs
         of the last forward (see mpm_autotune); returns the chosen options.

@@ -145,6 +145,8 @@ def test_design_create_needs_region_exactly_with_regions(lib):
 
 def test_set_boundaries_null_handle_fails_cleanly(lib):
     assert lib.mpm_set_boundaries(None, 0, None, None, None) == B.MPM_ERR_ARG
+    assert lib.mpm_set_field_gradient(None, None, None) == B.MPM_ERR_ARG
+    assert lib.mpm_field_gradient_grad(None, None, None) == B.MPM_ERR_ARG
     assert B.MPM_MAX_BOUNDARIES == 8
 
 
