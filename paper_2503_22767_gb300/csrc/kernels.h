@@ -52,6 +52,22 @@ cudaError_t launch_forward(int dim, bool g2p, bool p2g, bool write_all, bool fus
 // G2P^T substep from a.accG through the grid operation (fuse implies fuse_v).
 cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, bool fuse_v, const Params& P,
                            const StepArgs& a, int block, cudaStream_t st);
+// Per-dimension instantiations (D = 2, 3) of the two calls above, each in a
+// translation unit of its own.
+template <int D>
+cudaError_t launch_forward_dim(bool g2p, bool p2g, bool write_all, bool fuse, const Params& P,
+                               const StepArgs& a, int block, cudaStream_t st);
+template <int D>
+cudaError_t launch_adjoint_dim(bool p2gt, bool g2pt, bool fuse, bool fuse_v, const Params& P,
+                               const StepArgs& a, int block, cudaStream_t st);
+extern template cudaError_t launch_forward_dim<2>(bool, bool, bool, bool, const Params&, const StepArgs&,
+                                                  int, cudaStream_t);
+extern template cudaError_t launch_forward_dim<3>(bool, bool, bool, bool, const Params&, const StepArgs&,
+                                                  int, cudaStream_t);
+extern template cudaError_t launch_adjoint_dim<2>(bool, bool, bool, bool, const Params&, const StepArgs&,
+                                                  int, cudaStream_t);
+extern template cudaError_t launch_adjoint_dim<3>(bool, bool, bool, bool, const Params&, const StepArgs&,
+                                                  int, cudaStream_t);
 // Shared-memory tiled versions (kernels_tiled.cu): the forward kernel with
 // G2P (and P2G when a.acc is set), the adjoint kernel with P2G^T and G2P^T.
 cudaError_t launch_forward_tiled(int dim, bool write_all, bool fuse, const Params& P,

@@ -4,7 +4,9 @@
 //                    (Eq. 14-15, stress Eq. 7 / 31-33)
 //   k_adjoint_tiled  P2G^T of substep n + G2P^T of substep n-1 (Section 2.3)
 //
-// They compute exactly what k_forward / k_adjoint (kernels_step.cu) compute;
+// They compute exactly what k_forward / k_adjoint (particle_kernels.cuh)
+// compute without solid boxes or a field gradient (with either set the runtime
+// runs those instead);
 // only the grid traffic differs (see tile.cuh): node values are staged once
 // per CTA (with the grid operation, Eq. 16-18, or its reverse applied per tile
 // node in fused-grid mode) and scatters are warp-aggregated into a
@@ -25,7 +27,7 @@ __device__ __forceinline__ float4 gather_node(const TileBox<D>& box, const float
                                               const NodeTerm<D>& t, const Params& P, int step) {
     if (box.use) return tile[box_index<D>(box, t.c)];
     float gv[D];
-    node_velocity<D, FUSE>(direct, t, P, gv, step);
+    node_velocity<D, FUSE, false>(direct, t, P, gv, step);
     return make_float4(gv[0], gv[1 % D], D == 3 ? gv[2 % D] : 0.0f, 0.0f);
 }
 
@@ -38,7 +40,7 @@ __device__ __forceinline__ float4 stage_velocity(const float4* __restrict__ src,
     if (!FUSE) return g;
     float mv[D], v[D];
     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-    grid_velocity<D>(P, c, g.x, mv, v, step);
+    grid_velocity<D, false>(P, c, g.x, mv, v, step);
     return make_float4(v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f, 0.0f);
 }
 
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
                 float mv[D], vbv[D], mvb[D], mbv;
                 unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
                 unpack3<D>(__ldg(a.VbarIn + gi), vbv);
-                grid_velocity_adjoint<D>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
+                grid_velocity_adjoint<D, false>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
                 tileG[t] = pack4<D>(mbv, mvb);
             } else {
                 tileG[t] = __ldg(a.gadj + gi);
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiled(Params P, StepArgs a) {
                 float mv[D], vbv[D], mvb[D], mbv;
                 unpack3<D>(make_float4(g4.y, g4.z, g4.w, 0.0f), mv);
                 unpack3<D>(__ldg(a.VbarIn + off + t.node), vbv);
-                grid_velocity_adjoint<D>(P, t.c, g4.x, mv, vbv, mbv, mvb, a.n_p2g);
+                grid_velocity_adjoint<D, false>(P, t.c, g4.x, mv, vbv, mbv, mvb, a.n_p2g);
                 g = pack4<D>(mbv, mvb);
             } else {
                 g = __ldg(a.gadj + off + t.node);

@@ -2,7 +2,7 @@
 //
 // Templated on the spatial dimension D (2 or 3).  Everything here is
 // single-precision and register-resident; the kernels that use it live in
-// kernels_step.cu.  Equations refer to arxiv 2503.22767.
+// particle_kernels.cuh and kernels_step.cu.  Equations refer to arxiv 2503.22767.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -399,10 +399,10 @@ __device__ __forceinline__ void magnetic_force(const float* __restrict__ Gn, con
 // the (moved) box, with the box velocity vb and the outward normal sgn e_axis
 // of the face nearest to the node (ties: lowest axis, low face first).
 template <int D>
-__device__ __forceinline__ bool box_contact(const Params& P, int b, int step, const int (&c)[D],
-                                            float (&vb)[D], int& axis, float& sgn) {
-    const Boundary B = P.ext->box[b];
-    const float* mo = P.ext->motion ? P.ext->motion + ((long long)b * P.n_steps + step) * 2 * D : nullptr;
+__device__ __forceinline__ bool box_contact(const Extras* ext, float dx, int n_steps, int b, int step,
+                                            const int* c, float (&vb)[D], int& axis, float& sgn) {
+    const Boundary B = ext->box[b];
+    const float* mo = ext->motion ? ext->motion + ((long long)b * n_steps + step) * 2 * D : nullptr;
     bool inside = true;
     float best = 3.0e38f;
     axis = 0;
@@ -411,7 +411,7 @@ __device__ __forceinline__ bool box_contact(const Params& P, int b, int step, co
     for (int a = 0; a < D; ++a) {
         const float off = mo ? mo[a] : 0.0f;
         vb[a] = mo ? mo[D + a] : 0.0f;
-        const float x = (float)c[a] * P.dx, lo = B.lo[a] + off, hi = B.hi[a] + off;
+        const float x = (float)c[a] * dx, lo = B.lo[a] + off, hi = B.hi[a] + off;
         if (x < lo || x > hi) inside = false;
         if (x - lo < best) {
             best = x - lo;
@@ -446,7 +446,108 @@ __device__ __forceinline__ void coulomb_project(int a, float sgn, float mu, cons
     for (int i = 0; i < D; ++i) v[i] = vb[i] + (i == a ? 0.0f : vr[i] * f);
 }
 
+// The solid boxes of the grid operation and their reverse.  Not inlined:
+// every grid-operation call site would otherwise carry the box loops, which
+// multiplies compile time and costs the fused particle kernels registers
+// even without boxes; they are called only when boxes are set.
+//
+// apply_boxes: boxes act after the walls, in order; attached boxes set
+// v = v_b, the others act when the velocity relative to the box points into
+// it (Eq. 18 relative to the box).
 template <int D>
+__device__ __forceinline__ void apply_boxes(const Extras* ext, float dx, int n_steps, int step, const int* c,
+                                         float* v) {
+    float w[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) w[i] = v[i];
+    for (int b = 0; b < ext->n; ++b) {
+        float vb[D], sgn;
+        int axis;
+        if (!box_contact<D>(ext, dx, n_steps, b, step, c, vb, axis, sgn)) continue;
+        const int kind = ext->box[b].kind;
+        if (kind != kBoundaryAttached && !(sgn * (w[axis] - vb[axis]) < 0.0f)) continue;
+        if (kind == kBoundaryCoulomb) {
+            coulomb_project<D>(axis, sgn, ext->box[b].mu, vb, w);
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) w[i] = vb[i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = w[i];
+}
+
+// reverse_boxes: Vbar through the boxes, last first, given the velocity v
+// that entered the first box (the walls' output).  The velocity entering box
+// b is recomputed by replaying boxes 0..b-1 (at most 8 boxes, no per-box
+// arrays).  The box velocity is a constant, so the Coulomb Jacobian acts on
+// the relative velocity r = v - v_b: out_t = r_t (1 + mu vn / u), out_n = 0,
+// vn = sgn r_a, u = |r_t|.
+template <int D>
+__device__ __noinline__ void reverse_boxes(const Extras* ext, float dx, int n_steps, int step, const int* c,
+                                           const float* v, float* vbar) {
+    float vb[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) vb[i] = vbar[i];
+    const int nb = min(ext->n, kMaxBoundaries);
+    for (int b = nb - 1; b >= 0; --b) {
+        float ve[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) ve[i] = v[i];
+        for (int e = 0; e <= b; ++e) {
+            float vbx[D], sgn;
+            int axis;
+            if (!box_contact<D>(ext, dx, n_steps, e, step, c, vbx, axis, sgn)) continue;
+            const int kind = ext->box[e].kind;
+            if (kind != kBoundaryAttached && !(sgn * (ve[axis] - vbx[axis]) < 0.0f)) continue;
+            if (e < b) {  // replay an earlier box
+                if (kind == kBoundaryCoulomb) {
+                    coulomb_project<D>(axis, sgn, ext->box[e].mu, vbx, ve);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) ve[i] = vbx[i];
+                }
+                continue;
+            }
+            // box b fired on the entering velocity ve
+            if (kind != kBoundaryCoulomb) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) vb[i] = 0.0f;
+                continue;
+            }
+            const float mu = ext->box[e].mu;
+            float r[D], t2 = 0.0f, tdot = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) r[i] = ve[i] - vbx[i];
+            const float vn = sgn * r[axis];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+                if (i != axis) {
+                    t2 += r[i] * r[i];
+                    tdot += vb[i] * r[i];
+                }
+            const float u = sqrtf(t2);
+            if (u > 0.0f && u + mu * vn > 0.0f) {
+                const float ru = 1.0f / u;
+                const float f = 1.0f + mu * vn * ru;
+                const float g = mu * vn * tdot * ru * ru * ru;
+                const float out_n = sgn * mu * tdot * ru;
+#pragma unroll
+                for (int i = 0; i < D; ++i) vb[i] = (i == axis) ? out_n : vb[i] * f - g * r[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < D; ++i) vb[i] = 0.0f;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) vbar[i] = vb[i];
+}
+
+// BOXES: the caller may run with solid boxes (P.ext set).  Kernels launched
+// without them pass false and carry no box code, which the fused particle
+// kernels (one grid operation per stencil node) need for their registers.
+template <int D, bool BOXES = true>
 __device__ __forceinline__ void grid_velocity(const Params& P, const int (&c)[D], float m,
                                               const float (&mv)[D], float (&v)[D], int step) {
     if (!(m > 0.0f)) {
@@ -481,27 +582,13 @@ __device__ __forceinline__ void grid_velocity(const Params& P, const int (&c)[D]
             }
         }
     }
-    // solid boxes after the walls, in order: attached boxes set v = v_b; the
-    // others act when the velocity relative to the box points into it
-    const int nbox = P.ext ? P.ext->n : 0;
-    for (int b = 0; b < nbox; ++b) {
-        float vb[D], sgn;
-        int axis;
-        if (!box_contact<D>(P, b, step, c, vb, axis, sgn)) continue;
-        const int kind = P.ext->box[b].kind;
-        if (kind != kBoundaryAttached && !(sgn * (v[axis] - vb[axis]) < 0.0f)) continue;
-        if (kind == kBoundaryCoulomb) {
-            coulomb_project<D>(axis, sgn, P.ext->box[b].mu, vb, v);
-        } else {
-#pragma unroll
-            for (int i = 0; i < D; ++i) v[i] = vb[i];
-        }
-    }
+    // solid boxes after the walls (only when set)
+    if (BOXES && P.ext && P.ext->n > 0) apply_boxes<D>(P.ext, P.dx, P.n_steps, step, c, v);
 }
 
 // Reverse of grid_velocity: Vbar -> (mbar, mvbar).  The forward branches are
 // replayed from (m, mv); overwritten components pass no gradient.
-template <int D>
+template <int D, bool BOXES = true>
 __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int (&c)[D], float m,
                                                       const float (&mv)[D], const float (&Vbar)[D],
                                                       float& mbar, float (&mvbar)[D], int step) {
@@ -551,66 +638,11 @@ __device__ __forceinline__ void grid_velocity_adjoint(const Params& P, const int
             }
         }
     }
-    // Reverse of the solid boxes, last first.  The velocity entering box b is
-    // recomputed by replaying boxes 0..b-1 from the walls' output (at most 8
-    // boxes, so no per-box arrays; nothing runs without boxes).  The box
-    // velocity is a constant, so the Coulomb Jacobian acts on the relative
-    // velocity r = v - v_b: out_t = r_t (1 + mu vn / u), out_n = 0,
-    // vn = sgn r_a, u = |r_t|.
     float vb[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) vb[i] = Vbar[i];
-    const int nb = P.ext ? min(P.ext->n, kMaxBoundaries) : 0;
-    for (int b = nb - 1; b >= 0; --b) {
-        float ve[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) ve[i] = v[i];
-        for (int e = 0; e <= b; ++e) {
-            float vbx[D], sgn;
-            int axis;
-            if (!box_contact<D>(P, e, step, c, vbx, axis, sgn)) continue;
-            const int kind = P.ext->box[e].kind;
-            if (kind != kBoundaryAttached && !(sgn * (ve[axis] - vbx[axis]) < 0.0f)) continue;
-            if (e < b) {  // replay an earlier box
-                if (kind == kBoundaryCoulomb) {
-                    coulomb_project<D>(axis, sgn, P.ext->box[e].mu, vbx, ve);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < D; ++i) ve[i] = vbx[i];
-                }
-                continue;
-            }
-            // box b fired on the entering velocity ve
-            if (kind != kBoundaryCoulomb) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) vb[i] = 0.0f;
-                continue;
-            }
-            const float mu = P.ext->box[e].mu;
-            float r[D], t2 = 0.0f, tdot = 0.0f;
-#pragma unroll
-            for (int i = 0; i < D; ++i) r[i] = ve[i] - vbx[i];
-            const float vn = sgn * r[axis];
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-                if (i != axis) {
-                    t2 += r[i] * r[i];
-                    tdot += vb[i] * r[i];
-                }
-            const float u = sqrtf(t2);
-            if (u > 0.0f && u + mu * vn > 0.0f) {
-                const float ru = 1.0f / u;
-                const float f = 1.0f + mu * vn * ru;
-                const float g = mu * vn * tdot * ru * ru * ru;
-                const float out_n = sgn * mu * tdot * ru;
-#pragma unroll
-                for (int i = 0; i < D; ++i) vb[i] = (i == axis) ? out_n : vb[i] * f - g * r[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < D; ++i) vb[i] = 0.0f;
-            }
-        }
-    }
+    // reverse of the solid boxes (only when set), from the walls' output v
+    if (BOXES && P.ext && P.ext->n > 0) reverse_boxes<D>(P.ext, P.dx, P.n_steps, step, c, v, vb);
     if (nops > 0) {
 #pragma unroll
         for (int op = 2 * D - 1; op >= 0; --op) {

@@ -13,7 +13,7 @@
 // pointer) and caches it per device. Make that first call before any CUDA
 // stream capture begins.
 //
-// The substep itself reuses the library's kernels: P2G (kernels_step.cu,
+// The substep itself reuses the library's kernels: P2G (particle_kernels.cuh,
 // Eq. 14-15 with the stress of Eq. 7 / 31-33), the grid operation
 // (Eq. 16-18) and G2P (Eq. 19-22).
 #include <cuda_runtime.h>

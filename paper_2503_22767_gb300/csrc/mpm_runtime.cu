@@ -1,7 +1,7 @@
 // Runtime behind the C ABI of include/mpm.h.
 //
 // One handle owns every device buffer of a batch of simulations (allocated
-// once in mpm_create) and drives the kernels of kernels_step.cu and
+// once in mpm_create) and drives the kernels of particle_kernels.cuh, kernels_step.cu and
 // kernels_sort.cu:
 //
 //   forward   for each segment of K substeps: sort the particles by cell and
@@ -508,7 +508,9 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
 
 // The tiled kernels take the uniform field only; a field gradient uses the
 // direct kernels.
-bool use_tiles(const mpm_handle* h) { return h->tile && !h->ext_host.fgrad; }
+// The tiled kernels carry no solid boxes and no field gradient: with either
+// set, the direct kernels run.
+bool use_tiles(const mpm_handle* h) { return h->tile && h->P.ext == nullptr; }
 
 StepArgs base_args(mpm_handle* h) {
     StepArgs a;

@@ -97,14 +97,14 @@ __device__ __forceinline__ void clear_buffer(const StepArgs& a) {
 
 // Grid velocity at a stencil node: read V (separate grid kernel) or apply
 // the grid operation (Eq. 16-18) to the node's accumulator (fused).
-template <int D, bool FUSE>
+template <int D, bool FUSE, bool BOXES = true>
 __device__ __forceinline__ void node_velocity(const float4* __restrict__ grid, const NodeTerm<D>& t,
                                               const Params& P, float (&gv)[D], int step) {
     const float4 g = __ldg(grid + t.node);
     if (FUSE) {
         float mv[D];
         unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-        grid_velocity<D>(P, t.c, g.x, mv, gv, step);
+        grid_velocity<D, BOXES>(P, t.c, g.x, mv, gv, step);
     } else {
         unpack3<D>(g, gv);
     }

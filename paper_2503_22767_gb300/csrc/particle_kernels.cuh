@@ -1,0 +1,668 @@
+// Particle kernels of the magneto-elastic MLS-MPM substep and its reverse.
+//
+// Forward (arxiv 2503.22767, Section 2.2): the particle kernel fuses the G2P
+// of substep n (Eq. 19-22) with the P2G of substep n+1 (Eq. 14-15 with the
+// SIMP-scaled stress of Eq. 7/31-33), so between substeps a particle's state
+// is read once and written once.  Reverse (Section 2.3): the particle kernel
+// fuses the P2G^T of substep n with the G2P^T of substep n-1.
+//
+// Particle arrays are structure-of-arrays with component stride P.np:
+// x[D], v[D], C[D][D], E[D][D] (row-major), i.e. 2D + 2D^2 components, where
+// E = F - I is the strain form of the deformation gradient (see
+// mpm_device.cuh: it keeps small strains exact to float32 precision).
+// Grids are float4 per node ([inst][node]): accumulators (m, mv), velocities
+// (v, 0), adjoints (mbar, mvbar).
+//
+// The kernels are templates over the dimension and the fused stages; each
+// dimension and direction is instantiated in a translation unit of its own
+// (kernels_particle2.cu, kernels_forward3.cu, kernels_adjoint3.cu), so they
+// compile in parallel.
+#pragma once
+
+#include "kernels.h"
+#include "particle_io.cuh"
+#include "warp_box.cuh"
+
+namespace mpm {
+
+// Resident 256-thread blocks per SM that the register allocation must allow
+// (the compiler caps registers at 65536 / (256 x this)).  The transfer kernels
+// are latency-bound, so occupancy is traded against spills: the 3D forward
+// kernel is held to 64 registers, and the adjoint kernel is compiled for 2
+// (<= 128 registers) and 3 (<= 80) blocks, chosen per launch (Params::adj_blocks).
+constexpr int kMinBlocksForward3 = 4;
+
+namespace {
+
+inline int particle_blocks(long long n, int block) { return (int)((n + block - 1) / block); }
+
+// 3D: at most 64 registers (32 warps per SM) to keep more gathers in flight
+// EXT: P.ext is set (solid boxes or a non-uniform field); without it the
+// kernel carries no code for the field gradient.
+template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT>
+__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forward(Params P, StepArgs a) {
+    using L = Layout<D>;
+    // Early loads: with the grid operation in its own kernel, this kernel's
+    // predecessor is that grid kernel, which writes none of the particle
+    // arrays read first here.  Every kernel of the chain waits before it
+    // triggers its dependents, so when this kernel starts, the particle
+    // kernel before the grid kernel has completed, and the state loads can
+    // overlap the grid kernel's tail.
+    constexpr bool kEarly = G2P && !FUSE;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = p < P.n_total;
+    const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
+    const long long np = P.np;
+    int flags = 0;
+    float x[D], v[D], C[D][D], F[D][D];
+    float phi = 0.0f, mp = 0.0f;
+    auto load_state = [&]() {
+        load_vec<D>(a.s_in, L::X, np, p, x);
+        load_mat<D>(a.s_in, L::F, np, p, F);
+        phi = a.phi[p];
+        mp = phi * P.rho0 * P.p_vol;  // Eq. 33
+        if (!G2P) {
+            load_vec<D>(a.s_in, L::V, np, p, v);
+            load_mat<D>(a.s_in, L::C, np, p, C);
+        }
+    };
+    if (kEarly && active) load_state();
+    pdl_wait();
+    pdl_trigger();
+    if (FUSE) clear_buffer(a);
+    if (!kEarly && active) load_state();
+    if (G2P) {
+        float mom_x[1] = {0.0f};
+        Stencil<D> s;
+#pragma unroll
+        for (int i = 0; i < D; ++i) s.base[i] = 0;
+        if (active && !make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        const float4* __restrict__ Vg = FUSE ? a.accG : a.V;
+        __shared__ float4 s_box[kBoxWarps * box_nodes<D>()];
+        float4* sm = s_box + (threadIdx.x >> 5) * box_nodes<D>();
+        const WarpBox<D> box = warp_box<D>(s.base, active, inst, P.box != 0);
+        if (box.use) {
+            const float4* __restrict__ Vb = Vg + (long long)box.inst * P.nodes;
+            stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
+                const float4 g = __ldg(Vb + node);
+                if (!FUSE) return g;
+                float mv[D], gv[D];
+                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                grid_velocity<D, EXT>(P, c, g.x, mv, gv, a.n_g2p);  // Eq. 16-18 once per node
+                return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
+            });
+        }
+        if (active) {
+            const float4* __restrict__ Vi = Vg + (long long)inst * P.nodes;
+            // Eq. 19-20 with x_i - x_p = (o - r) dx for stencil offset o:
+            //   v = sum w V,  C = (4/dx) (sum w V o^T - v r^T)
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                v[i] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) C[i][j] = 0.0f;  // sum w V o^T
+            }
+#pragma unroll
+            for (int k = 0; k < stencil_size<D>(); ++k) {
+                NodeTerm<D> t;
+                node_term<D>(s, k, P, t);
+                float gv[D];
+                if (box.use) {
+                    unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
+                } else {
+                    node_velocity<D, FUSE, EXT>(Vi, t, P, gv, a.n_g2p);
+                }
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float wv = t.w * gv[i];
+                    v[i] += wv;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const int o = stencil_offset<D>(k, j);
+                        if (o == 1) C[i][j] += wv;
+                        else if (o == 2) C[i][j] += 2.0f * wv;
+                    }
+                }
+            }
+            float Fn[D][D];
+            const float c4 = 4.0f * P.inv_dx;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) C[i][j] = c4 * (C[i][j] - v[i] * s.r[j]);
+                x[i] += P.dt * v[i];                              // Eq. 21
+            }
+            // Eq. 22 in strain form: E' = E + dt C (I + E)
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float acc = C[i][j];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc += C[i][k] * F[k][j];
+                    Fn[i][j] = F[i][j] + P.dt * acc;
+                }
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) F[i][j] = Fn[i][j];
+            float Jm1 = det_minus_one<D>(F);
+            if (!(Jm1 > -1.0f) || !isfinite(Jm1)) flags |= kErrNumeric;
+            store_vec<D>(a.s_out, L::X, np, p, x);
+            store_mat<D>(a.s_out, L::F, np, p, F);
+            if (WRITE_ALL) {
+                store_vec<D>(a.s_out, L::V, np, p, v);
+                store_mat<D>(a.s_out, L::C, np, p, C);
+            }
+            mom_x[0] = mp * v[0];
+        }
+        if (P.loss_kind == 1 && a.mom != nullptr)
+            warp_add_per_instance<1>(mom_x, inst, a.mom + (long long)a.n_g2p * P.n_inst, 1);
+    }
+    if (P2G && active) {
+        Stencil<D> s;
+        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        StressParts<D> S;
+        stress_parts<D>(F, phi, P, S);
+        if (!(S.J > 0.0f)) flags |= kErrNumeric;
+        float Br[D], Ba[D], Pk[D][D], A[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            Br[i] = a.mag[(long long)i * np + p];
+            Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
+        }
+        if (EXT && P.ext->fgrad) {
+            const float* Gn = P.ext->fgrad + ((long long)inst * P.n_steps + a.n_p2g) * D * D;
+            field_at_particle<D>(Gn, x, Ba);
+            // body force of the non-uniform field, folded into the momentum
+            // m v (f and m both vanish with phi, so m > 0 whenever f != 0)
+            float f[D];
+            magnetic_force<D>(Gn, F, Br, S.s, P, f);
+            if (mp > 0.0f) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) v[i] += P.dt * f[i] / mp;
+            }
+        }
+        piola<D>(S, Br, Ba, Pk);
+        const float sc = P.dt * P.kappa * P.p_vol;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
+#pragma unroll
+                for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
+                // MLS-MPM affine momentum (Eq. 15 with the time step and the
+                // x_i - x_p offset of the MLS-MPM form): m C - dt (4/dx^2) V P F^T
+                A[i][j] = mp * C[i][j] - sc * pft;
+            }
+        float4* __restrict__ ai = a.acc + (long long)inst * P.nodes;
+        // Eq. 15 with x_i - x_p = (o - r) dx: node momentum w (u + dx A o),
+        // u = m v - dx A r
+        float u[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float ar = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                A[i][j] *= P.dx;
+                ar += A[i][j] * s.r[j];
+            }
+            u[i] = mp * v[i] - ar;
+        }
+#pragma unroll
+        for (int k = 0; k < stencil_size<D>(); ++k) {
+            NodeTerm<D> t;
+            node_term<D>(s, k, P, t);
+            float mv[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float m = u[i];
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const int o = stencil_offset<D>(k, j);
+                    if (o == 1) m += A[i][j];
+                    else if (o == 2) m += 2.0f * A[i][j];
+                }
+                mv[i] = t.w * m;
+            }
+            atomicAdd(ai + t.node, pack4<D>(t.w * mp, mv));  // Eq. 14 in .x
+        }
+    }
+    if (flags) atomicOr(a.err, flags);
+}
+
+
+// ---------------------------------------------------------------------------
+// adjoint particle kernel
+//   P2GT: reverse of P2G at substep n = a.n_p2g; completes the particle
+//         adjoint of state n (x, v, C, F), accumulates design gradients.
+//   G2PT: reverse of G2P at substep m (= n-1 when fused, else n): consumes
+//         the adjoint of state m+1, scatters Vbar, writes the partial
+//         adjoint (x, F) of state m.
+// ---------------------------------------------------------------------------
+// FUSE: P2G^T evaluates the grid adjoint per stencil node from (accP, VbarIn);
+// FUSE_V: G2P^T takes the grid velocity from accG through the grid operation.
+// EXT: P.ext is set (solid boxes or a non-uniform field), as in k_forward.
+template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, int MINB, bool EXT>
+__global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
+    using L = Layout<D>;
+    // Early loads as in k_forward: the fused kernel without grid-adjoint
+    // fusion follows the grid adjoint kernel, which writes none of the
+    // particle arrays of state n, the partial adjoint or the design.
+    constexpr bool kEarly = P2GT && G2PT && !FUSE;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = p < P.n_total;
+    const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
+    const long long np = P.np;
+    int flags = 0;
+    // adjoint of the state between the two halves (state n if P2GT)
+    float xb[D], vb[D], Cb[D][D], Fb[D][D];
+    float Cn[D][D];  // C of state n (= m+1), needed by G2P^T
+    float x_n[D], v_n[D], F_n[D][D], phi_n = 0.0f;  // state n and design (P2G^T)
+    auto load_state_n = [&]() {
+        load_vec<D>(a.s_in, L::X, np, p, x_n);
+        load_vec<D>(a.s_in, L::V, np, p, v_n);
+        load_mat<D>(a.s_in, L::C, np, p, Cn);
+        load_mat<D>(a.s_in, L::F, np, p, F_n);
+        load_vec<D>(a.adj, L::X, np, p, xb);
+        load_mat<D>(a.adj, L::F, np, p, Fb);
+        phi_n = a.phi[p];
+    };
+    if (kEarly && active) load_state_n();
+    pdl_wait();
+    pdl_trigger();
+    clear_buffer(a);
+    if (P2GT && !kEarly && active) load_state_n();
+    // warps with every lane active may stage their stencil nodes (the staging
+    // runs inside the per-particle branches)
+    const bool full_warp = __ballot_sync(0xffffffffu, active) == 0xffffffffu;
+    __shared__ float4 s_box[kBoxWarps * box_nodes<D>()];
+    float4* sm = s_box + (threadIdx.x >> 5) * box_nodes<D>();
+    float bab[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) bab[i] = 0.0f;
+    // non-uniform field: G of this substep (uniform over the launch), and the
+    // particle's contribution to dL/dG
+    const bool has_fgrad = EXT && P2GT && P.ext->fgrad;
+    float gG[D * D];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) gG[i] = 0.0f;
+    if (P2GT) {
+        if (active) {
+            const int n = a.n_p2g;
+            const float* Gn = has_fgrad ? P.ext->fgrad + ((long long)inst * P.n_steps + n) * D * D : nullptr;
+            float(&x)[D] = x_n;
+            float(&v)[D] = v_n;
+            float(&F)[D][D] = F_n;
+            const float phi = phi_n;
+            const float mp = phi * P.rho0 * P.p_vol;
+            float Br[D], Ba[D], Pk[D][D], A[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                Br[i] = a.mag[(long long)i * np + p];
+                Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + n) * D + i);
+            }
+            if (Gn) field_at_particle<D>(Gn, x, Ba);
+            Stencil<D> s;
+            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+            StressParts<D> S;
+            stress_parts<D>(F, phi, P, S);
+            piola<D>(S, Br, Ba, Pk);
+            const float sc = P.dt * P.kappa * P.p_vol;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
+#pragma unroll
+                    for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
+                    A[i][j] = mp * Cn[i][j] - sc * pft;
+                }
+            // Node sums factored with x_i - x_p = (o - r) dx (o the stencil offset):
+            //   S0 = sum w mvb,  T = sum w mvb o^T,  mbs = sum w mb
+            // give vbar = mp S0, Abar = dx (T - S0 r^T) and
+            // mbar_p = mbs + S0 . v + C : Abar.  Per node there remain A^T mvb
+            // (for the x adjoint) and the value of the node's contribution,
+            //   inner = mb mp + mvb . (mp v + A dpos) = mb mp + mvb . u + dx (A^T mvb) . o,
+            // with u = mp v - dx A r.
+            float S0[D], T[D][D], u[D], mbs = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                S0[i] = 0.0f;
+                float ar = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    T[i][j] = 0.0f;
+                    ar += A[i][j] * s.r[j];
+                }
+                u[i] = mp * v[i] - P.dx * ar;
+            }
+            if (Gn) {  // the body force is part of the particle's momentum term
+                float f[D];
+                magnetic_force<D>(Gn, F, Br, S.s, P, f);
+#pragma unroll
+                for (int i = 0; i < D; ++i) u[i] += P.dt * f[i];
+            }
+            const float4* __restrict__ gi = (FUSE ? a.accP : a.gadj) + (long long)inst * P.nodes;
+            const float4* __restrict__ vbi = FUSE ? a.VbarIn + (long long)inst * P.nodes : nullptr;
+            const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
+            if (box.use)
+                stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
+                    const float4 g = __ldg(gi + node);
+                    if (!FUSE) return g;
+                    // grid adjoint (reverse of Eq. 16-18) once per node
+                    float mv[D], vbv[D], mbv, mvb[D];
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                    unpack3<D>(__ldg(vbi + node), vbv);
+                    grid_velocity_adjoint<D, EXT>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
+                    return make_float4(mbv, mvb[0], mvb[1], D == 3 ? mvb[D - 1] : 0.0f);
+                });
+#pragma unroll
+            for (int k = 0; k < stencil_size<D>(); ++k) {
+                NodeTerm<D> t;
+                node_term<D>(s, k, P, t);
+                float4 g;
+                float mvb[D];
+                if (box.use) {
+                    g = sm[box_slot<D>(box, t.c)];
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
+                } else if (FUSE) {
+                    g = __ldg(gi + t.node);
+                    // grid adjoint (reverse of Eq. 16-18) of this node, on the fly
+                    float mv[D], vbv[D], mbv;
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                    unpack3<D>(__ldg(vbi + t.node), vbv);
+                    grid_velocity_adjoint<D, EXT>(P, t.c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
+                    g.x = mbv;
+                } else {
+                    g = __ldg(gi + t.node);
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
+                }
+                float atm[D], ao = 0.0f, inner = g.x * mp;
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    atm[c] = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) atm[c] += A[i][c] * mvb[i];
+                    const int o = stencil_offset<D>(k, c);
+                    if (o == 1) ao += atm[c];
+                    else if (o == 2) ao += 2.0f * atm[c];
+                    inner += mvb[c] * u[c];
+                }
+                inner += P.dx * ao;
+                mbs += t.w * g.x;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float wm = t.w * mvb[i];
+                    S0[i] += wm;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const int o = stencil_offset<D>(k, j);
+                        if (o == 1) T[i][j] += wm;
+                        else if (o == 2) T[i][j] += 2.0f * wm;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < D; ++c) xb[c] += t.gw[c] * inner - t.w * atm[c];
+            }
+            float Ab[D][D], mpb = mbs;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                vb[i] = mp * S0[i];
+                mpb += S0[i] * v[i];
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    Ab[i][j] = P.dx * (T[i][j] - S0[i] * s.r[j]);
+                    mpb += Cn[i][j] * Ab[i][j];
+                }
+            }
+            // A = mp C - sc P F^T
+            float Pb[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) Cb[i][j] = mp * Ab[i][j];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float pb = Ab[i][j], fb = 0.0f;  // (Abar F)_ij with F = I + E
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        pb += Ab[i][k] * F[k][j];
+                        fb += Ab[k][i] * Pk[k][j];   // (Abar^T P)_ij
+                    }
+                    Pb[i][j] = -sc * pb;
+                    Fb[i][j] -= sc * fb;
+                }
+            float phib = 0.0f, brb[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) brb[i] = 0.0f;
+            piola_adjoint<D>(F, phi, S, Br, Ba, Pb, P, Fb, phib, brb, bab);
+            float gph = phib + mpb * P.rho0 * P.p_vol;
+            if (Gn) {
+                // B at the particle = B_a + G (x - x_c): dL/dB_a stays in bab,
+                // dL/dG += bab (x - x_c)^T, xbar += G^T bab
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        gG[i * D + j] += bab[i] * (x[j] - 0.5f);
+                        xb[j] += __ldg(Gn + i * D + j) * bab[i];
+                    }
+                // body force f = c G^T (F B~_r), c = s V / mu0, whose adjoint is
+                // fbar = dt sum_i w mvb_i = dt S0
+                const float c = S.s * P.p_vol * (1.0f / kMu0);
+                float FB[D], Gfb[D], fraw = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    FB[i] = Br[i];
+                    Gfb[i] = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        FB[i] += F[i][k] * Br[k];
+                        Gfb[i] += __ldg(Gn + i * D + k) * (P.dt * S0[k]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    fraw += Gfb[i] * FB[i];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        Fb[i][k] += c * Gfb[i] * Br[k];
+                        brb[k] += c * Gfb[i] * ((i == k ? 1.0f : 0.0f) + F[i][k]);
+                        gG[i * D + k] += c * FB[i] * (P.dt * S0[k]);
+                    }
+                }
+                const float ds = P.simp_q > 0 ? (float)P.simp_q * int_pow(phi, P.simp_q - 1) : 0.0f;
+                gph += ds * P.p_vol * (1.0f / kMu0) * fraw;
+            }
+            // locomotion seed on state n (n >= 1), Eq. 40
+            if (P.loss_kind == 1 && n >= 1) {
+                const float M = a.Minst[inst];
+                if (M > 0.0f) {
+                    const float dl = a.dloss[inst];
+                    const float rM = 1.0f / M;
+                    const float vbar = a.mom[(long long)(n - 1) * P.n_inst + inst] * rM;
+                    vb[0] -= P.dt * mp * rM * dl;
+                    gph -= P.dt * (v[0] - vbar) * rM * dl * P.rho0 * P.p_vol;
+                }
+            }
+            a.gphi[p] += gph;
+#pragma unroll
+            for (int i = 0; i < D; ++i) a.gmag[(long long)i * np + p] += brb[i];
+        }
+        warp_add_per_instance<D>(bab, inst, a.gfield + (long long)a.n_p2g * D,
+                                 (long long)P.n_steps * D);
+        if (has_fgrad)  // uniform over the launch: every lane takes part
+            warp_add_per_instance<D * D>(gG, inst, P.ext->gfgrad + (long long)a.n_p2g * D * D,
+                                         (long long)P.n_steps * D * D);
+        if (!G2PT && active) {
+            store_vec<D>(a.adj, L::X, np, p, xb);
+            store_vec<D>(a.adj, L::V, np, p, vb);
+            store_mat<D>(a.adj, L::C, np, p, Cb);
+            store_mat<D>(a.adj, L::F, np, p, Fb);
+        }
+    }
+    if (G2PT && active) {
+        if (!P2GT) {
+            // adjoint of state m+1 and C_{m+1} from memory
+            load_vec<D>(a.adj, L::X, np, p, xb);
+            load_vec<D>(a.adj, L::V, np, p, vb);
+            load_mat<D>(a.adj, L::C, np, p, Cb);
+            load_mat<D>(a.adj, L::F, np, p, Fb);
+            load_mat<D>(a.s_in, L::C, np, p, Cn);
+        }
+        float x[D], F[D][D];
+        load_vec<D>(a.s_aux, L::X, np, p, x);
+        load_mat<D>(a.s_aux, L::F, np, p, F);
+        Stencil<D> s;
+        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+        // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
+        float vt[D], Ct[D][D], Fo[D][D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) vt[i] = vb[i] + P.dt * xb[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                float fft = Fb[i][j], ctf = Fb[i][j];  // F = I + E
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    fft += Fb[i][k] * F[j][k];          // (Fbar F^T)_ij
+                    ctf += P.dt * Cn[k][i] * Fb[k][j];  // ((I + dt C')^T Fbar)_ij
+                }
+                Ct[i][j] = Cb[i][j] + P.dt * fft;
+                Fo[i][j] = ctf;
+            }
+        const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
+        float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
+        const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
+        if (box.use)
+            stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
+                const float4 g = __ldg(Vi + node);
+                if (!FUSE_V) return g;
+                float mv[D], gv[D];
+                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                grid_velocity<D, EXT>(P, c, g.x, mv, gv, a.n_p2g - 1);  // Eq. 16-18 once per node
+                return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
+            });
+        // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T), factored
+        // with dpos = (o - r) dx: the node's velocity adjoint is
+        //   w (vt + kappa Ct dpos) = w (q + kappa dx Ct o),  q = vt - kappa dx Ct r
+        float q[D];
+        const float kdx = P.kappa * P.dx;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float cr = 0.0f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) cr += Ct[i][j] * s.r[j];
+            q[i] = vt[i] - kdx * cr;
+        }
+#pragma unroll
+        for (int k = 0; k < stencil_size<D>(); ++k) {
+            NodeTerm<D> t;
+            node_term<D>(s, k, P, t);
+            float gv[D];
+            if (box.use) unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
+            else node_velocity<D, FUSE_V, EXT>(Vi, t, P, gv, a.n_p2g - 1);
+            float sv[D], dot = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float co = 0.0f;  // (Ct o)_i
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const int o = stencil_offset<D>(k, j);
+                    if (o == 1) co += Ct[i][j];
+                    else if (o == 2) co += 2.0f * Ct[i][j];
+                }
+                sv[i] = q[i] + kdx * co;
+                dot += gv[i] * sv[i];  // gv . (vt + kappa Ct dpos)
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                float ctv = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) ctv += Ct[i][c] * gv[i];
+                xb[c] += t.gw[c] * dot - P.kappa * t.w * ctv;
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) sv[i] *= t.w;
+            float4 c4 = make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f);
+            atomicAdd(Vbi + t.node, c4);
+        }
+        store_vec<D>(a.adj, L::X, np, p, xb);
+        store_mat<D>(a.adj, L::F, np, p, Fo);
+    }
+    if (flags) atomicOr(a.err, flags);
+}
+
+
+}  // namespace
+
+template <int D, bool FUSE>
+static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, const StepArgs& a,
+                             int block, cudaStream_t st) {
+    // a fused launch also clears a.zero4, so it runs even without particles
+    if (P.n_total == 0 && !(FUSE && a.zero4)) return cudaSuccess;
+    long long threads = P.n_total > 0 ? P.n_total : block;
+    dim3 grid(particle_blocks(threads, block));
+    const bool ext = P.ext != nullptr;
+    if (g2p && p2g) {
+        if (ext) {
+            if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE, true>, grid, block, st, P, a);
+            return launch_chain(P, k_forward<D, true, true, false, FUSE, true>, grid, block, st, P, a);
+        }
+        if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE, false>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, true, true, false, FUSE, false>, grid, block, st, P, a);
+    } else if (g2p) {
+        if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE, false>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, true, false, false, FUSE, false>, grid, block, st, P, a);
+    } else {
+        if (ext) return launch_chain(P, k_forward<D, false, true, false, FUSE, true>, grid, block, st, P, a);
+        return launch_chain(P, k_forward<D, false, true, false, FUSE, false>, grid, block, st, P, a);
+    }
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_forward_dim(bool g2p, bool p2g, bool write_all, bool fuse, const Params& P,
+                               const StepArgs& a, int block, cudaStream_t st) {
+    return fuse ? forward_d<D, true>(g2p, p2g, write_all, P, a, block, st)
+                : forward_d<D, false>(g2p, p2g, write_all, P, a, block, st);
+}
+
+template <int D, bool FUSE, bool FUSE_V>
+static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepArgs& a, int block,
+                             cudaStream_t st) {
+    if (P.n_total == 0 && !a.zero4) return cudaSuccess;
+    long long threads = P.n_total > 0 ? P.n_total : block;
+    dim3 grid(particle_blocks(threads, block));
+    // with solid boxes or a field gradient only the 128-register budget is built
+    const bool ext = P.ext != nullptr;
+    if (p2gt && g2pt) {
+        if (ext) return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 2, true>, grid, block, st, P, a);
+        if (P.adj_blocks == 3)
+            return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 3, false>, grid, block, st, P, a);
+        return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 2, false>, grid, block, st, P, a);
+    }
+    // the segment-edge halves run once per checkpoint segment
+    if (p2gt) {
+        if (ext) return launch_chain(P, k_adjoint<D, true, false, FUSE, FUSE_V, 2, true>, grid, block, st, P, a);
+        return launch_chain(P, k_adjoint<D, true, false, FUSE, FUSE_V, 2, false>, grid, block, st, P, a);
+    }
+    if (ext) return launch_chain(P, k_adjoint<D, false, true, FUSE, FUSE_V, 2, true>, grid, block, st, P, a);
+    return launch_chain(P, k_adjoint<D, false, true, FUSE, FUSE_V, 2, false>, grid, block, st, P, a);
+}
+
+template <int D>
+cudaError_t launch_adjoint_dim(bool p2gt, bool g2pt, bool fuse, bool fuse_v, const Params& P,
+                               const StepArgs& a, int block, cudaStream_t st) {
+    if (fuse) return adjoint_d<D, true, true>(p2gt, g2pt, P, a, block, st);
+    if (fuse_v) return adjoint_d<D, false, true>(p2gt, g2pt, P, a, block, st);
+    return adjoint_d<D, false, false>(p2gt, g2pt, P, a, block, st);
+}
+
+
+}  // namespace mpm

@@ -124,7 +124,8 @@ def test_boundaries_match_oracle(key):
 @pytest.mark.parametrize("key", ["clamp2d", "box3d"])
 def test_boundaries_in_every_execution_mode(key, fuse, tile, box):
     """The grid operation (and its reverse) runs in the grid kernels, inside
-    the particle kernels (grid fusion), in warp-staged boxes and in tiles."""
+    the particle kernels (grid fusion) and in warp-staged boxes; with tiles
+    requested the runtime runs the direct kernels."""
     w, o, ob = _oracle(key)
     _check(run_gpu(w, {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_TILE: tile, B.MPM_OPT_WARP_BOX: box}), o, ob, w)
 
