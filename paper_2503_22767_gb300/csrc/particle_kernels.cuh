@@ -617,6 +617,11 @@ static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, cons
         if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE, false>, grid, block, st, P, a);
         return launch_chain(P, k_forward<D, true, true, false, FUSE, false>, grid, block, st, P, a);
     } else if (g2p) {
+        // with grid fusion the G2P applies the grid operation, boxes included
+        if (ext && FUSE) {
+            if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE, true>, grid, block, st, P, a);
+            return launch_chain(P, k_forward<D, true, false, false, FUSE, true>, grid, block, st, P, a);
+        }
         if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE, false>, grid, block, st, P, a);
         return launch_chain(P, k_forward<D, true, false, false, FUSE, false>, grid, block, st, P, a);
     } else {
