@@ -165,6 +165,28 @@ __device__ __forceinline__ constexpr int stencil_offset(int k, int b) {
     return D == 2 ? (b == 0 ? k / 3 : k % 3) : (b == 0 ? k / 9 : (b == 1 ? (k / 3) % 3 : k % 3));
 }
 
+// a + o d for a stencil offset o in {0, 1, 2}: with o a compile-time
+// constant (unrolled stencil loops) this is no instruction, one add or one FMA.
+__device__ __forceinline__ float add_offset(float a, int o, float d) {
+    return o == 0 ? a : (o == 1 ? a + d : fmaf(2.0f, d, a));
+}
+
+// Index of the stencil's base node within the instance grid, and the offset
+// of stencil node k from it (last axis fastest).
+template <int D>
+__device__ __forceinline__ int base_node(const Stencil<D>& s, int res) {
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) idx = idx * res + s.base[a];
+    return idx;
+}
+
+template <int D>
+__device__ __forceinline__ int node_offset(int k, int res) {
+    return D == 2 ? stencil_offset<D>(k, 0) * res + stencil_offset<D>(k, 1)
+                  : (stencil_offset<D>(k, 0) * res + stencil_offset<D>(k, 1)) * res + stencil_offset<D>(k, 2);
+}
+
 // ---------------------------------------------------------------------------
 // small dense algebra
 // ---------------------------------------------------------------------------

@@ -102,19 +102,29 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
 #pragma unroll
                 for (int j = 0; j < D; ++j) C[i][j] = 0.0f;  // sum w V o^T
             }
+            const int nb = base_node<D>(s, P.res);
+            const int sb = box.use ? box_slot<D>(box, s.base) : 0;
+            float pw = 0.0f;  // product of the weights of all but the last axis
 #pragma unroll
             for (int k = 0; k < stencil_size<D>(); ++k) {
-                NodeTerm<D> t;
-                node_term<D>(s, k, P, t);
+                const int ol = stencil_offset<D>(k, D - 1);
+                if (ol == 0)
+                    pw = D == 2 ? s.w[0][stencil_offset<D>(k, 0)]
+                                : s.w[0][stencil_offset<D>(k, 0)] * s.w[1 % D][stencil_offset<D>(k, 1 % D)];
+                const float w = pw * s.w[D - 1][ol];
                 float gv[D];
                 if (box.use) {
-                    unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
+                    unpack3<D>(sm[sb + box_offset<D>(k)], gv);
                 } else {
+                    NodeTerm<D> t;
+                    t.node = nb + node_offset<D>(k, P.res);
+#pragma unroll
+                    for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
                     node_velocity<D, FUSE, EXT>(Vi, t, P, gv, a.n_g2p);
                 }
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    const float wv = t.w * gv[i];
+                    const float wv = w * gv[i];
                     v[i] += wv;
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
@@ -210,23 +220,24 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
             }
             u[i] = mp * v[i] - ar;
         }
+        const int nb = base_node<D>(s, P.res);
+        float pw = 0.0f;  // product of the weights of all but the last axis
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
-            NodeTerm<D> t;
-            node_term<D>(s, k, P, t);
+            const int ol = stencil_offset<D>(k, D - 1);
+            if (ol == 0)
+                pw = D == 2 ? s.w[0][stencil_offset<D>(k, 0)]
+                            : s.w[0][stencil_offset<D>(k, 0)] * s.w[1 % D][stencil_offset<D>(k, 1 % D)];
+            const float w = pw * s.w[D - 1][ol];
             float mv[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 float m = u[i];
 #pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    const int o = stencil_offset<D>(k, j);
-                    if (o == 1) m += A[i][j];
-                    else if (o == 2) m += 2.0f * A[i][j];
-                }
-                mv[i] = t.w * m;
+                for (int j = 0; j < D; ++j) m = add_offset(m, stencil_offset<D>(k, j), A[i][j]);
+                mv[i] = w * m;
             }
-            atomicAdd(ai + t.node, pack4<D>(t.w * mp, mv));  // Eq. 14 in .x
+            atomicAdd(ai + nb + node_offset<D>(k, P.res), pack4<D>(w * mp, mv));  // Eq. 14 in .x
         }
     }
     if (flags) atomicOr(a.err, flags);
@@ -319,22 +330,24 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
                     A[i][j] = mp * Cn[i][j] - sc * pft;
                 }
-            // Node sums factored with x_i - x_p = (o - r) dx (o the stencil offset):
+            // Node sums with x_i - x_p = (o - r) dx (o the stencil offset):
             //   S0 = sum w mvb,  T = sum w mvb o^T,  mbs = sum w mb
             // give vbar = mp S0, Abar = dx (T - S0 r^T) and
-            // mbar_p = mbs + S0 . v + C : Abar.  Per node there remain A^T mvb
-            // (for the x adjoint) and the value of the node's contribution,
-            //   inner = mb mp + mvb . (mp v + A dpos) = mb mp + mvb . u + dx (A^T mvb) . o,
-            // with u = mp v - dx A r.
-            float S0[D], T[D][D], u[D], mbs = 0.0f;
+            // mbar_p = mbs + S0 . v + C : Abar.  The node's contribution to
+            // the particle's momentum is
+            //   inner = mb mp + mvb . (mp v + A dpos) = mb mp + mvb . (u + dx A o),
+            // u = mp v - dx A r, and xbar += sum (grad w) inner - A^T S0.
+            // Every stencil sum runs axis by axis: over the last axis with its
+            // 1D weights, then the partial sums are weighted by the other
+            // axes' weights, so no node forms a product of weights.
+            float u[D], dA[D][D];  // dA[c][i] = dx A_ic
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                S0[i] = 0.0f;
                 float ar = 0.0f;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    T[i][j] = 0.0f;
                     ar += A[i][j] * s.r[j];
+                    dA[j][i] = P.dx * A[i][j];
                 }
                 u[i] = mp * v[i] - P.dx * ar;
             }
@@ -358,53 +371,107 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     grid_velocity_adjoint<D, EXT>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
                     return make_float4(mbv, mvb[0], mvb[1], D == 3 ? mvb[D - 1] : 0.0f);
                 });
+            const int nb = base_node<D>(s, P.res);
+            const int sb = box.use ? box_slot<D>(box, s.base) : 0;
+            float S0[D], T[D][D], mbs = 0.0f, xg[D];
+            // partial sums over the last axis (h*) and, in 3D, the middle axis (l*)
+            float Ug[D], hv[D], hv2[D], hm = 0.0f, ha = 0.0f, hb = 0.0f, la = 0.0f, lb = 0.0f, lc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                S0[i] = xg[i] = Ug[i] = hv[i] = hv2[i] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) T[i][j] = 0.0f;
+            }
 #pragma unroll
             for (int k = 0; k < stencil_size<D>(); ++k) {
-                NodeTerm<D> t;
-                node_term<D>(s, k, P, t);
+                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                const int ol = stencil_offset<D>(k, D - 1);
+                if (ol == 0) {  // a new row along the last axis
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        float ug = add_offset(u[i], o0, dA[0][i]);
+                        if (D == 3) ug = add_offset(ug, om, dA[1 % D][i]);
+                        Ug[i] = ug;
+                        hv[i] = hv2[i] = 0.0f;
+                    }
+                    hm = ha = hb = 0.0f;
+                }
                 float4 g;
                 float mvb[D];
                 if (box.use) {
-                    g = sm[box_slot<D>(box, t.c)];
+                    g = sm[sb + box_offset<D>(k)];
                     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
                 } else if (FUSE) {
-                    g = __ldg(gi + t.node);
+                    const int node = nb + node_offset<D>(k, P.res);
+                    g = __ldg(gi + node);
                     // grid adjoint (reverse of Eq. 16-18) of this node, on the fly
+                    int c[D];
+#pragma unroll
+                    for (int e = 0; e < D; ++e) c[e] = s.base[e] + stencil_offset<D>(k, e);
                     float mv[D], vbv[D], mbv;
                     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                    unpack3<D>(__ldg(vbi + t.node), vbv);
-                    grid_velocity_adjoint<D, EXT>(P, t.c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
+                    unpack3<D>(__ldg(vbi + node), vbv);
+                    grid_velocity_adjoint<D, EXT>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
                     g.x = mbv;
                 } else {
-                    g = __ldg(gi + t.node);
+                    g = __ldg(gi + nb + node_offset<D>(k, P.res));
                     unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
                 }
-                float atm[D], ao = 0.0f, inner = g.x * mp;
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    atm[c] = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) atm[c] += A[i][c] * mvb[i];
-                    const int o = stencil_offset<D>(k, c);
-                    if (o == 1) ao += atm[c];
-                    else if (o == 2) ao += 2.0f * atm[c];
-                    inner += mvb[c] * u[c];
-                }
-                inner += P.dx * ao;
-                mbs += t.w * g.x;
+                const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
+                float inner = g.x * mp;
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    const float wm = t.w * mvb[i];
-                    S0[i] += wm;
+                    inner += mvb[i] * add_offset(Ug[i], ol, dA[D - 1][i]);
+                    const float wm = wl * mvb[i];
+                    hv[i] += wm;
+                    if (ol == 1) hv2[i] += wm;
+                    else if (ol == 2) hv2[i] += 2.0f * wm;
+                }
+                hm += wl * g.x;
+                ha += wl * inner;
+                hb += dwl * inner;
+                if (ol == 2) {  // the row is complete: weight it by the other axes
+                    const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
+                    float pw = w0;
+                    if (D == 2) {
+                        xg[0] += dw0 * ha;
+                        xg[D - 1] += w0 * hb;
+                    } else {
+                        const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
+                        if (om == 0) la = lb = lc = 0.0f;
+                        la += w1 * ha;
+                        lb += dw1 * ha;
+                        lc += w1 * hb;
+                        if (om == 2) {
+                            xg[0] += dw0 * la;
+                            xg[1 % D] += w0 * lb;
+                            xg[D - 1] += w0 * lc;
+                        }
+                        pw = w0 * w1;
+                    }
+                    mbs += pw * hm;
 #pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        const int o = stencil_offset<D>(k, j);
-                        if (o == 1) T[i][j] += wm;
-                        else if (o == 2) T[i][j] += 2.0f * wm;
+                    for (int i = 0; i < D; ++i) {
+                        const float hp = pw * hv[i];
+                        S0[i] += hp;
+                        T[i][D - 1] += pw * hv2[i];
+                        if (o0 == 1) T[i][0] += hp;
+                        else if (o0 == 2) T[i][0] += 2.0f * hp;
+                        if (D == 3) {
+                            if (om == 1) T[i][1 % D] += hp;
+                            else if (om == 2) T[i][1 % D] += 2.0f * hp;
+                        }
                     }
                 }
+            }
+            // grad w is (dw along its own axis) / dx times the other weights;
+            // A^T S0 = (dA S0) / dx
 #pragma unroll
-                for (int c = 0; c < D; ++c) xb[c] += t.gw[c] * inner - t.w * atm[c];
+            for (int c = 0; c < D; ++c) {
+                float g = xg[c];
+#pragma unroll
+                for (int i = 0; i < D; ++i) g -= dA[c][i] * S0[i];
+                xb[c] += P.inv_dx * g;
             }
             float Ab[D][D], mpb = mbs;
 #pragma unroll
@@ -536,6 +603,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                 Ct[i][j] = Cb[i][j] + P.dt * fft;
                 Fo[i][j] = ctf;
             }
+        store_mat<D>(a.adj, L::F, np, p, Fo);  // complete: the stencil sums add nothing to it
         const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
         float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
         const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
@@ -548,52 +616,99 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                 grid_velocity<D, EXT>(P, c, g.x, mv, gv, a.n_p2g - 1);  // Eq. 16-18 once per node
                 return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
             });
-        // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T), factored
-        // with dpos = (o - r) dx: the node's velocity adjoint is
-        //   w (vt + kappa Ct dpos) = w (q + kappa dx Ct o),  q = vt - kappa dx Ct r
-        float q[D];
+        // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T) with
+        // dpos = (o - r) dx: the node's velocity adjoint is w sv,
+        //   sv = vt + kappa Ct dpos = q + kappa dx Ct o,  q = vt - kappa dx Ct r,
+        // and xbar += sum (grad w) (V . sv) - kappa Ct^T sum w V.  The stencil
+        // sums run axis by axis as in P2G^T; only the scatter needs the
+        // node's weight.
+        float q[D], dC[D][D];  // dC[c][i] = kappa dx Ct_ic
         const float kdx = P.kappa * P.dx;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             float cr = 0.0f;
 #pragma unroll
-            for (int j = 0; j < D; ++j) cr += Ct[i][j] * s.r[j];
+            for (int j = 0; j < D; ++j) {
+                cr += Ct[i][j] * s.r[j];
+                dC[j][i] = kdx * Ct[i][j];
+            }
             q[i] = vt[i] - kdx * cr;
         }
+        const int nb = base_node<D>(s, P.res);
+        const int sb = box.use ? box_slot<D>(box, s.base) : 0;
+        float xg[D], vs[D], Sg[D], hv[D], pw = 0.0f, ha = 0.0f, hb = 0.0f, la = 0.0f, lb = 0.0f, lc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) xg[i] = vs[i] = Sg[i] = hv[i] = 0.0f;
 #pragma unroll
         for (int k = 0; k < stencil_size<D>(); ++k) {
-            NodeTerm<D> t;
-            node_term<D>(s, k, P, t);
+            const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+            const int ol = stencil_offset<D>(k, D - 1);
+            if (ol == 0) {  // a new row along the last axis
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    float sg = add_offset(q[i], o0, dC[0][i]);
+                    if (D == 3) sg = add_offset(sg, om, dC[1 % D][i]);
+                    Sg[i] = sg;
+                    hv[i] = 0.0f;
+                }
+                ha = hb = 0.0f;
+                pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
+            }
+            const int node = nb + node_offset<D>(k, P.res);
             float gv[D];
-            if (box.use) unpack3<D>(sm[box_slot<D>(box, t.c)], gv);
-            else node_velocity<D, FUSE_V, EXT>(Vi, t, P, gv, a.n_p2g - 1);
+            if (box.use) {
+                unpack3<D>(sm[sb + box_offset<D>(k)], gv);
+            } else {
+                NodeTerm<D> t;
+                t.node = node;
+#pragma unroll
+                for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
+                node_velocity<D, FUSE_V, EXT>(Vi, t, P, gv, a.n_p2g - 1);
+            }
+            const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
             float sv[D], dot = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                float co = 0.0f;  // (Ct o)_i
+                sv[i] = add_offset(Sg[i], ol, dC[D - 1][i]);
+                dot += gv[i] * sv[i];  // V . (vt + kappa Ct dpos)
+                hv[i] += wl * gv[i];
+            }
+            ha += wl * dot;
+            hb += dwl * dot;
+            const float w = pw * wl;
 #pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    const int o = stencil_offset<D>(k, j);
-                    if (o == 1) co += Ct[i][j];
-                    else if (o == 2) co += 2.0f * Ct[i][j];
+            for (int i = 0; i < D; ++i) sv[i] *= w;
+            atomicAdd(Vbi + node, make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f));
+            if (ol == 2) {  // the row is complete: weight it by the other axes
+                const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
+                if (D == 2) {
+                    xg[0] += dw0 * ha;
+                    xg[D - 1] += w0 * hb;
+                } else {
+                    const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
+                    if (om == 0) la = lb = lc = 0.0f;
+                    la += w1 * ha;
+                    lb += dw1 * ha;
+                    lc += w1 * hb;
+                    if (om == 2) {
+                        xg[0] += dw0 * la;
+                        xg[1 % D] += w0 * lb;
+                        xg[D - 1] += w0 * lc;
+                    }
                 }
-                sv[i] = q[i] + kdx * co;
-                dot += gv[i] * sv[i];  // gv . (vt + kappa Ct dpos)
+#pragma unroll
+                for (int i = 0; i < D; ++i) vs[i] += pw * hv[i];
             }
+        }
+        // kappa Ct^T vs = (dC vs) / dx
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                float ctv = 0.0f;
+        for (int c = 0; c < D; ++c) {
+            float g = xg[c];
 #pragma unroll
-                for (int i = 0; i < D; ++i) ctv += Ct[i][c] * gv[i];
-                xb[c] += t.gw[c] * dot - P.kappa * t.w * ctv;
-            }
-#pragma unroll
-            for (int i = 0; i < D; ++i) sv[i] *= t.w;
-            float4 c4 = make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f);
-            atomicAdd(Vbi + t.node, c4);
+            for (int i = 0; i < D; ++i) g -= dC[c][i] * vs[i];
+            xb[c] += P.inv_dx * g;
         }
         store_vec<D>(a.adj, L::X, np, p, xb);
-        store_mat<D>(a.adj, L::F, np, p, Fo);
     }
     if (flags) atomicOr(a.err, flags);
 }

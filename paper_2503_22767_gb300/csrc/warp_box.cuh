@@ -80,6 +80,15 @@ __device__ __forceinline__ int box_slot(const WarpBox<D>& b, const int (&c)[D]) 
     return i;
 }
 
+// Slot of stencil node k relative to the slot of the stencil's base node
+// (every stencil node of a lane lies inside the box when it is used, so the
+// per-axis fields never carry into each other).
+template <int D>
+__device__ __forceinline__ constexpr int box_offset(int k) {
+    return D == 2 ? ((k / 3) << box_log<D>(1)) + k % 3
+                  : ((k / 9) << (box_log<D>(1) + box_log<D>(2))) + (((k / 3) % 3) << box_log<D>(2)) + k % 3;
+}
+
 // Every lane of the warp: fill this warp's slots `sm` with load(c, node) for
 // the box nodes inside the touched extent.  node is the index within the
 // instance grid.  The other slots are left as they are and never read.
