@@ -14,13 +14,14 @@ namespace mpm {
 
 // Launch a per-substep kernel; with P.pdl the launch allows programmatic
 // dependent launch (the kernel begins with pdl_wait()).
+// launch_chain_smem also gives the launch smem bytes of dynamic shared memory.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_chain(const Params& P, void (*kernel)(KArgs...), dim3 grid, dim3 block,
-                         cudaStream_t st, Args&&... args) {
+cudaError_t launch_chain_smem(const Params& P, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -28,6 +29,12 @@ cudaError_t launch_chain(const Params& P, void (*kernel)(KArgs...), dim3 grid, d
     cfg.attrs = attr;
     cfg.numAttrs = P.pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chain(const Params& P, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                         cudaStream_t st, Args&&... args) {
+    return launch_chain_smem(P, kernel, grid, block, 0, st, std::forward<Args>(args)...);
 }
 
 template <int D>

@@ -49,6 +49,13 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
     // kernel before the grid kernel has completed, and the state loads can
     // overlap the grid kernel's tail.
     constexpr bool kEarly = G2P && !FUSE;
+    // the P2G scatter is aggregated over the lanes of one cell (scatter_aggregated)
+    constexpr bool AGG = P2G && aggregate_scatter<D>();
+    // per warp (dynamic shared memory, warp_slots<D, P2G>() float4 per
+    // warp): the staged gather box of G2P, then the scatter slab of P2G
+    constexpr int kSlots = warp_slots<D, P2G>();
+    extern __shared__ float4 s_warp[];
+    float4* sm = s_warp + (threadIdx.x >> 5) * kSlots;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
@@ -78,8 +85,6 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
         for (int i = 0; i < D; ++i) s.base[i] = 0;
         if (active && !make_stencil<D>(x, P, s)) flags |= kErrDomain;
         const float4* __restrict__ Vg = FUSE ? a.accG : a.V;
-        __shared__ float4 s_box[kBoxWarps * box_nodes<D>()];
-        float4* sm = s_box + (threadIdx.x >> 5) * box_nodes<D>();
         const WarpBox<D> box = warp_box<D>(s.base, active, inst, P.box != 0);
         if (box.use) {
             const float4* __restrict__ Vb = Vg + (long long)box.inst * P.nodes;
@@ -102,16 +107,18 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
 #pragma unroll
                 for (int j = 0; j < D; ++j) C[i][j] = 0.0f;  // sum w V o^T
             }
+            // The sums run axis by axis: over the last axis with its 1D weights
+            // (hv = sum w_l V, hv2 = sum o_l w_l V), then each row is weighted
+            // by the product pw of the other axes' weights.
             const int nb = base_node<D>(s, P.res);
             const int sb = box.use ? box_slot<D>(box, s.base) : 0;
-            float pw = 0.0f;  // product of the weights of all but the last axis
+            float hv[D], hv2[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) hv[i] = hv2[i] = 0.0f;
 #pragma unroll
             for (int k = 0; k < stencil_size<D>(); ++k) {
+                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
                 const int ol = stencil_offset<D>(k, D - 1);
-                if (ol == 0)
-                    pw = D == 2 ? s.w[0][stencil_offset<D>(k, 0)]
-                                : s.w[0][stencil_offset<D>(k, 0)] * s.w[1 % D][stencil_offset<D>(k, 1 % D)];
-                const float w = pw * s.w[D - 1][ol];
                 float gv[D];
                 if (box.use) {
                     unpack3<D>(sm[sb + box_offset<D>(k)], gv);
@@ -122,15 +129,23 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
                     for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
                     node_velocity<D, FUSE, EXT>(Vi, t, P, gv, a.n_g2p);
                 }
+                const float wl = s.w[D - 1][ol];
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    const float wv = w * gv[i];
-                    v[i] += wv;
+                    const float wv = wl * gv[i];
+                    hv[i] = ol == 0 ? wv : hv[i] + wv;
+                    if (ol == 0) hv2[i] = 0.0f;
+                    else hv2[i] = add_offset(hv2[i], ol, wv);
+                }
+                if (ol == 2) {  // the row is complete
+                    const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
 #pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        const int o = stencil_offset<D>(k, j);
-                        if (o == 1) C[i][j] += wv;
-                        else if (o == 2) C[i][j] += 2.0f * wv;
+                    for (int i = 0; i < D; ++i) {
+                        const float hp = pw * hv[i];
+                        v[i] += hp;
+                        C[i][D - 1] += pw * hv2[i];
+                        C[i][0] = add_offset(C[i][0], o0, hp);
+                        if (D == 3) C[i][1 % D] = add_offset(C[i][1 % D], om, hp);
                     }
                 }
             }
@@ -169,75 +184,111 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forwar
         if (P.loss_kind == 1 && a.mom != nullptr)
             warp_add_per_instance<1>(mom_x, inst, a.mom + (long long)a.n_g2p * P.n_inst, 1);
     }
-    if (P2G && active) {
+    if (P2G) {
         Stencil<D> s;
-        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
-        StressParts<D> S;
-        stress_parts<D>(F, phi, P, S);
-        if (!(S.J > 0.0f)) flags |= kErrNumeric;
-        float Br[D], Ba[D], Pk[D][D], A[D][D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            Br[i] = a.mag[(long long)i * np + p];
-            Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
-        }
-        if (EXT && P.ext->fgrad) {
-            const float* Gn = P.ext->fgrad + ((long long)inst * P.n_steps + a.n_p2g) * D * D;
-            field_at_particle<D>(Gn, x, Ba);
-            // body force of the non-uniform field, folded into the momentum
-            // m v (f and m both vanish with phi, so m > 0 whenever f != 0)
-            float f[D];
-            magnetic_force<D>(Gn, F, Br, S.s, P, f);
-            if (mp > 0.0f) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) v[i] += P.dt * f[i] / mp;
-            }
-        }
-        piola<D>(S, Br, Ba, Pk);
-        const float sc = P.dt * P.kappa * P.p_vol;
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
-#pragma unroll
-                for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
-                // MLS-MPM affine momentum (Eq. 15 with the time step and the
-                // x_i - x_p offset of the MLS-MPM form): m C - dt (4/dx^2) V P F^T
-                A[i][j] = mp * C[i][j] - sc * pft;
-            }
-        float4* __restrict__ ai = a.acc + (long long)inst * P.nodes;
-        // Eq. 15 with x_i - x_p = (o - r) dx: node momentum w (u + dx A o),
-        // u = m v - dx A r
-        float u[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            float ar = 0.0f;
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                A[i][j] *= P.dx;
-                ar += A[i][j] * s.r[j];
-            }
-            u[i] = mp * v[i] - ar;
-        }
-        const int nb = base_node<D>(s, P.res);
-        float pw = 0.0f;  // product of the weights of all but the last axis
-#pragma unroll
-        for (int k = 0; k < stencil_size<D>(); ++k) {
-            const int ol = stencil_offset<D>(k, D - 1);
-            if (ol == 0)
-                pw = D == 2 ? s.w[0][stencil_offset<D>(k, 0)]
-                            : s.w[0][stencil_offset<D>(k, 0)] * s.w[1 % D][stencil_offset<D>(k, 1 % D)];
-            const float w = pw * s.w[D - 1][ol];
-            float mv[D];
+        float A[D][D], u[D];
+        int nb = 0;
+        float4* __restrict__ ai = a.acc + (long long)(active ? inst : 0) * P.nodes;
+        if (active) {
+            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+            StressParts<D> S;
+            stress_parts<D>(F, phi, P, S);
+            if (!(S.J > 0.0f)) flags |= kErrNumeric;
+            float Br[D], Ba[D], Pk[D][D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                float m = u[i];
-#pragma unroll
-                for (int j = 0; j < D; ++j) m = add_offset(m, stencil_offset<D>(k, j), A[i][j]);
-                mv[i] = w * m;
+                Br[i] = a.mag[(long long)i * np + p];
+                Ba[i] = __ldg(a.field + ((long long)inst * P.n_steps + a.n_p2g) * D + i);
             }
-            atomicAdd(ai + nb + node_offset<D>(k, P.res), pack4<D>(w * mp, mv));  // Eq. 14 in .x
+            if (EXT && P.ext->fgrad) {
+                const float* Gn = P.ext->fgrad + ((long long)inst * P.n_steps + a.n_p2g) * D * D;
+                field_at_particle<D>(Gn, x, Ba);
+                // body force of the non-uniform field, folded into the momentum
+                // m v (f and m both vanish with phi, so m > 0 whenever f != 0)
+                float f[D];
+                magnetic_force<D>(Gn, F, Br, S.s, P, f);
+                if (mp > 0.0f) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) v[i] += P.dt * f[i] / mp;
+                }
+            }
+            piola<D>(S, Br, Ba, Pk);
+            const float sc = P.dt * P.kappa * P.p_vol;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float pft = Pk[i][j];  // (P F^T)_ij with F = I + E
+#pragma unroll
+                    for (int k = 0; k < D; ++k) pft += Pk[i][k] * F[j][k];
+                    // MLS-MPM affine momentum (Eq. 15 with the time step and the
+                    // x_i - x_p offset of the MLS-MPM form): m C - dt (4/dx^2) V P F^T
+                    A[i][j] = mp * C[i][j] - sc * pft;
+                }
+            // Eq. 15 with x_i - x_p = (o - r) dx: node momentum w (u + dx A o),
+            // u = m v - dx A r
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float ar = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    A[i][j] *= P.dx;
+                    ar += A[i][j] * s.r[j];
+                }
+                u[i] = mp * v[i] - ar;
+            }
+            nb = base_node<D>(s, P.res);
+        } else {  // a lane past the end takes part in the aggregated scatter with zeros
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                u[i] = 0.0f;
+                s.base[i] = 0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) A[i][j] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) s.w[i][j] = 0.0f;
+            }
+        }
+        if constexpr (AGG) {
+            // node (o0, .., ol) receives w (mp, u + A o), w = (w0 w1) w2 as below
+            scatter_aggregated<D>(nb, inst, active, ai, P.res, sm, [&](int k) {
+                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                const int ol = stencil_offset<D>(k, D - 1);
+                const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
+                const float w = pw * s.w[D - 1][ol];
+                float mv[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    float t = add_offset(u[i], o0, A[i][0]);
+                    if (D == 3) t = add_offset(t, om, A[i][1 % D]);
+                    mv[i] = w * add_offset(t, ol, A[i][D - 1]);
+                }
+                return pack4<D>(w * mp, mv);
+            });
+        } else if (active) {
+            float pw = 0.0f, Ug[D];  // per row: product of the other axes' weights, u + dx A o
+#pragma unroll
+            for (int i = 0; i < D; ++i) Ug[i] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < stencil_size<D>(); ++k) {
+                const int ol = stencil_offset<D>(k, D - 1);
+                if (ol == 0)
+                    pw = D == 2 ? s.w[0][stencil_offset<D>(k, 0)]
+                                : s.w[0][stencil_offset<D>(k, 0)] * s.w[1 % D][stencil_offset<D>(k, 1 % D)];
+                const float w = pw * s.w[D - 1][ol];
+                if (ol == 0) {  // a new row: u + dx A o over all but the last axis
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        float ug = add_offset(u[i], stencil_offset<D>(k, 0), A[i][0]);
+                        if (D == 3) ug = add_offset(ug, stencil_offset<D>(k, 1 % D), A[i][1 % D]);
+                        Ug[i] = ug;
+                    }
+                }
+                float mv[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) mv[i] = w * add_offset(Ug[i], ol, A[i][D - 1]);
+                atomicAdd(ai + nb + node_offset<D>(k, P.res), pack4<D>(w * mp, mv));  // Eq. 14 in .x
+            }
         }
     }
     if (flags) atomicOr(a.err, flags);
@@ -288,8 +339,12 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     // warps with every lane active may stage their stencil nodes (the staging
     // runs inside the per-particle branches)
     const bool full_warp = __ballot_sync(0xffffffffu, active) == 0xffffffffu;
-    __shared__ float4 s_box[kBoxWarps * box_nodes<D>()];
-    float4* sm = s_box + (threadIdx.x >> 5) * box_nodes<D>();
+    // per warp (dynamic shared memory, warp_slots<D, G2PT>() float4 per
+    // warp): the staged gather boxes, then the scatter slab of G2P^T
+    constexpr bool AGG = G2PT && aggregate_scatter<D>();
+    constexpr int kSlots = warp_slots<D, G2PT>();
+    extern __shared__ float4 s_warp[];
+    float4* sm = s_warp + (threadIdx.x >> 5) * kSlots;
     float bab[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) bab[i] = 0.0f;
@@ -572,143 +627,175 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
             store_mat<D>(a.adj, L::F, np, p, Fb);
         }
     }
-    if (G2PT && active) {
-        if (!P2GT) {
-            // adjoint of state m+1 and C_{m+1} from memory
-            load_vec<D>(a.adj, L::X, np, p, xb);
-            load_vec<D>(a.adj, L::V, np, p, vb);
-            load_mat<D>(a.adj, L::C, np, p, Cb);
-            load_mat<D>(a.adj, L::F, np, p, Fb);
-            load_mat<D>(a.s_in, L::C, np, p, Cn);
-        }
-        float x[D], F[D][D];
-        load_vec<D>(a.s_aux, L::X, np, p, x);
-        load_mat<D>(a.s_aux, L::F, np, p, F);
+    if (G2PT) {
         Stencil<D> s;
-        if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
-        // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
-        float vt[D], Ct[D][D], Fo[D][D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) vt[i] = vb[i] + P.dt * xb[i];
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                float fft = Fb[i][j], ctf = Fb[i][j];  // F = I + E
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    fft += Fb[i][k] * F[j][k];          // (Fbar F^T)_ij
-                    ctf += P.dt * Cn[k][i] * Fb[k][j];  // ((I + dt C')^T Fbar)_ij
-                }
-                Ct[i][j] = Cb[i][j] + P.dt * fft;
-                Fo[i][j] = ctf;
-            }
-        store_mat<D>(a.adj, L::F, np, p, Fo);  // complete: the stencil sums add nothing to it
-        const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
-        float4* __restrict__ Vbi = a.Vbar + (long long)inst * P.nodes;
-        const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
-        if (box.use)
-            stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
-                const float4 g = __ldg(Vi + node);
-                if (!FUSE_V) return g;
-                float mv[D], gv[D];
-                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                grid_velocity<D, EXT>(P, c, g.x, mv, gv, a.n_p2g - 1);  // Eq. 16-18 once per node
-                return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
-            });
-        // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T) with
-        // dpos = (o - r) dx: the node's velocity adjoint is w sv,
-        //   sv = vt + kappa Ct dpos = q + kappa dx Ct o,  q = vt - kappa dx Ct r,
-        // and xbar += sum (grad w) (V . sv) - kappa Ct^T sum w V.  The stencil
-        // sums run axis by axis as in P2G^T; only the scatter needs the
-        // node's weight.
         float q[D], dC[D][D];  // dC[c][i] = kappa dx Ct_ic
-        const float kdx = P.kappa * P.dx;
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            float cr = 0.0f;
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                cr += Ct[i][j] * s.r[j];
-                dC[j][i] = kdx * Ct[i][j];
+        int nb = 0;
+        float4* __restrict__ Vbi = a.Vbar + (long long)(active ? inst : 0) * P.nodes;
+        if (active) {
+            if (!P2GT) {
+                // adjoint of state m+1 and C_{m+1} from memory
+                load_vec<D>(a.adj, L::X, np, p, xb);
+                load_vec<D>(a.adj, L::V, np, p, vb);
+                load_mat<D>(a.adj, L::C, np, p, Cb);
+                load_mat<D>(a.adj, L::F, np, p, Fb);
+                load_mat<D>(a.s_in, L::C, np, p, Cn);
             }
-            q[i] = vt[i] - kdx * cr;
-        }
-        const int nb = base_node<D>(s, P.res);
-        const int sb = box.use ? box_slot<D>(box, s.base) : 0;
-        float xg[D], vs[D], Sg[D], hv[D], pw = 0.0f, ha = 0.0f, hb = 0.0f, la = 0.0f, lb = 0.0f, lc = 0.0f;
+            float x[D], F[D][D];
+            load_vec<D>(a.s_aux, L::X, np, p, x);
+            load_mat<D>(a.s_aux, L::F, np, p, F);
+            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+            // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
+            float vt[D], Ct[D][D], Fo[D][D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) xg[i] = vs[i] = Sg[i] = hv[i] = 0.0f;
+            for (int i = 0; i < D; ++i) vt[i] = vb[i] + P.dt * xb[i];
 #pragma unroll
-        for (int k = 0; k < stencil_size<D>(); ++k) {
-            const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
-            const int ol = stencil_offset<D>(k, D - 1);
-            if (ol == 0) {  // a new row along the last axis
+            for (int i = 0; i < D; ++i)
 #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    float sg = add_offset(q[i], o0, dC[0][i]);
-                    if (D == 3) sg = add_offset(sg, om, dC[1 % D][i]);
-                    Sg[i] = sg;
-                    hv[i] = 0.0f;
+                for (int j = 0; j < D; ++j) {
+                    float fft = Fb[i][j], ctf = Fb[i][j];  // F = I + E
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        fft += Fb[i][k] * F[j][k];          // (Fbar F^T)_ij
+                        ctf += P.dt * Cn[k][i] * Fb[k][j];  // ((I + dt C')^T Fbar)_ij
+                    }
+                    Ct[i][j] = Cb[i][j] + P.dt * fft;
+                    Fo[i][j] = ctf;
                 }
-                ha = hb = 0.0f;
-                pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
-            }
-            const int node = nb + node_offset<D>(k, P.res);
-            float gv[D];
-            if (box.use) {
-                unpack3<D>(sm[sb + box_offset<D>(k)], gv);
-            } else {
-                NodeTerm<D> t;
-                t.node = node;
-#pragma unroll
-                for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
-                node_velocity<D, FUSE_V, EXT>(Vi, t, P, gv, a.n_p2g - 1);
-            }
-            const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
-            float sv[D], dot = 0.0f;
+            store_mat<D>(a.adj, L::F, np, p, Fo);  // complete: the stencil sums add nothing to it
+            const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
+            const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
+            if (box.use)
+                stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
+                    const float4 g = __ldg(Vi + node);
+                    if (!FUSE_V) return g;
+                    float mv[D], gv[D];
+                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                    grid_velocity<D, EXT>(P, c, g.x, mv, gv, a.n_p2g - 1);  // Eq. 16-18 once per node
+                    return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
+                });
+            // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T) with
+            // dpos = (o - r) dx: the node's velocity adjoint is w sv,
+            //   sv = vt + kappa Ct dpos = q + kappa dx Ct o,  q = vt - kappa dx Ct r,
+            // and xbar += sum (grad w) (V . sv) - kappa Ct^T sum w V.  The stencil
+            // sums run axis by axis as in P2G^T; only the scatter needs the
+            // node's weight.
+            const float kdx = P.kappa * P.dx;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                sv[i] = add_offset(Sg[i], ol, dC[D - 1][i]);
-                dot += gv[i] * sv[i];  // V . (vt + kappa Ct dpos)
-                hv[i] += wl * gv[i];
-            }
-            ha += wl * dot;
-            hb += dwl * dot;
-            const float w = pw * wl;
+                float cr = 0.0f;
 #pragma unroll
-            for (int i = 0; i < D; ++i) sv[i] *= w;
-            atomicAdd(Vbi + node, make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f));
-            if (ol == 2) {  // the row is complete: weight it by the other axes
-                const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
-                if (D == 2) {
-                    xg[0] += dw0 * ha;
-                    xg[D - 1] += w0 * hb;
-                } else {
-                    const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
-                    if (om == 0) la = lb = lc = 0.0f;
-                    la += w1 * ha;
-                    lb += dw1 * ha;
-                    lc += w1 * hb;
-                    if (om == 2) {
-                        xg[0] += dw0 * la;
-                        xg[1 % D] += w0 * lb;
-                        xg[D - 1] += w0 * lc;
-                    }
+                for (int j = 0; j < D; ++j) {
+                    cr += Ct[i][j] * s.r[j];
+                    dC[j][i] = kdx * Ct[i][j];
                 }
+                q[i] = vt[i] - kdx * cr;
+            }
+            nb = base_node<D>(s, P.res);
+            const int sb = box.use ? box_slot<D>(box, s.base) : 0;
+            float xg[D], vs[D], Sg[D], hv[D], pw = 0.0f, ha = 0.0f, hb = 0.0f, la = 0.0f, lb = 0.0f, lc = 0.0f;
 #pragma unroll
-                for (int i = 0; i < D; ++i) vs[i] += pw * hv[i];
+            for (int i = 0; i < D; ++i) xg[i] = vs[i] = Sg[i] = hv[i] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < stencil_size<D>(); ++k) {
+                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                const int ol = stencil_offset<D>(k, D - 1);
+                if (ol == 0) {  // a new row along the last axis
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        float sg = add_offset(q[i], o0, dC[0][i]);
+                        if (D == 3) sg = add_offset(sg, om, dC[1 % D][i]);
+                        Sg[i] = sg;
+                        hv[i] = 0.0f;
+                    }
+                    ha = hb = 0.0f;
+                    pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
+                }
+                const int node = nb + node_offset<D>(k, P.res);
+                float gv[D];
+                if (box.use) {
+                    unpack3<D>(sm[sb + box_offset<D>(k)], gv);
+                } else {
+                    NodeTerm<D> t;
+                    t.node = node;
+#pragma unroll
+                    for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
+                    node_velocity<D, FUSE_V, EXT>(Vi, t, P, gv, a.n_p2g - 1);
+                }
+                const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
+                float sv[D], dot = 0.0f;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    sv[i] = add_offset(Sg[i], ol, dC[D - 1][i]);
+                    dot += gv[i] * sv[i];  // V . (vt + kappa Ct dpos)
+                    hv[i] += wl * gv[i];
+                }
+                ha += wl * dot;
+                hb += dwl * dot;
+                if constexpr (!AGG) {
+                    const float w = pw * wl;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) sv[i] *= w;
+                    atomicAdd(Vbi + node, make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f));
+                }
+                if (ol == 2) {  // the row is complete: weight it by the other axes
+                    const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
+                    if (D == 2) {
+                        xg[0] += dw0 * ha;
+                        xg[D - 1] += w0 * hb;
+                    } else {
+                        const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
+                        if (om == 0) la = lb = lc = 0.0f;
+                        la += w1 * ha;
+                        lb += dw1 * ha;
+                        lc += w1 * hb;
+                        if (om == 2) {
+                            xg[0] += dw0 * la;
+                            xg[1 % D] += w0 * lb;
+                            xg[D - 1] += w0 * lc;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < D; ++i) vs[i] += pw * hv[i];
+                }
+            }
+            // kappa Ct^T vs = (dC vs) / dx
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                float g = xg[c];
+#pragma unroll
+                for (int i = 0; i < D; ++i) g -= dC[c][i] * vs[i];
+                xb[c] += P.inv_dx * g;
+            }
+            store_vec<D>(a.adj, L::X, np, p, xb);
+        } else {  // a lane past the end takes part in the aggregated scatter with zeros
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                q[i] = 0.0f;
+                s.base[i] = 0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) dC[i][j] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) s.w[i][j] = 0.0f;
             }
         }
-        // kappa Ct^T vs = (dC vs) / dx
+        if constexpr (AGG) {
+            // node (o0, .., ol) receives w sv, sv = q + kappa dx Ct o, as above
+            scatter_aggregated<D>(nb, inst, active, Vbi, P.res, sm, [&](int k) {
+                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                const int ol = stencil_offset<D>(k, D - 1);
+                const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
+                const float w = pw * s.w[D - 1][ol];
+                float sv[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            float g = xg[c];
-#pragma unroll
-            for (int i = 0; i < D; ++i) g -= dC[c][i] * vs[i];
-            xb[c] += P.inv_dx * g;
+                for (int i = 0; i < D; ++i) {
+                    float t = add_offset(q[i], o0, dC[0][i]);
+                    if (D == 3) t = add_offset(t, om, dC[1 % D][i]);
+                    sv[i] = w * add_offset(t, ol, dC[D - 1][i]);
+                }
+                return make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f);
+            });
         }
-        store_vec<D>(a.adj, L::X, np, p, xb);
     }
     if (flags) atomicOr(a.err, flags);
 }
@@ -724,24 +811,28 @@ static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, cons
     long long threads = P.n_total > 0 ? P.n_total : block;
     dim3 grid(particle_blocks(threads, block));
     const bool ext = P.ext != nullptr;
+    const size_t warps = (size_t)(block + 31) / 32;
+    auto go = [&](auto kernel, size_t smem) { return launch_chain_smem(P, kernel, grid, block, smem, st, P, a); };
+    const size_t smem_p2g = warps * warp_slots<D, true>() * sizeof(float4);
+    const size_t smem_g2p = warps * warp_slots<D, false>() * sizeof(float4);
     if (g2p && p2g) {
         if (ext) {
-            if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE, true>, grid, block, st, P, a);
-            return launch_chain(P, k_forward<D, true, true, false, FUSE, true>, grid, block, st, P, a);
+            if (all) return go(k_forward<D, true, true, true, FUSE, true>, smem_p2g);
+            return go(k_forward<D, true, true, false, FUSE, true>, smem_p2g);
         }
-        if (all) return launch_chain(P, k_forward<D, true, true, true, FUSE, false>, grid, block, st, P, a);
-        return launch_chain(P, k_forward<D, true, true, false, FUSE, false>, grid, block, st, P, a);
+        if (all) return go(k_forward<D, true, true, true, FUSE, false>, smem_p2g);
+        return go(k_forward<D, true, true, false, FUSE, false>, smem_p2g);
     } else if (g2p) {
         // with grid fusion the G2P applies the grid operation, boxes included
         if (ext && FUSE) {
-            if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE, true>, grid, block, st, P, a);
-            return launch_chain(P, k_forward<D, true, false, false, FUSE, true>, grid, block, st, P, a);
+            if (all) return go(k_forward<D, true, false, true, FUSE, true>, smem_g2p);
+            return go(k_forward<D, true, false, false, FUSE, true>, smem_g2p);
         }
-        if (all) return launch_chain(P, k_forward<D, true, false, true, FUSE, false>, grid, block, st, P, a);
-        return launch_chain(P, k_forward<D, true, false, false, FUSE, false>, grid, block, st, P, a);
+        if (all) return go(k_forward<D, true, false, true, FUSE, false>, smem_g2p);
+        return go(k_forward<D, true, false, false, FUSE, false>, smem_g2p);
     } else {
-        if (ext) return launch_chain(P, k_forward<D, false, true, false, FUSE, true>, grid, block, st, P, a);
-        return launch_chain(P, k_forward<D, false, true, false, FUSE, false>, grid, block, st, P, a);
+        if (ext) return go(k_forward<D, false, true, false, FUSE, true>, smem_p2g);
+        return go(k_forward<D, false, true, false, FUSE, false>, smem_p2g);
     }
     return cudaGetLastError();
 }
@@ -761,19 +852,23 @@ static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepAr
     dim3 grid(particle_blocks(threads, block));
     // with solid boxes or a field gradient only the 128-register budget is built
     const bool ext = P.ext != nullptr;
+    const size_t warps = (size_t)(block + 31) / 32;
+    auto go = [&](auto kernel, size_t smem) { return launch_chain_smem(P, kernel, grid, block, smem, st, P, a); };
+    const size_t sm_g2pt = warps * warp_slots<D, true>() * sizeof(float4);
+    const size_t sm_p2gt = warps * warp_slots<D, false>() * sizeof(float4);
     if (p2gt && g2pt) {
-        if (ext) return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 2, true>, grid, block, st, P, a);
+        if (ext) return go(k_adjoint<D, true, true, FUSE, FUSE_V, 2, true>, sm_g2pt);
         if (P.adj_blocks == 3)
-            return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 3, false>, grid, block, st, P, a);
-        return launch_chain(P, k_adjoint<D, true, true, FUSE, FUSE_V, 2, false>, grid, block, st, P, a);
+            return go(k_adjoint<D, true, true, FUSE, FUSE_V, 3, false>, sm_g2pt);
+        return go(k_adjoint<D, true, true, FUSE, FUSE_V, 2, false>, sm_g2pt);
     }
     // the segment-edge halves run once per checkpoint segment
     if (p2gt) {
-        if (ext) return launch_chain(P, k_adjoint<D, true, false, FUSE, FUSE_V, 2, true>, grid, block, st, P, a);
-        return launch_chain(P, k_adjoint<D, true, false, FUSE, FUSE_V, 2, false>, grid, block, st, P, a);
+        if (ext) return go(k_adjoint<D, true, false, FUSE, FUSE_V, 2, true>, sm_p2gt);
+        return go(k_adjoint<D, true, false, FUSE, FUSE_V, 2, false>, sm_p2gt);
     }
-    if (ext) return launch_chain(P, k_adjoint<D, false, true, FUSE, FUSE_V, 2, true>, grid, block, st, P, a);
-    return launch_chain(P, k_adjoint<D, false, true, FUSE, FUSE_V, 2, false>, grid, block, st, P, a);
+    if (ext) return go(k_adjoint<D, false, true, FUSE, FUSE_V, 2, true>, sm_g2pt);
+    return go(k_adjoint<D, false, true, FUSE, FUSE_V, 2, false>, sm_g2pt);
 }
 
 template <int D>
