@@ -55,6 +55,24 @@ __device__ __forceinline__ void unpack3(const float4& g, float (&v)[D]) {
     if (D == 3) v[2 % D] = g.z;
 }
 
+// A load that stays where it is written (asm volatile, so it is neither
+// merged with an earlier load of the same address nor moved): reloading a
+// value after a long stretch of code frees its registers in between.
+__device__ __forceinline__ float reload(const float* p) {
+    float v;
+    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+template <int D>
+__device__ __forceinline__ void reload_mat(const float* __restrict__ s, int base, long long np, int p,
+                                           float (&M)[D][D]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) M[a][b] = reload(s + (long long)(base + a * D + b) * np + p);
+}
+
 template <int D>
 __device__ __forceinline__ void load_vec(const float* __restrict__ s, int base, long long np, int p,
                                          float (&v)[D]) {

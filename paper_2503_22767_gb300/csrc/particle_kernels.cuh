@@ -328,7 +328,6 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
         load_mat<D>(a.s_in, L::C, np, p, Cn);
         load_mat<D>(a.s_in, L::F, np, p, F_n);
         load_vec<D>(a.adj, L::X, np, p, xb);
-        load_mat<D>(a.adj, L::F, np, p, Fb);
         phi_n = a.phi[p];
     };
     if (kEarly && active) load_state_n();
@@ -519,6 +518,15 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     }
                 }
             }
+            // The node loop needs none of C, E, the stress (all used for A
+            // before it) and Fbar of state n: they are read again, and the
+            // stress recomputed, here, so their registers are free during the
+            // loop (the recomputation is cheaper than the spills).
+            reload_mat<D>(a.s_in, L::C, np, p, Cn);
+            reload_mat<D>(a.s_in, L::F, np, p, F);
+            load_mat<D>(a.adj, L::F, np, p, Fb);
+            stress_parts<D>(F, phi, P, S);
+            piola<D>(S, Br, Ba, Pk);
             // grad w is (dw along its own axis) / dx times the other weights;
             // A^T S0 = (dA S0) / dx
 #pragma unroll
