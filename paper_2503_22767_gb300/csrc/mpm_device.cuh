@@ -66,6 +66,9 @@ struct Extras {
 // Without a programmatic predecessor both instructions are no-ops.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// A hint to bring the line holding *p into L2 (the point of coherence, so it
+// is safe for data another kernel may still write); no register is used.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Index of the instance owning particle p (instance ranges are contiguous
 // and survive the cell sort, whose key starts with the instance).

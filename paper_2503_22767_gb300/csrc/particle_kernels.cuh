@@ -331,6 +331,22 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
         phi_n = a.phi[p];
     };
     if (kEarly && active) load_state_n();
+    if (P2GT && G2PT && active) {
+        // x and E of state m = n-1 (G2P^T) come from the segment store in HBM;
+        // request them now so that their loads after P2G^T find them in L2
+#pragma unroll
+        for (int c = 0; c < D; ++c) prefetch_l2(a.s_aux + (long long)(L::X + c) * np + p);
+#pragma unroll
+        for (int c = 0; c < D * D; ++c) prefetch_l2(a.s_aux + (long long)(L::F + c) * np + p);
+    }
+    if (P2GT && active) {  // the design and its gradients, read late in P2G^T
+        prefetch_l2(a.gphi + p);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            prefetch_l2(a.mag + (long long)c * np + p);
+            prefetch_l2(a.gmag + (long long)c * np + p);
+        }
+    }
     pdl_wait();
     pdl_trigger();
     clear_buffer(a);
