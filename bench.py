@@ -106,6 +106,34 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+# DRAM traffic per launch of the dominant kernel, from an ncu capture summarised
+# under profiles/ (traffic.json).  A figure is used only while the particle
+# kernels' sources hash to the value stored beside it, i.e. while the kernel
+# is the one the counters were taken on; otherwise traffic is null.
+KERNEL_SOURCES = ("particle_kernels.cuh", "mpm_device.cuh", "particle_io.cuh", "warp_box.cuh")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2503_22767_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, kernel_class):
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+        e = rec[workload][kernel_class]
+        if e["kernel_sources_sha256_16"] != kernel_source_hash():
+            return None, "kernel changed since the capture"
+        return float(e["dram_bytes_per_launch"]), e["profile"]
+    except (OSError, KeyError, ValueError, TypeError):
+        return None, "no capture recorded for this workload and kernel"
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -304,6 +332,9 @@ def run_ours(args):
                           "one extra design iteration on one stream after the timed region")
     if args.traffic_bytes:
         roofline["traffic"] = args.traffic_bytes
+        roofline["traffic_source"] = "--traffic-bytes"
+    else:
+        roofline["traffic"], roofline["traffic_source"] = recorded_traffic(args.workload, CLASS_NAMES[dom])
     # the whole design iteration against the same peak: algorithmic bytes of
     # every particle-substep over the timed step
     bps = particle_step_bytes(cfg)
