@@ -31,6 +31,10 @@ namespace mpm {
 // kernel is held to 64 registers, and the adjoint kernel is compiled for 2
 // (<= 128 registers) and 3 (<= 80) blocks, chosen per launch (Params::adj_blocks).
 constexpr int kMinBlocksForward3 = 4;
+// 2D: at most 48 registers (40 warps per SM, no spills); the 2D batch's
+// forward launch went from 83 to 79 us, the single 2D locomotion body is
+// unchanged (its 469 blocks of 64 threads are far from filling the GPU)
+constexpr int kMinBlocksForward2 = 5;
 
 namespace {
 
@@ -40,7 +44,7 @@ inline int particle_blocks(long long n, int block) { return (int)((n + block - 1
 // EXT: P.ext is set (solid boxes or a non-uniform field); without it the
 // kernel carries no code for the field gradient.
 template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT>
-__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : 1) k_forward(Params P, StepArgs a) {
+__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksForward2) k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
     // Early loads: with the grid operation in its own kernel, this kernel's
     // predecessor is that grid kernel, which writes none of the particle
