@@ -212,9 +212,9 @@ enum {
                            launch, so a kernel's CTAs are scheduled while its predecessor
                            drains; 0: plain stream order */
     MPM_OPT_ADJOINT_BLOCKS = 8, /* register budget of the fused adjoint particle kernel, as
-                           resident 256-thread blocks per SM: 2 (default, <= 128 registers)
-                           or 3 (<= 80 registers: more warps to hide gather latency, at the
-                           cost of spills) */
+                           resident 256-thread blocks per SM: 2 (default, <= 128 registers),
+                           3 (<= 80 registers: more warps to hide gather latency, at the
+                           cost of spills) or 4 (<= 64 registers; 2D only, 3D takes it as 3) */
     MPM_OPT_WARP_BOX = 9 /* 1 (default in 3D): in the direct particle kernels, each fully
                            active warp whose stencils fit a 128-node box loads that box into
                            shared memory once, and its gathers read from there; 0 (default

@@ -1009,7 +1009,7 @@ bool cache_lookup(const char* path, const std::string& sig, TuneChoice* out) {
         if (std::sscanf(p + key.size(),
                         "{\"block\": %d, \"fuse\": %d, \"tile\": %d, \"adj\": %d, \"box\": %d, \"ms\": %lf}",
                         &c.block, &c.fuse, &c.tile, &c.adj, &c.box, &c.ms) == 6 &&
-            (c.adj == 2 || c.adj == 3) && (c.box == 0 || c.box == 1)) {
+            c.adj >= 2 && c.adj <= 4 && (c.box == 0 || c.box == 1)) {
             *out = c;
             found = true;
         }
@@ -1078,8 +1078,10 @@ int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cu
     int rc = MPM_OK;
     for (int block : {64, 128, 256}) {
         for (int fuse : {0, 1}) {
-            for (int cand = 0; cand < 4; ++cand) {
-                const int adj = 2 + (cand & 1), box = cand >> 1;
+            // register budgets: 2 and 3 blocks per SM, and 4 in 2D
+            const int n_adj = h->dim == 2 ? 3 : 2;
+            for (int cand = 0; cand < 2 * n_adj; ++cand) {
+                const int adj = 2 + cand % n_adj, box = cand / n_adj;
                 TuneChoice c{block, fuse, 0, adj, box, 0.0};
                 apply_choice(h, c);
                 h->tune_T = sample;
@@ -1372,7 +1374,7 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             h->P.box = (int)value;
             return MPM_OK;
         case MPM_OPT_ADJOINT_BLOCKS:
-            if (value != 2 && value != 3) return fail(h, MPM_ERR_ARG, "adjoint blocks must be 2 or 3");
+            if (value < 2 || value > 4) return fail(h, MPM_ERR_ARG, "adjoint blocks must be 2, 3 or 4");
             if (h->P.adj_blocks != (int)value) drop_graphs(h);
             h->P.adj_blocks = (int)value;
             return MPM_OK;

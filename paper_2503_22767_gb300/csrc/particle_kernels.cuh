@@ -29,7 +29,8 @@ namespace mpm {
 // (the compiler caps registers at 65536 / (256 x this)).  The transfer kernels
 // are latency-bound, so occupancy is traded against spills: the 3D forward
 // kernel is held to 64 registers, and the adjoint kernel is compiled for 2
-// (<= 128 registers) and 3 (<= 80) blocks, chosen per launch (Params::adj_blocks).
+// (<= 128 registers), 3 (<= 80) and, in 2D, 4 (<= 64) blocks, chosen per
+// launch (Params::adj_blocks; 4 acts as 3 in 3D).
 constexpr int kMinBlocksForward3 = 4;
 // 2D: at most 48 registers (40 warps per SM, no spills); the 2D batch's
 // forward launch went from 83 to 79 us, the single 2D locomotion body is
@@ -886,7 +887,10 @@ static cudaError_t adjoint_d(bool p2gt, bool g2pt, const Params& P, const StepAr
     const size_t sm_p2gt = warps * warp_slots<D, false>() * sizeof(float4);
     if (p2gt && g2pt) {
         if (ext) return go(k_adjoint<D, true, true, FUSE, FUSE_V, 2, true>, sm_g2pt);
-        if (P.adj_blocks == 3)
+        if constexpr (D == 2) {
+            if (P.adj_blocks == 4) return go(k_adjoint<D, true, true, FUSE, FUSE_V, 4, false>, sm_g2pt);
+        }
+        if (P.adj_blocks >= 3)
             return go(k_adjoint<D, true, true, FUSE, FUSE_V, 3, false>, sm_g2pt);
         return go(k_adjoint<D, true, true, FUSE, FUSE_V, 2, false>, sm_g2pt);
     }
