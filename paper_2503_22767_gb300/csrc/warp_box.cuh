@@ -127,13 +127,18 @@ __device__ __forceinline__ void stage_box(const WarpBox<D>& b, int res, float4* 
 // node; issued one per lane, their float4 atomics reach L2 as separate
 // same-address updates.  Here the lanes of one base node (found with one
 // __match_any_sync) sum their contributions in shared memory first, slab by
-// slab (the 9 nodes of one first-axis offset in 3D, the whole stencil in 2D):
-// every lane writes its 9 node values, then the j-th lane of a group of g sums
-// nodes j, j + g, ... over the group (in lane order, so the sum is
-// deterministic) and issues one atomic per node.  A group of one issues
-// exactly the per-lane atomics.
+// slab of kAggSlab stencil nodes: every lane writes its node values, then the
+// j-th lane of a group of g sums nodes j, j + g, ... of the slab over the
+// group (in lane order) and issues one atomic per node.  A group of one
+// issues exactly the per-lane atomics.
 // ---------------------------------------------------------------------------
-constexpr int kAggSlots = 9 * 32;  // float4 per warp: 9 nodes x 32 lanes
+// Nodes per slab: 8, so that a group of 8 lanes (8 particles per cell in 3D)
+// sums one node per lane and slab (27 = 8 + 8 + 8 + 3).  A lane's slots are 9
+// float4 apart (144 bytes, 36 banks): the 8 lanes of one quarter-warp store
+// then hit disjoint banks, where a 128-byte stride would put all on the same 4.
+constexpr int kAggSlab = 8;
+constexpr int kAggStride = 9;
+constexpr int kAggSlots = kAggStride * 32;  // float4 per warp
 
 // 3D only: with 4 particles per cell in 2D the exchange cost more than the
 // atomics it saved on every 2D workload measured (2D locomotion 15.8 -> 17.4
@@ -166,26 +171,29 @@ __device__ __forceinline__ void scatter_aggregated(int nb, int inst, bool active
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int g = __popc(peers);
     const int j = __popc(peers & ((1u << lane) - 1u));
-    float4* mine = sm + lane * 9;
-    constexpr int kSlabs = D == 3 ? 3 : 1;
+    float4* mine = sm + lane * kAggStride;
+    constexpr int kNodes = D == 3 ? 27 : 9;
 #pragma unroll
-    for (int o0 = 0; o0 < kSlabs; ++o0) {
+    for (int k0 = 0; k0 < kNodes; k0 += kAggSlab) {
+        const int nk = kNodes - k0 < kAggSlab ? kNodes - k0 : kAggSlab;  // nodes in this slab
         __syncwarp();  // the slots' earlier readers are done
 #pragma unroll
-        for (int n = 0; n < 9; ++n) mine[n] = value(o0 * 9 + n);
+        for (int n = 0; n < kAggSlab; ++n)
+            if (n < nk) mine[n] = value(k0 + n);
         __syncwarp();
         if (active) {
-            const int row = D == 3 ? nb + o0 * res * res : nb;
-            for (int n = j; n < 9; n += g) {
+            for (int n = j; n < nk; n += g) {
                 float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 for (unsigned q = peers; q; q &= q - 1u) {
-                    const float4 c = sm[(__ffs(q) - 1) * 9 + n];
+                    const float4 c = sm[(__ffs(q) - 1) * kAggStride + n];
                     acc.x += c.x;
                     acc.y += c.y;
                     acc.z += c.z;
                     acc.w += c.w;
                 }
-                atomicAdd(grid + row + (n / 3) * res + n % 3, acc);
+                const int k = k0 + n;
+                const int off = D == 3 ? ((k / 9) * res + (k / 3) % 3) * res + k % 3 : (k / 3) * res + k % 3;
+                atomicAdd(grid + nb + off, acc);
             }
         }
     }

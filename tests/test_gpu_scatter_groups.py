@@ -3,8 +3,8 @@ share a base node in shared memory before one atomic per node (P2G in the
 forward kernel, G2P^T in the adjoint kernel).  These cases drive that grouping
 through its edge cases, against the FP64 oracle:
 
-- 27 particles per cell: groups larger than the 9-node slab, so some lanes of
-  a group sum no node at all;
+- 27 particles per cell: groups larger than a slab of stencil nodes, so some
+  lanes of a group sum no node at all;
 - particle counts that leave the last warp partly empty;
 - massless particles (phi = 0) inside groups;
 - one sort for the whole horizon while the body translates by about a cell:
@@ -52,7 +52,9 @@ def case(key):
                       phi_lo=0.3, v_scale=0.05, field_scale=0.2, mag_scale=1.0)
         return w
     if key == "massless":  # 8 per cell, 360 particles, a third of them with phi = 0
-        w = W.tiny_3d(seed=22, n_steps=12, res=16, per_axis=2, cells=(5, 3, 3), lift=5, bound=2, loss_kind=1,
+        # (the position loss: under the locomotion loss over 12 substeps dL/dB~_r is
+        # ~1e-7 of dL/dphi, below what float32 resolves)
+        w = W.tiny_3d(seed=22, n_steps=12, res=16, per_axis=2, cells=(5, 3, 3), lift=5, bound=2, loss_kind=0,
                       phi_lo=0.3, v_scale=0.05, field_scale=0.2, mag_scale=1.0)
         phi = np.array(w.phi, np.float64)
         phi[np.random.default_rng(5).random(phi.size) < 1.0 / 3.0] = 0.0
