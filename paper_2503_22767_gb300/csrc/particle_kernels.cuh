@@ -19,6 +19,8 @@
 // compile in parallel.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "particle_io.cuh"
 #include "warp_box.cuh"
@@ -45,7 +47,8 @@ inline int particle_blocks(long long n, int block) { return (int)((n + block - 1
 // EXT: P.ext is set (solid boxes or a non-uniform field); without it the
 // kernel carries no code for the field gradient.
 template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT>
-__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksForward2) k_forward(Params P, StepArgs a) {
+__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksForward2)
+    k_forward(Params P, StepArgs a) {
     using L = Layout<D>;
     // Early loads: with the grid operation in its own kernel, this kernel's
     // predecessor is that grid kernel, which writes none of the particle
@@ -120,40 +123,47 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
             float hv[D], hv2[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) hv[i] = hv2[i] = 0.0f;
+            // the node loop, compiled once with the warp box and once without, so a
+            // warp runs a branch-free copy (and the instruction cache holds one)
+            auto node_loop = [&](auto box_c) {
+                constexpr bool kBox = decltype(box_c)::value;
 #pragma unroll
-            for (int k = 0; k < stencil_size<D>(); ++k) {
-                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
-                const int ol = stencil_offset<D>(k, D - 1);
-                float gv[D];
-                if (box.use) {
-                    unpack3<D>(sm[sb + box_offset<D>(k)], gv);
-                } else {
-                    NodeTerm<D> t;
-                    t.node = nb + node_offset<D>(k, P.res);
+                for (int k = 0; k < stencil_size<D>(); ++k) {
+                    const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                    const int ol = stencil_offset<D>(k, D - 1);
+                    float gv[D];
+                    if (kBox) {
+                        unpack3<D>(sm[sb + box_offset<D>(k)], gv);
+                    } else {
+                        NodeTerm<D> t;
+                        t.node = nb + node_offset<D>(k, P.res);
 #pragma unroll
-                    for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
-                    node_velocity<D, FUSE, EXT>(Vi, t, P, gv, a.n_g2p);
-                }
-                const float wl = s.w[D - 1][ol];
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    const float wv = wl * gv[i];
-                    hv[i] = ol == 0 ? wv : hv[i] + wv;
-                    if (ol == 0) hv2[i] = 0.0f;
-                    else hv2[i] = add_offset(hv2[i], ol, wv);
-                }
-                if (ol == 2) {  // the row is complete
-                    const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
+                        for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
+                        node_velocity<D, FUSE, EXT>(Vi, t, P, gv, a.n_g2p);
+                    }
+                    const float wl = s.w[D - 1][ol];
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
-                        const float hp = pw * hv[i];
-                        v[i] += hp;
-                        C[i][D - 1] += pw * hv2[i];
-                        C[i][0] = add_offset(C[i][0], o0, hp);
-                        if (D == 3) C[i][1 % D] = add_offset(C[i][1 % D], om, hp);
+                        const float wv = wl * gv[i];
+                        hv[i] = ol == 0 ? wv : hv[i] + wv;
+                        if (ol == 0) hv2[i] = 0.0f;
+                        else hv2[i] = add_offset(hv2[i], ol, wv);
+                    }
+                    if (ol == 2) {  // the row is complete
+                        const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            const float hp = pw * hv[i];
+                            v[i] += hp;
+                            C[i][D - 1] += pw * hv2[i];
+                            C[i][0] = add_offset(C[i][0], o0, hp);
+                            if (D == 3) C[i][1 % D] = add_offset(C[i][1 % D], om, hp);
+                        }
                     }
                 }
-            }
+            };
+            if (box.use) node_loop(std::true_type{});
+            else node_loop(std::false_type{});
             float Fn[D][D];
             const float c4 = 4.0f * P.inv_dx;
 #pragma unroll
@@ -457,88 +467,95 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
 #pragma unroll
                 for (int j = 0; j < D; ++j) T[i][j] = 0.0f;
             }
+            // the node loop, compiled once with the warp box and once without, so a
+            // warp runs a branch-free copy (and the instruction cache holds one)
+            auto node_loop = [&](auto box_c) {
+                constexpr bool kBox = decltype(box_c)::value;
 #pragma unroll
-            for (int k = 0; k < stencil_size<D>(); ++k) {
-                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
-                const int ol = stencil_offset<D>(k, D - 1);
-                if (ol == 0) {  // a new row along the last axis
+                for (int k = 0; k < stencil_size<D>(); ++k) {
+                    const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                    const int ol = stencil_offset<D>(k, D - 1);
+                    if (ol == 0) {  // a new row along the last axis
 #pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        float ug = add_offset(u[i], o0, dA[0][i]);
-                        if (D == 3) ug = add_offset(ug, om, dA[1 % D][i]);
-                        Ug[i] = ug;
-                        hv[i] = hv2[i] = 0.0f;
+                        for (int i = 0; i < D; ++i) {
+                            float ug = add_offset(u[i], o0, dA[0][i]);
+                            if (D == 3) ug = add_offset(ug, om, dA[1 % D][i]);
+                            Ug[i] = ug;
+                            hv[i] = hv2[i] = 0.0f;
+                        }
+                        hm = ha = hb = 0.0f;
                     }
-                    hm = ha = hb = 0.0f;
-                }
-                float4 g;
-                float mvb[D];
-                if (box.use) {
-                    g = sm[sb + box_offset<D>(k)];
-                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
-                } else if (FUSE) {
-                    const int node = nb + node_offset<D>(k, P.res);
-                    g = __ldg(gi + node);
-                    // grid adjoint (reverse of Eq. 16-18) of this node, on the fly
-                    int c[D];
+                    float4 g;
+                    float mvb[D];
+                    if (kBox) {
+                        g = sm[sb + box_offset<D>(k)];
+                        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
+                    } else if (FUSE) {
+                        const int node = nb + node_offset<D>(k, P.res);
+                        g = __ldg(gi + node);
+                        // grid adjoint (reverse of Eq. 16-18) of this node, on the fly
+                        int c[D];
 #pragma unroll
-                    for (int e = 0; e < D; ++e) c[e] = s.base[e] + stencil_offset<D>(k, e);
-                    float mv[D], vbv[D], mbv;
-                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                    unpack3<D>(__ldg(vbi + node), vbv);
-                    grid_velocity_adjoint<D, EXT>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
-                    g.x = mbv;
-                } else {
-                    g = __ldg(gi + nb + node_offset<D>(k, P.res));
-                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
-                }
-                const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
-                float inner = g.x * mp;
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    inner += mvb[i] * add_offset(Ug[i], ol, dA[D - 1][i]);
-                    const float wm = wl * mvb[i];
-                    hv[i] += wm;
-                    if (ol == 1) hv2[i] += wm;
-                    else if (ol == 2) hv2[i] += 2.0f * wm;
-                }
-                hm += wl * g.x;
-                ha += wl * inner;
-                hb += dwl * inner;
-                if (ol == 2) {  // the row is complete: weight it by the other axes
-                    const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
-                    float pw = w0;
-                    if (D == 2) {
-                        xg[0] += dw0 * ha;
-                        xg[D - 1] += w0 * hb;
+                        for (int e = 0; e < D; ++e) c[e] = s.base[e] + stencil_offset<D>(k, e);
+                        float mv[D], vbv[D], mbv;
+                        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                        unpack3<D>(__ldg(vbi + node), vbv);
+                        grid_velocity_adjoint<D, EXT>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
+                        g.x = mbv;
                     } else {
-                        const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
-                        if (om == 0) la = lb = lc = 0.0f;
-                        la += w1 * ha;
-                        lb += dw1 * ha;
-                        lc += w1 * hb;
-                        if (om == 2) {
-                            xg[0] += dw0 * la;
-                            xg[1 % D] += w0 * lb;
-                            xg[D - 1] += w0 * lc;
-                        }
-                        pw = w0 * w1;
+                        g = __ldg(gi + nb + node_offset<D>(k, P.res));
+                        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
                     }
-                    mbs += pw * hm;
+                    const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
+                    float inner = g.x * mp;
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
-                        const float hp = pw * hv[i];
-                        S0[i] += hp;
-                        T[i][D - 1] += pw * hv2[i];
-                        if (o0 == 1) T[i][0] += hp;
-                        else if (o0 == 2) T[i][0] += 2.0f * hp;
-                        if (D == 3) {
-                            if (om == 1) T[i][1 % D] += hp;
-                            else if (om == 2) T[i][1 % D] += 2.0f * hp;
+                        inner += mvb[i] * add_offset(Ug[i], ol, dA[D - 1][i]);
+                        const float wm = wl * mvb[i];
+                        hv[i] += wm;
+                        if (ol == 1) hv2[i] += wm;
+                        else if (ol == 2) hv2[i] += 2.0f * wm;
+                    }
+                    hm += wl * g.x;
+                    ha += wl * inner;
+                    hb += dwl * inner;
+                    if (ol == 2) {  // the row is complete: weight it by the other axes
+                        const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
+                        float pw = w0;
+                        if (D == 2) {
+                            xg[0] += dw0 * ha;
+                            xg[D - 1] += w0 * hb;
+                        } else {
+                            const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
+                            if (om == 0) la = lb = lc = 0.0f;
+                            la += w1 * ha;
+                            lb += dw1 * ha;
+                            lc += w1 * hb;
+                            if (om == 2) {
+                                xg[0] += dw0 * la;
+                                xg[1 % D] += w0 * lb;
+                                xg[D - 1] += w0 * lc;
+                            }
+                            pw = w0 * w1;
+                        }
+                        mbs += pw * hm;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            const float hp = pw * hv[i];
+                            S0[i] += hp;
+                            T[i][D - 1] += pw * hv2[i];
+                            if (o0 == 1) T[i][0] += hp;
+                            else if (o0 == 2) T[i][0] += 2.0f * hp;
+                            if (D == 3) {
+                                if (om == 1) T[i][1 % D] += hp;
+                                else if (om == 2) T[i][1 % D] += 2.0f * hp;
+                            }
                         }
                     }
                 }
-            }
+            };
+            if (box.use) node_loop(std::true_type{});
+            else node_loop(std::false_type{});
             // The node loop needs none of C, E, the stress (all used for A
             // before it) and Fbar of state n: they are read again, and the
             // stress recomputed, here, so their registers are free during the
@@ -725,69 +742,76 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
             float xg[D], vs[D], Sg[D], hv[D], pw = 0.0f, ha = 0.0f, hb = 0.0f, la = 0.0f, lb = 0.0f, lc = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; ++i) xg[i] = vs[i] = Sg[i] = hv[i] = 0.0f;
+            // the node loop, compiled once with the warp box and once without, so a
+            // warp runs a branch-free copy (and the instruction cache holds one)
+            auto node_loop = [&](auto box_c) {
+                constexpr bool kBox = decltype(box_c)::value;
 #pragma unroll
-            for (int k = 0; k < stencil_size<D>(); ++k) {
-                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
-                const int ol = stencil_offset<D>(k, D - 1);
-                if (ol == 0) {  // a new row along the last axis
+                for (int k = 0; k < stencil_size<D>(); ++k) {
+                    const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                    const int ol = stencil_offset<D>(k, D - 1);
+                    if (ol == 0) {  // a new row along the last axis
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            float sg = add_offset(q[i], o0, dC[0][i]);
+                            if (D == 3) sg = add_offset(sg, om, dC[1 % D][i]);
+                            Sg[i] = sg;
+                            hv[i] = 0.0f;
+                        }
+                        ha = hb = 0.0f;
+                        pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
+                    }
+                    const int node = nb + node_offset<D>(k, P.res);
+                    float gv[D];
+                    if (kBox) {
+                        unpack3<D>(sm[sb + box_offset<D>(k)], gv);
+                    } else {
+                        NodeTerm<D> t;
+                        t.node = node;
+#pragma unroll
+                        for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
+                        node_velocity<D, FUSE_V, EXT>(Vi, t, P, gv, a.n_p2g - 1);
+                    }
+                    const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
+                    float sv[D], dot = 0.0f;
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
-                        float sg = add_offset(q[i], o0, dC[0][i]);
-                        if (D == 3) sg = add_offset(sg, om, dC[1 % D][i]);
-                        Sg[i] = sg;
-                        hv[i] = 0.0f;
+                        sv[i] = add_offset(Sg[i], ol, dC[D - 1][i]);
+                        dot += gv[i] * sv[i];  // V . (vt + kappa Ct dpos)
+                        hv[i] += wl * gv[i];
                     }
-                    ha = hb = 0.0f;
-                    pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
-                }
-                const int node = nb + node_offset<D>(k, P.res);
-                float gv[D];
-                if (box.use) {
-                    unpack3<D>(sm[sb + box_offset<D>(k)], gv);
-                } else {
-                    NodeTerm<D> t;
-                    t.node = node;
+                    ha += wl * dot;
+                    hb += dwl * dot;
+                    if constexpr (!AGG) {
+                        const float w = pw * wl;
 #pragma unroll
-                    for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
-                    node_velocity<D, FUSE_V, EXT>(Vi, t, P, gv, a.n_p2g - 1);
-                }
-                const float wl = s.w[D - 1][ol], dwl = s.dw[D - 1][ol];
-                float sv[D], dot = 0.0f;
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    sv[i] = add_offset(Sg[i], ol, dC[D - 1][i]);
-                    dot += gv[i] * sv[i];  // V . (vt + kappa Ct dpos)
-                    hv[i] += wl * gv[i];
-                }
-                ha += wl * dot;
-                hb += dwl * dot;
-                if constexpr (!AGG) {
-                    const float w = pw * wl;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) sv[i] *= w;
-                    atomicAdd(Vbi + node, make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f));
-                }
-                if (ol == 2) {  // the row is complete: weight it by the other axes
-                    const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
-                    if (D == 2) {
-                        xg[0] += dw0 * ha;
-                        xg[D - 1] += w0 * hb;
-                    } else {
-                        const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
-                        if (om == 0) la = lb = lc = 0.0f;
-                        la += w1 * ha;
-                        lb += dw1 * ha;
-                        lc += w1 * hb;
-                        if (om == 2) {
-                            xg[0] += dw0 * la;
-                            xg[1 % D] += w0 * lb;
-                            xg[D - 1] += w0 * lc;
+                        for (int i = 0; i < D; ++i) sv[i] *= w;
+                        atomicAdd(Vbi + node, make_float4(sv[0], sv[1 % D], D == 3 ? sv[2 % D] : 0.0f, 0.0f));
+                    }
+                    if (ol == 2) {  // the row is complete: weight it by the other axes
+                        const float w0 = s.w[0][o0], dw0 = s.dw[0][o0];
+                        if (D == 2) {
+                            xg[0] += dw0 * ha;
+                            xg[D - 1] += w0 * hb;
+                        } else {
+                            const float w1 = s.w[1 % D][om], dw1 = s.dw[1 % D][om];
+                            if (om == 0) la = lb = lc = 0.0f;
+                            la += w1 * ha;
+                            lb += dw1 * ha;
+                            lc += w1 * hb;
+                            if (om == 2) {
+                                xg[0] += dw0 * la;
+                                xg[1 % D] += w0 * lb;
+                                xg[D - 1] += w0 * lc;
+                            }
                         }
-                    }
 #pragma unroll
-                    for (int i = 0; i < D; ++i) vs[i] += pw * hv[i];
+                        for (int i = 0; i < D; ++i) vs[i] += pw * hv[i];
+                    }
                 }
-            }
+            };
+            if (box.use) node_loop(std::true_type{});
+            else node_loop(std::false_type{});
             // kappa Ct^T vs = (dC vs) / dx
 #pragma unroll
             for (int c = 0; c < D; ++c) {
