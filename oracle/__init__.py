@@ -45,17 +45,41 @@ class Params(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, no -march, FMA contraction off)."""
+    """Compile the oracle shared library (gcc, no -march, FMA contraction off),
+    with OpenMP when the compiler has it (the threaded passes give the serial
+    results bit for bit; without OpenMP the library runs on one thread)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(base + ["-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's passes (1 = serial).  Results are
+    identical for every thread count.  Returns the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+class threads:
+    """Context manager: run the oracle on ``n`` host threads (default: all
+    cores of this host), then go back to one."""
+
+    def __init__(self, n: int | None = None):
+        self.n = n if n else (os.cpu_count() or 1)
+
+    def __enter__(self):
+        self.used = set_threads(self.n)
+        return self.used
+
+    def __exit__(self, *exc):
+        set_threads(1)
 
 
 def lib():
@@ -96,6 +120,8 @@ def lib():
             _lib.orc_cell_keys.restype = None
             _lib.orc_sort_perm.argtypes = [ip, ctypes.c_int, ip]
             _lib.orc_sort_perm.restype = ctypes.c_int
+            _lib.orc_set_threads.argtypes = [ctypes.c_int]
+            _lib.orc_set_threads.restype = ctypes.c_int
         return _lib
 
 

@@ -7,8 +7,8 @@
  * leg of the benchmark do.  It shares no code, header, table or helper with
  * the CUDA kernels.
  *
- * Everything is double precision and serial, in the order the paper states
- * the algorithm (arxiv 2503.22767):
+ * Everything is double precision, in the order the paper states the
+ * algorithm (arxiv 2503.22767):
  *   - Piola stress of the ideal hard-magnetic neo-Hookean solid: Eq. 7
  *     (energy Eq. 4-6), SIMP interpolation of energy and mass: Eq. 31-33.
  *   - P2G with the quadratic B-spline (MLS-MPM, Section 2.2 step 1): Eq. 14-15.
@@ -54,6 +54,17 @@
  *       its negative x-derivative f = (phi^q V / mu0) G^T (F B~_r) enters the
  *       particle's momentum in P2G.
  *
+ * Threads (orc_set_threads; default 1): with OpenMP the particle loops run
+ * on several host cores without changing a single result bit.  A gather
+ * (G2P, P2G^T) or a per-node loop (grid operation and its reverse) writes
+ * nothing another particle or node writes.  A scatter (P2G, G2P^T) splits
+ * the node columns along axis 0 into slabs, one per thread: each thread
+ * visits the particles in index order and adds only to the nodes of its own
+ * slab, so every node receives its terms in the serial order.  Sums over
+ * all particles (dL/dB_a, dL/dG, momentum, loss) stay serial loops over
+ * per-particle terms.  Hence the threaded oracle equals the serial one bit
+ * for bit, which the tests check.
+ *
  * Layout: per particle x[3], v[3], C[9], F[9] (row-major 3x3; in 2D only the
  * leading 2 components / 2x2 block are used and the rest stay zero).
  * Instances are independent simulations concatenated in particle order, each
@@ -62,6 +73,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -97,6 +111,25 @@ typedef struct {
     const double* fgrad;
     double* g_fgrad;
 } orc_params;
+
+/* ------------------------------------------------------------------ */
+/* host threads (see the header: results do not depend on them)         */
+/* ------------------------------------------------------------------ */
+
+#define ORC_MAX_THREADS 256
+static int g_threads = 1;
+
+/* Use n host threads (clamped to [1, 256]; 1 without OpenMP).  Returns the
+ * number in effect. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : (n > ORC_MAX_THREADS ? ORC_MAX_THREADS : n);
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
 
 /* ------------------------------------------------------------------ */
 /* small dense helpers (3x3 storage, d x d used)                       */
@@ -368,47 +401,118 @@ static void magnetic_force(const orc_params* P, const double* Gn, const double* 
         for (int i = 0; i < d; ++i) f[j] += c * Gn[3 * i + j] * FB[i];
 }
 
-/* P2G (Eq. 14-15 with reading R1) for the particles [p0, p1) into one grid;
- * Gn is the field gradient of this instance and substep, or NULL. */
-static int p2g(const orc_params* P, int p0, int p1, const state_t* s, const double* phi,
-               const double* mag, const double* Ba, const double* Gn, double* gm, double* gmv) {
+/* Axis-0 offset of stencil entry k (the order of stencil_node). */
+static int offset0(int d, int k) { return d == 2 ? k / 3 : k / 9; }
+
+/* Split the node columns [0, res) along axis 0 into T slabs of about equal
+ * scatter work (a particle with base column b adds to columns b .. b+2);
+ * slab t is [lo[t], lo[t+1]).  b0[p] is the base column of particle p. */
+static void make_slabs(const orc_params* P, const int* b0, int p0, int p1, int T, int* lo) {
+    int res = P->res;
+    double* work = (double*)calloc((size_t)res + 1, sizeof(double));
+    double total = 0.0;
+    if (work) {
+        for (int p = p0; p < p1; ++p)
+            for (int o = 0; o < 3; ++o) work[b0[p] + o] += 1.0;
+        for (int c = 0; c < res; ++c) total += work[c];
+    }
+    lo[0] = 0;
+    double acc = 0.0;
+    int t = 1;
+    for (int c = 0; c < res && t < T; ++c) {
+        acc += work ? work[c] : 0.0;
+        while (t < T && acc >= total * t / T) lo[t++] = c + 1;
+    }
+    while (t < T) lo[t++] = res;
+    lo[T] = res;
+    free(work);
+}
+
+/* Base column (axis 0) and stencil check of particles [p0, p1): returns 1
+ * when every stencil lies inside the grid. */
+static int base_columns(const orc_params* P, int p0, int p1, const double* x, int* b0) {
+    int ok = 1;
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(&& : ok)
+    for (int p = p0; p < p1; ++p) {
+        stencil_t S;
+        int good = make_stencil(P, x + 3 * p, &S);
+        ok = ok && good;
+        b0[p] = good ? S.base[0] : 0;
+    }
+    return ok;
+}
+
+/* P2G (Eq. 14-15 with reading R1) of particle p into the nodes whose axis-0
+ * index lies in [c_lo, c_hi).  Returns 0 when J <= 0. */
+static int p2g_particle(const orc_params* P, int p, const state_t* s, const double* phi,
+                        const double* mag, const double* Ba, const double* Gn, double* gm,
+                        double* gmv, int c_lo, int c_hi) {
     int d = P->dim;
     double G, K;
     lame(P, &G, &K);
     double dx = 1.0 / P->res;
     double kappa = 4.0 / (dx * dx);
-    int status = ORC_OK;
-    for (int p = p0; p < p1; ++p) {
-        stencil_t S;
-        if (!make_stencil(P, s->x + 3 * p, &S)) return ORC_ERR_DOMAIN;
-        double Pst[9], Bp[3], fp[3];
-        field_at(d, Ba, Gn, s->x + 3 * p, Bp);
-        double J = orc_stress(d, G, K, s->F + 9 * p, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Bp, Pst);
-        if (!(J > 0.0)) status = ORC_ERR_NUMERIC;
-        double mp = particle_mass(P, phi[p]);
-        const double* F = s->F + 9 * p;
-        magnetic_force(P, Gn, F, mag + 3 * p, phi[p], fp);
-        const double* C = s->C + 9 * p;
-        double A[9] = {0};
-        for (int i = 0; i < d; ++i)
-            for (int j = 0; j < d; ++j) {
-                double PFt = 0.0;
-                for (int k = 0; k < d; ++k) PFt += Pst[i * 3 + k] * F[j * 3 + k];
-                A[i * 3 + j] = mp * C[i * 3 + j] - P->dt * kappa * P->p_vol * PFt;
-            }
-        for (int k = 0; k < n_offsets(d); ++k) {
-            int node;
-            double w, gw[3], dpos[3];
-            stencil_node(P, &S, k, &node, &w, gw, dpos);
-            gm[node] += w * mp;
-            for (int i = 0; i < d; ++i) {
-                double Ad = 0.0;
-                for (int j = 0; j < d; ++j) Ad += A[i * 3 + j] * dpos[j];
-                gmv[3 * node + i] += w * (mp * s->v[3 * p + i] + P->dt * fp[i] + Ad);
-            }
+    stencil_t S;
+    make_stencil(P, s->x + 3 * p, &S);
+    double Pst[9], Bp[3], fp[3];
+    field_at(d, Ba, Gn, s->x + 3 * p, Bp);
+    double J = orc_stress(d, G, K, s->F + 9 * p, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Bp, Pst);
+    double mp = particle_mass(P, phi[p]);
+    const double* F = s->F + 9 * p;
+    magnetic_force(P, Gn, F, mag + 3 * p, phi[p], fp);
+    const double* C = s->C + 9 * p;
+    double A[9] = {0};
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double PFt = 0.0;
+            for (int k = 0; k < d; ++k) PFt += Pst[i * 3 + k] * F[j * 3 + k];
+            A[i * 3 + j] = mp * C[i * 3 + j] - P->dt * kappa * P->p_vol * PFt;
+        }
+    for (int k = 0; k < n_offsets(d); ++k) {
+        int c0 = S.base[0] + offset0(d, k);
+        if (c0 < c_lo || c0 >= c_hi) continue;
+        int node;
+        double w, gw[3], dpos[3];
+        stencil_node(P, &S, k, &node, &w, gw, dpos);
+        gm[node] += w * mp;
+        for (int i = 0; i < d; ++i) {
+            double Ad = 0.0;
+            for (int j = 0; j < d; ++j) Ad += A[i * 3 + j] * dpos[j];
+            gmv[3 * node + i] += w * (mp * s->v[3 * p + i] + P->dt * fp[i] + Ad);
         }
     }
-    return status;
+    return J > 0.0;
+}
+
+/* P2G (Eq. 14-15 with reading R1) for the particles [p0, p1) into one grid;
+ * Gn is the field gradient of this instance and substep, or NULL.  Each
+ * thread scatters into its own slab of node columns (see the header). */
+static int p2g(const orc_params* P, int p0, int p1, const state_t* s, const double* phi,
+               const double* mag, const double* Ba, const double* Gn, double* gm, double* gmv) {
+    if (p1 <= p0) return ORC_OK;
+    int* b0 = (int*)malloc(sizeof(int) * (size_t)p1);
+    if (!b0) return ORC_ERR_OOM;
+    if (!base_columns(P, p0, p1, s->x, b0)) {
+        free(b0);
+        return ORC_ERR_DOMAIN;
+    }
+    int T = g_threads;
+    int lo[ORC_MAX_THREADS + 1];
+    make_slabs(P, b0, p0, p1, T, lo);
+    int good = 1;
+#pragma omp parallel num_threads(T) reduction(&& : good)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        for (int p = p0; p < p1; ++p) {
+            if (b0[p] + 2 < lo[t] || b0[p] >= lo[t + 1]) continue;
+            good = p2g_particle(P, p, s, phi, mag, Ba, Gn, gm, gmv, lo[t], lo[t + 1]) && good;
+        }
+    }
+    free(b0);
+    return good ? ORC_OK : ORC_ERR_NUMERIC;
 }
 
 /* Boundary projection trace of one node (readings R5/R6/R18). */
@@ -517,6 +621,7 @@ static void apply_bc(const orc_params* P, const int* c, double* v, bc_trace* tr,
 static void grid_update(const orc_params* P, const double* gm, const double* gmv, double* gv, int step) {
     long G = grid_size(P);
     int d = P->dim;
+#pragma omp parallel for schedule(static) num_threads(g_threads)
     for (long n = 0; n < G; ++n) {
         for (int i = 0; i < 3; ++i) gv[3 * n + i] = 0.0;
         if (!(gm[n] > 0.0)) continue; /* reading R7 */
@@ -538,10 +643,14 @@ static int g2p(const orc_params* P, int p0, int p1, const state_t* si, const dou
     int d = P->dim;
     double dx = 1.0 / P->res;
     double kappa = 4.0 / (dx * dx);
-    int status = ORC_OK;
+    int inside = 1, positive = 1;
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(&& : inside, positive)
     for (int p = p0; p < p1; ++p) {
         stencil_t S;
-        if (!make_stencil(P, si->x + 3 * p, &S)) return ORC_ERR_DOMAIN;
+        if (!make_stencil(P, si->x + 3 * p, &S)) {
+            inside = 0;
+            continue;
+        }
         double vp[3] = {0, 0, 0}, Cp[9] = {0};
         for (int k = 0; k < n_offsets(d); ++k) {
             int node;
@@ -566,9 +675,10 @@ static int g2p(const orc_params* P, int p0, int p1, const state_t* si, const dou
         }
         memcpy(so->C + 9 * p, Cp, sizeof Cp);
         memcpy(so->F + 9 * p, Fn, sizeof Fn);
-        if (!(det_d(d, Fn) > 0.0)) status = ORC_ERR_NUMERIC;
+        if (!(det_d(d, Fn) > 0.0)) positive = 0;
     }
-    return status;
+    if (!inside) return ORC_ERR_DOMAIN;
+    return positive ? ORC_OK : ORC_ERR_NUMERIC;
 }
 
 /* ------------------------------------------------------------------ */
@@ -872,6 +982,82 @@ typedef struct {
     double* F;  /* [9N] */
 } adj_t;
 
+/* Reverse of G2P (Eq. 19-22) for particle p: consumes the adjoint ab of
+ * the state after the substep, writes the particle's partial adjoint into an
+ * (when `owner`) and adds its terms to Vbar at the nodes whose axis-0 index
+ * lies in [c_lo, c_hi). */
+static void g2p_adjoint_particle(const orc_params* P, int p, const state_t* sn, const double* gv,
+                                 const adj_t* ab, adj_t* an, double* Vbar, int c_lo, int c_hi,
+                                 int owner) {
+    int d = P->dim;
+    double dx = 1.0 / P->res;
+    double kappa = 4.0 / (dx * dx);
+    stencil_t Sp;
+    make_stencil(P, sn->x + 3 * p, &Sp);
+    /* recompute v', C' */
+    double vp[3] = {0, 0, 0}, Cp[9] = {0};
+    for (int k = 0; k < n_offsets(d); ++k) {
+        int node;
+        double w, gw[3], dpos[3];
+        stencil_node(P, &Sp, k, &node, &w, gw, dpos);
+        for (int i = 0; i < d; ++i) {
+            vp[i] += w * gv[3 * node + i];
+            for (int j = 0; j < d; ++j) Cp[i * 3 + j] += kappa * w * gv[3 * node + i] * dpos[j];
+        }
+    }
+    const double* F = sn->F + 9 * p;
+    const double* xb1 = ab->x + 3 * p;
+    const double* vb1 = ab->v + 3 * p;
+    const double* Cb1 = ab->C + 9 * p;
+    const double* Fb1 = ab->F + 9 * p;
+    /* x' = x + dt v' ; F' = (I + dt C') F */
+    double vtot[3] = {0, 0, 0}, Ctot[9] = {0};
+    for (int i = 0; i < d; ++i) vtot[i] = vb1[i] + P->dt * xb1[i];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double acc = 0.0; /* (Fbar' F^T)_ij */
+            for (int k = 0; k < d; ++k) acc += Fb1[i * 3 + k] * F[j * 3 + k];
+            Ctot[i * 3 + j] = Cb1[i * 3 + j] + P->dt * acc;
+        }
+    double xbn[3] = {0, 0, 0}, Fbn[9] = {0};
+    for (int i = 0; i < d; ++i) xbn[i] = xb1[i];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            /* ((I + dt C')^T Fbar')_ij */
+            double acc = Fb1[i * 3 + j];
+            for (int k = 0; k < d; ++k) acc += P->dt * Cp[k * 3 + i] * Fb1[k * 3 + j];
+            Fbn[i * 3 + j] = acc;
+        }
+    for (int k = 0; k < n_offsets(d); ++k) {
+        int node;
+        double w, gw[3], dpos[3];
+        stencil_node(P, &Sp, k, &node, &w, gw, dpos);
+        const double* V = gv + 3 * node;
+        double Vdotv = 0.0, VCd = 0.0;
+        for (int i = 0; i < d; ++i) {
+            Vdotv += V[i] * vtot[i];
+            for (int j = 0; j < d; ++j) VCd += V[i] * Ctot[i * 3 + j] * dpos[j];
+        }
+        for (int c = 0; c < d; ++c) {
+            double CtV = 0.0;
+            for (int i = 0; i < d; ++i) CtV += Ctot[i * 3 + c] * V[i];
+            xbn[c] += gw[c] * (Vdotv + kappa * VCd) - kappa * w * CtV;
+        }
+        int c0 = Sp.base[0] + offset0(d, k);
+        if (c0 < c_lo || c0 >= c_hi) continue;
+        for (int i = 0; i < d; ++i) {
+            double Cd = 0.0;
+            for (int j = 0; j < d; ++j) Cd += Ctot[i * 3 + j] * dpos[j];
+            Vbar[3 * node + i] += w * (vtot[i] + kappa * Cd);
+        }
+    }
+    if (!owner) return;
+    for (int i = 0; i < 3; ++i) an->x[3 * p + i] = xbn[i];
+    for (int i = 0; i < 9; ++i) an->F[9 * p + i] = Fbn[i];
+    for (int i = 0; i < 3; ++i) an->v[3 * p + i] = 0.0;
+    for (int i = 0; i < 9; ++i) an->C[9 * p + i] = 0.0;
+}
+
 /*
  * Reverse of substep n for all instances.
  *   sn: state at the start of substep n; ab: adjoint of the state after it
@@ -906,75 +1092,44 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
         memset(Vbar, 0, sizeof(double) * 3 * Gn);
 
         /* --- reverse of G2P (Eq. 19-22) --- */
-        for (int p = p0; p < p1; ++p) {
-            stencil_t Sp;
-            make_stencil(P, sn->x + 3 * p, &Sp);
-            /* recompute v', C' */
-            double vp[3] = {0, 0, 0}, Cp[9] = {0};
-            for (int k = 0; k < n_offsets(d); ++k) {
-                int node;
-                double w, gw[3], dpos[3];
-                stencil_node(P, &Sp, k, &node, &w, gw, dpos);
-                for (int i = 0; i < d; ++i) {
-                    vp[i] += w * S->gv[3 * node + i];
-                    for (int j = 0; j < d; ++j) Cp[i * 3 + j] += kappa * w * S->gv[3 * node + i] * dpos[j];
+        {
+            int* b0 = (int*)malloc(sizeof(int) * (size_t)(p1 > 0 ? p1 : 1));
+            if (!b0) { free(Vbar); free(mbar); free(mvbar); return ORC_ERR_OOM; }
+            base_columns(P, p0, p1, sn->x, b0);
+            int T = g_threads;
+            int lo[ORC_MAX_THREADS + 1];
+            make_slabs(P, b0, p0, p1, T, lo);
+#pragma omp parallel num_threads(T)
+            {
+                int t = 0;
+#ifdef _OPENMP
+                t = omp_get_thread_num();
+#endif
+                for (int p = p0; p < p1; ++p) {
+                    if (b0[p] + 2 < lo[t] || b0[p] >= lo[t + 1]) continue;
+                    /* the thread whose slab holds the base column writes the
+                     * particle's own adjoint; every thread adds to its nodes */
+                    int owner = b0[p] >= lo[t] && b0[p] < lo[t + 1];
+                    g2p_adjoint_particle(P, p, sn, S->gv, ab, an, Vbar, lo[t], lo[t + 1], owner);
                 }
             }
-            const double* F = sn->F + 9 * p;
-            const double* xb1 = ab->x + 3 * p;
-            const double* vb1 = ab->v + 3 * p;
-            const double* Cb1 = ab->C + 9 * p;
-            const double* Fb1 = ab->F + 9 * p;
-            /* x' = x + dt v' ; F' = (I + dt C') F */
-            double vtot[3] = {0, 0, 0}, Ctot[9] = {0};
-            for (int i = 0; i < d; ++i) vtot[i] = vb1[i] + P->dt * xb1[i];
-            for (int i = 0; i < d; ++i)
-                for (int j = 0; j < d; ++j) {
-                    double acc = 0.0; /* (Fbar' F^T)_ij */
-                    for (int k = 0; k < d; ++k) acc += Fb1[i * 3 + k] * F[j * 3 + k];
-                    Ctot[i * 3 + j] = Cb1[i * 3 + j] + P->dt * acc;
-                }
-            double* xbn = an->x + 3 * p;
-            double* Fbn = an->F + 9 * p;
-            for (int i = 0; i < d; ++i) xbn[i] = xb1[i];
-            for (int i = 0; i < d; ++i)
-                for (int j = 0; j < d; ++j) {
-                    /* ((I + dt C')^T Fbar')_ij */
-                    double acc = Fb1[i * 3 + j];
-                    for (int k = 0; k < d; ++k) acc += P->dt * Cp[k * 3 + i] * Fb1[k * 3 + j];
-                    Fbn[i * 3 + j] = acc;
-                }
-            for (int k = 0; k < n_offsets(d); ++k) {
-                int node;
-                double w, gw[3], dpos[3];
-                stencil_node(P, &Sp, k, &node, &w, gw, dpos);
-                const double* V = S->gv + 3 * node;
-                double Vdotv = 0.0, VCd = 0.0;
-                for (int i = 0; i < d; ++i) {
-                    Vdotv += V[i] * vtot[i];
-                    for (int j = 0; j < d; ++j) VCd += V[i] * Ctot[i * 3 + j] * dpos[j];
-                }
-                for (int c = 0; c < d; ++c) {
-                    double CtV = 0.0;
-                    for (int i = 0; i < d; ++i) CtV += Ctot[i * 3 + c] * V[i];
-                    xbn[c] += gw[c] * (Vdotv + kappa * VCd) - kappa * w * CtV;
-                }
-                for (int i = 0; i < d; ++i) {
-                    double Cd = 0.0;
-                    for (int j = 0; j < d; ++j) Cd += Ctot[i * 3 + j] * dpos[j];
-                    Vbar[3 * node + i] += w * (vtot[i] + kappa * Cd);
-                }
-            }
-            for (int i = 0; i < 3; ++i) an->v[3 * p + i] = 0.0;
-            for (int i = 0; i < 9; ++i) an->C[9 * p + i] = 0.0;
+            free(b0);
         }
 
         /* --- reverse of the grid operation (Eq. 16-18) --- */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
         for (long nd = 0; nd < Gn; ++nd)
             grid_update_adjoint_node(P, nd, S->gm[nd], S->gmv + 3 * nd, Vbar + 3 * nd, mbar + nd,
                                      mvbar + 3 * nd, n);
 
-        /* --- reverse of P2G (Eq. 14-15, stress Eq. 7, SIMP Eq. 31-33) --- */
+        /* --- reverse of P2G (Eq. 14-15, stress Eq. 7, SIMP Eq. 31-33) ---
+         * per-particle terms of dL/dB_a and dL/dG are kept and summed in
+         * particle order after the loop */
+        size_t np_ = (size_t)(p1 - p0);
+        double* tBa = (double*)calloc(3 * np_ + 1, sizeof(double));
+        double* tG = gGf ? (double*)calloc(18 * np_ + 1, sizeof(double)) : NULL;
+        if (!tBa || (gGf && !tG)) { free(tBa); free(tG); free(Vbar); free(mbar); free(mvbar); return ORC_ERR_OOM; }
+#pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int p = p0; p < p1; ++p) {
             stencil_t Sp;
             make_stencil(P, sn->x + 3 * p, &Sp);
@@ -1052,11 +1207,13 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
             orc_stress_adjoint(d, G, K, F, phi[p], P->simp_q, P->simp_eps, mag + 3 * p, Bp, Pbar, Fbn,
                                &phib, g_mag + 3 * p, Bpb);
             /* B_p = B_a + G (x_p - x_c): dL/dB_a, dL/dG and the x_p term */
-            for (int i = 0; i < d; ++i) gBa[i] += Bpb[i];
+            double* tBap = tBa + 3 * (size_t)(p - p0);
+            double* tGp = tG ? tG + 18 * (size_t)(p - p0) : NULL;
+            for (int i = 0; i < d; ++i) tBap[i] = Bpb[i];
             if (Gf) {
                 for (int i = 0; i < d; ++i)
                     for (int j = 0; j < d; ++j) {
-                        if (gGf) gGf[3 * i + j] += Bpb[i] * (sn->x[3 * p + j] - 0.5);
+                        if (tGp) tGp[3 * i + j] = Bpb[i] * (sn->x[3 * p + j] - 0.5);
                         xbn[j] += Gf[3 * i + j] * Bpb[i];
                     }
                 /* f = c G^T (F B~_r), c = phi^q V / mu0 */
@@ -1073,14 +1230,25 @@ static int substep_adjoint(sim_t* S, int n, const state_t* sn, const double* phi
                         Fbn[3 * i + k] += c * Gfb[i] * Br[k];
                         g_mag[3 * p + k] += c * Gfb[i] * F[3 * i + k];
                     }
-                    if (gGf)
-                        for (int j = 0; j < d; ++j) gGf[3 * i + j] += c * FB[i] * fbar[j];
+                    if (tGp)
+                        for (int j = 0; j < d; ++j) tGp[9 + 3 * i + j] = c * FB[i] * fbar[j];
                 }
                 double dsdphi = P->simp_q > 0 ? P->simp_q * ipow(phi[p], P->simp_q - 1) : 0.0;
                 phib += dsdphi * P->p_vol / MU0 * fraw;
             }
             g_phi[p] += phib + mpbar * P->rho0 * P->p_vol;
         }
+        for (int p = p0; p < p1; ++p) {
+            const double* tBap = tBa + 3 * (size_t)(p - p0);
+            for (int i = 0; i < d; ++i) gBa[i] += tBap[i];
+            if (Gf && gGf) {
+                const double* tGp = tG + 18 * (size_t)(p - p0);
+                for (int e = 0; e < 9; ++e) gGf[e] += tGp[e];
+                for (int e = 0; e < 9; ++e) gGf[e] += tGp[9 + e];
+            }
+        }
+        free(tBa);
+        free(tG);
     }
     free(Vbar);
     free(mbar);
