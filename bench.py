@@ -1,13 +1,14 @@
 """Throughput of the differentiable magneto-elastic MPM on one GB300.
 
-One bench step = one design iteration of a workload (default: the 2D
-locomotion configuration, 30,000 particles on 128^2 for 4,000 substeps): the
-forward pass over the whole horizon (cell sort, P2G, grid operation, G2P,
-objective) plus the checkpointed adjoint (recomputation and the reverse
-kernels), producing dL/dphi, dL/dB~_r and dL/dB_applied.
+One bench step = one design iteration of a workload (default: the 3D
+locomotion configuration, about 1,000,000 particles on 128^3 for 5,000
+substeps, the largest single-GPU configuration): the forward pass over the
+whole horizon (cell sort, P2G, grid operation, G2P, objective) plus the
+checkpointed adjoint (recomputation and the reverse kernels), producing
+dL/dphi, dL/dB~_r and dL/dB_applied.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload walker2d_128|beam2d_64|plate3d_64|walker3d_128|walker2d_batch64]
+                    [--workload walker3d_128|walker2d_128|beam2d_64|plate3d_64|walker2d_batch64]
 
 Prints one JSON line (rank 0).  ``value`` is particle-steps per second of
 forward+adjoint over all ranks (sum of particles x substeps / max time);
@@ -40,8 +41,8 @@ CLASS_NAMES = ["forward particle (G2P+P2G)", "adjoint particle (P2G^T+G2P^T)", "
 
 
 # the paper's five workload shapes: generator and full horizon.  The default,
-# walker2d_128, is the configuration the metric is quoted on; the others are
-# for measuring the same step on the other shapes.
+# walker3d_128, is the largest configuration that fits one GPU; the others
+# measure the same step on the other shapes.
 WORKLOADS = {
     "walker2d_128": (lambda seed, n: W.walker_2d(seed=seed, n_steps=n, checkpoint_every=100), 4000),
     "beam2d_64": (lambda seed, n: W.beam_2d(seed=seed, n_steps=n), 200),
@@ -51,7 +52,7 @@ WORKLOADS = {
 }
 
 
-def workload(name="walker2d_128", seed=0, substeps=None):
+def workload(name="walker3d_128", seed=0, substeps=None):
     """A named workload; ``substeps`` shortens the horizon (profiling runs)."""
     make, full = WORKLOADS[name]
     return make(seed, substeps if substeps else full)
@@ -76,24 +77,39 @@ def workload_desc(w, name):
     }
 
 
-def particle_step_bytes(cfg):
-    """Algorithmic bytes per particle-substep of one design iteration.
+def method_bytes(dim):
+    """Algorithmic bytes per particle-substep that the method itself must move
+    (float32), by pass: what the roofline fractions are computed with.
 
-    Per kernel and particle, in float32: the lean forward (G2P + P2G) reads
-    and writes x and E and reads phi, B~_r; the store pass of the
-    recomputation writes the full state instead; the fused adjoint reads
-    state n, (x, E) of state n-1, the partial adjoint in and out, the design,
-    and read-modify-writes the design gradients.  Without checkpointing the
-    forward pass is the store pass and nothing is recomputed.
+    forward: read the state (x, v, C, F) and write it, read the design
+    (phi, B~_r): 108 B in 2D, 208 B in 3D; plus the grid per active node (P2G
+    write, grid read and write, G2P read: 40 B / 56 B) over the particles per
+    cell (4 / 8): +10 B / +7 B.  adjoint: read the stored state, read the
+    adjoint of n+1 and write that of n, read the design and read-modify-write
+    its gradients: 180 B / 336 B, plus twice the forward grid term.
+    Recomputation and sort traffic are not counted, so they count against the
+    fractions.  Returns (forward, adjoint, forward + adjoint).
     """
+    if dim == 2:
+        fwd, adj = 108 + 10, 180 + 20
+    else:
+        fwd, adj = 208 + 7, 336 + 14
+    return fwd, adj, fwd + adj
+
+
+def kernel_bytes(cfg):
+    """Bytes per particle and launch of this build's fused kernels (float32):
+    the lean forward (G2P n + P2G n+1) reads and writes x and E and reads phi,
+    B~_r; the store pass of the recomputation writes the full state instead;
+    the fused adjoint reads state n, (x, E) of state n-1, the partial adjoint
+    in and out, the design, and read-modify-writes the design gradients.
+    Reported beside the method's bytes."""
     d = cfg.dim
     xf, full, design = d + d * d, 2 * d + 2 * d * d, 1 + d
     lean = 4 * (xf + xf + design)
     store = 4 * (xf + full + design)
     adjoint = 4 * (full + xf + 2 * xf + design + 2 * design)
-    if cfg.checkpoint_every and cfg.checkpoint_every < cfg.n_steps:
-        return lean + store + adjoint
-    return store + adjoint
+    return {"forward lean": lean, "forward store": store, "adjoint": adjoint}
 
 
 def load_peaks():
@@ -281,21 +297,31 @@ def run_ours(args):
     sim_options = sim.options()
 
     # Per-kernel durations: one more design iteration after the timed region,
-    # with CUDA events around every k-th launch of each kernel class, on one
-    # stream.  The timed region overlaps the recomputation of one checkpoint
-    # segment with the adjoint of the next on two streams, and a kernel timed
-    # there would share the GPU with the other stream's kernels.
+    # on one stream and with programmatic dependent launch off, with CUDA
+    # events around every k-th launch of each kernel class.  With PDL on, a
+    # kernel's start event would fire while its predecessor still runs (its
+    # CTAs wait inside it), and on two streams a kernel shares the GPU with
+    # the other stream's; here each timed launch runs alone, so its events
+    # bracket its own duration.  Class time per iteration = average duration
+    # x the class's launches in one iteration; the sum over classes is
+    # reported beside the timed step.
     sim.set_option(6, 1)
+    sim.set_option(7, 0)
     sim.set_option(1, args.timing_stride)
     iteration()  # captures the instrumented graphs
     torch.cuda.synchronize()
     sim.reset_stats()
     flush.zero_()
+    tp0, tp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tp0.record(stream)
     iteration()
+    tp1.record(stream)
     torch.cuda.synchronize()
+    timing_pass_ms = tp0.elapsed_time(tp1)
     stats = sim.stats()
     sim.set_option(1, 0)
     sim.set_option(6, sim_options["streams"])
+    sim.set_option(7, sim_options["pdl"])
     if dist:
         tt = torch.tensor([total_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -305,11 +331,27 @@ def run_ours(args):
     value = total_ps / (ms_per_step / 1000.0)
     loss_val = float(loss.sum().item())
 
-    # dominant kernel class by measured time
-    per_class_ms = [stats["timed_ms"][c] for c in range(4)]
-    dom = int(np.argmax(per_class_ms))
+    # dominant kernel class by its time per design iteration
+    avg_ms = [stats["timed_ms"][c] / stats["timed_launches"][c] if stats["timed_launches"][c] else 0.0
+              for c in range(4)]
+    class_ms = [avg_ms[c] * stats["class_launches"][c] for c in range(4)]
+    dom = int(np.argmax(class_ms))
     peak, peak_kind = load_peaks()
-    achieved = (stats["timed_bytes"][dom] / 1e9) / (stats["timed_ms"][dom] / 1e3) if stats["timed_ms"][dom] else 0.0
+    fwd_b, adj_b, step_b = method_bytes(cfg.dim)
+    kb = kernel_bytes(cfg)
+    # bytes per launch: every particle kernel launch covers all particles of
+    # the batch, one substep of its pass
+    per_particle = {0: fwd_b, 1: adj_b}.get(dom)
+    if per_particle is not None:
+        bytes_launch = per_particle * cfg.n_total
+        what = (f"{per_particle} B per particle-substep (the method's {'forward' if dom == 0 else 'adjoint'} "
+                f"bytes) x {cfg.n_total} particles")
+    else:  # a grid class: 48 B (64 B adjoint) per node of every instance's grid
+        per_node = 48 if dom == 2 else 64
+        bytes_launch = per_node * cfg.n_instances * cfg.res ** cfg.dim
+        what = f"{per_node} B per grid node x {cfg.n_instances * cfg.res ** cfg.dim} nodes"
+    dur_s = avg_ms[dom] / 1e3
+    achieved = bytes_launch / 1e9 / dur_s if dur_s > 0 else 0.0
     launches_timed = stats["timed_launches"][dom]
     roofline = {
         "bound": "hbm",
@@ -318,31 +360,41 @@ def run_ours(args):
         "peak": peak,
         "unit": "GB/s",
         "frac": round(achieved / peak, 4),
-        "peak_source": f"{peak_kind} hbm_gbs",
+        "peak_source": f"{peak_kind} hbm_gbs (burst copy; the kernel is timed alone)",
         "traffic": None,
-        "avg_launch_us": round(1e3 * stats["timed_ms"][dom] / max(launches_timed, 1), 2),
-        "algorithmic_bytes_per_launch": round(stats["timed_bytes"][dom] / max(launches_timed, 1)),
+        "avg_launch_us": round(1e3 * avg_ms[dom], 2),
+        "algorithmic_bytes_per_launch": round(bytes_launch),
+        "algorithmic_bytes": what,
         "timed_launches": launches_timed,
-        "time_share_by_class": {CLASS_NAMES[c]: round(per_class_ms[c] / max(sum(per_class_ms), 1e-9), 3)
-                                for c in range(4)},
-        "avg_launch_us_by_class": {CLASS_NAMES[c]: round(1e3 * per_class_ms[c] / max(stats["timed_launches"][c], 1), 2)
-                                   for c in range(4)},
+        "class_ms_per_iteration": {CLASS_NAMES[c]: round(class_ms[c], 3) for c in range(4)},
+        "class_launches_per_iteration": {CLASS_NAMES[c]: int(stats["class_launches"][c]) for c in range(4)},
+        "avg_launch_us_by_class": {CLASS_NAMES[c]: round(1e3 * avg_ms[c], 2) for c in range(4)},
+        "class_ms_sum": round(sum(class_ms), 3),
+        "class_ms_sum_over_step": round(sum(class_ms) / ms_per_step, 4),
+        "timing_pass_ms": round(timing_pass_ms, 3),
+        "time_share_by_class": {CLASS_NAMES[c]: round(class_ms[c] / ms_per_step, 4) for c in range(4)},
     }
+    if dom in (0, 1):
+        kname = "forward lean" if dom == 0 else "adjoint"
+        kach = kb[kname] * cfg.n_total / 1e9 / dur_s if dur_s > 0 else 0.0
+        roofline["fused_kernel_bytes"] = {"bytes_per_particle": kb[kname], "achieved": round(kach, 1),
+                                          "frac": round(kach / peak, 4),
+                                          "what": f"{kname} kernel's own loads and stores per particle"}
     roofline["timing"] = (f"CUDA events around every {args.timing_stride}th launch of each kernel class, "
-                          "one extra design iteration on one stream after the timed region")
+                          "in one extra design iteration after the timed region: one stream, programmatic "
+                          "dependent launch off")
     if args.traffic_bytes:
         roofline["traffic"] = args.traffic_bytes
         roofline["traffic_source"] = "--traffic-bytes"
     else:
         roofline["traffic"], roofline["traffic_source"] = recorded_traffic(args.workload, CLASS_NAMES[dom])
-    # the whole design iteration against the same peak: algorithmic bytes of
-    # every particle-substep over the timed step
-    bps = particle_step_bytes(cfg)
-    step_achieved = ps * bps / 1e9 / (ms_per_step / 1e3)
+    # the whole design iteration against the same peak: the method's bytes of
+    # every particle-substep (forward + adjoint) over the timed step
+    step_achieved = ps * step_b / 1e9 / (ms_per_step / 1e3)
     step_roofline = {"bound": "hbm", "achieved": round(step_achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(step_achieved / peak, 4), "bytes_per_particle_step": bps,
-                     "what": "algorithmic bytes of a design iteration (forward, recomputation, adjoint) "
-                             "over the timed step"}
+                     "frac": round(step_achieved / peak, 4), "bytes_per_particle_step": step_b,
+                     "what": "the method's forward + adjoint bytes of every particle-substep over the timed "
+                             "design iteration (recomputation, sort and full-grid traffic count against it)"}
 
     # end to end through the host-buffer entry points (pinned memory)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -543,31 +595,51 @@ def run_codesign(w, sim, dev, steps):
 # ---------------------------------------------------------------------------
 # oracle arm (CPU baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def _oracle_sample(w, n_steps):
+def _oracle_sample(w, n_steps, cores):
+    """Forward + adjoint of the first n_steps substeps on `cores` host threads
+    (the oracle's threaded passes give the serial results bit for bit)."""
     import oracle
 
     ws = W.with_steps(w, n_steps)
-    t0 = time.perf_counter()
-    oracle.forward(ws)
-    oracle.backward(ws, ckpt_every=max(1, n_steps // 4))
-    dt = time.perf_counter() - t0
-    return ws.cfg.n_total * n_steps / dt, dt
+    with oracle.threads(cores) as used:
+        t0 = time.perf_counter()
+        oracle.forward(ws)
+        oracle.backward(ws, ckpt_every=max(1, n_steps // 4))
+        dt = time.perf_counter() - t0
+    return ws.cfg.n_total * n_steps / dt, dt, used
 
 
-def sample_steps(w, n_steps):
-    """Oracle sample length: the requested substeps, or (0) about 7 million
-    particle-steps, some 10-20 s of one host core."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def sample_steps(w, n_steps, cores=1):
+    """Oracle sample length: the requested substeps, or (0) a window of about
+    7 million 2D particle-steps per core (a 3D particle-step costs about 5x
+    as much; the threads scale at about half of ideal), some 10-30 s of host
+    time."""
     if n_steps > 0:
         return min(n_steps, w.cfg.n_steps)
-    return int(max(1, min(w.cfg.n_steps, 7.0e6 // max(w.cfg.n_total, 1))))
+    cost = 1.0 if w.cfg.dim == 2 else 5.0
+    budget = 7.0e6 * max(1.0, 0.5 * cores) / cost
+    return int(max(1, min(w.cfg.n_steps, budget // max(w.cfg.n_total, 1))))
 
 
 def cpu_baseline(w, n_steps):
-    n_steps = sample_steps(w, n_steps)
-    v, dt = _oracle_sample(w, n_steps)
-    return {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"first {n_steps} of {w.cfg.n_steps} substeps, all {w.cfg.n_total} particles, "
-                       f"forward + adjoint (FP64 serial C oracle; {dt:.1f} s; host has {os.cpu_count()} cores)")}
+    cores = host_cores()
+    n_all = sample_steps(w, n_steps, cores)
+    v_all, dt_all, used = _oracle_sample(w, n_all, cores)
+    n_one = sample_steps(w, n_steps, 1)
+    v_one, dt_one, _ = _oracle_sample(w, n_one, 1)
+    return {"value": round(v_all, 1), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": (f"window of the first {n_all} of {w.cfg.n_steps} substeps, all {w.cfg.n_total} particles, "
+                       f"forward + adjoint of the FP64 C oracle on {used} host threads ({dt_all:.1f} s)"),
+            "one_core": {"value": round(v_one, 1), "unit": UNIT, "cores": 1,
+                         "sample": (f"window of the first {n_one} substeps, all particles, forward + adjoint, "
+                                    f"one thread ({dt_one:.1f} s)")}}
 
 
 def run_reference(args):
@@ -575,25 +647,30 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload(args.workload, substeps=args.substeps)
-    n = sample_steps(w, args.cpu_sample_steps)
+    cores = host_cores()
+    # each step is a window of the workload, sized so that the whole run
+    # (warm-up included) stays within a few minutes
+    n = sample_steps(w, args.cpu_sample_steps, cores)
+    n = max(1, n // max(1, (args.steps + args.warmup) // 4))
+    used = cores
     for _ in range(args.warmup):
-        _oracle_sample(w, max(1, n // 4))
+        _oracle_sample(w, 1, cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _oracle_sample(w, n)
+        _, _, used = _oracle_sample(w, n, cores)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
     value = w.cfg.n_total * n / (ms / 1e3)
-    sample = (f"each step: first {n} of {w.cfg.n_steps} substeps, all {w.cfg.n_total} particles, "
-              "forward + adjoint of the FP64 serial C oracle")
+    sample = (f"each step: the first {n} of {w.cfg.n_steps} substeps, all {w.cfg.n_total} particles, "
+              f"forward + adjoint of the FP64 C oracle on {used} host threads")
     out = {
         "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {**workload_desc(w, args.workload), "parallelism": "CPU, one core"},
-        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {**workload_desc(w, args.workload), "parallelism": f"CPU, {used} host threads"},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -607,10 +684,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--timing-stride", type=int, default=32,
                     help="time every k-th launch of each kernel class with CUDA events")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="walker2d_128",
-                    help="workload shape (default: the 2D locomotion configuration)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="walker3d_128",
+                    help="workload shape (default: the 3D locomotion configuration, 1M particles on 128^3)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0,
-                    help="substeps of the oracle sample (0: about 7 million particle-steps)")
+                    help="substeps of the oracle window (0: sized to some 10-30 s of host time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch options")
     ap.add_argument("--no-codesign", action="store_true",

@@ -303,10 +303,11 @@ int mpm_autotune(mpm_handle* h, const char* cache_path, int sample_substeps, voi
 
 /*
  * Counters since creation or the last reset: kernel launches issued by the
- * library, and, with MPM_OPT_TIMING on, the number of timed launches and
- * total milliseconds of the named kernel class, plus the algorithmic bytes
- * those launches moved.  kernel_class: 0 = forward particle kernel
- * (G2P + P2G), 1 = adjoint particle kernel (P2G^T + G2P^T), 2 = grid
+ * library (a replayed graph counts every kernel it holds), the launches of
+ * each kernel class, and, with MPM_OPT_TIMING on, the number of timed
+ * launches and total milliseconds of each class, plus the algorithmic bytes
+ * those launches moved.  Kernel classes (array index): 0 = forward particle
+ * kernel (G2P + P2G), 1 = adjoint particle kernel (P2G^T + G2P^T), 2 = grid
  * operation, 3 = grid adjoint.
  */
 typedef struct {
@@ -315,6 +316,7 @@ typedef struct {
     double timed_ms[4];
     double timed_bytes[4];
     long long device_bytes;
+    long long class_launches[4];
 } mpm_stats;
 int mpm_get_stats(const mpm_handle* h, mpm_stats* out);
 int mpm_reset_stats(mpm_handle* h);
@@ -326,8 +328,8 @@ int mpm_reset_stats(mpm_handle* h);
  * callers that must not call cudaMalloc.  Examples are a host framework whose
  * pool allocator owns the whole device-memory budget, and a latency-critical
  * loop where an allocation could block or fail.  Instead of a handle it keeps
- * its grid scratch in a fixed array compiled into the library: every GPU that
- * loads the library holds MPM_NOALLOC_MAX_NODES x 2 float4 (8 MiB) of it
+ * its grid scratch in a fixed array compiled into the library: every GPU on
+ * which it is called holds MPM_NOALLOC_MAX_NODES x 2 float4 (8 MiB) of it
  * until the process exits.  The caller passes all inputs and outputs.
  *
  * It runs P2G (Eq. 14-15), the grid operation (Eq. 16-18) and G2P
@@ -341,11 +343,20 @@ int mpm_reset_stats(mpm_handle* h);
  *   phi_bar    device [N]; mag device [d][N] (B~_r, Tesla)
  *   field      device [n_steps][d] (B_applied, Tesla)
  *   state_out  device [2d + 2d^2][N], same layout; may be state_in itself
- * Blocks until the substep finishes on cuda_stream.  Errors: MPM_ERR_ARG (bad
- * config, sizes beyond the scratch maximum, missing pointers; reason on
- * stderr), MPM_ERR_CUDA, MPM_ERR_DOMAIN, MPM_ERR_NUMERIC.
- * The first call on a device looks up the scratch array's address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
+ * N = 0 is allowed (nothing moves).  The particles are not cell-sorted
+ * here: the results do not depend on their order, but the P2G scatter merges
+ * the atomics of particles that share a cell only when they are adjacent, so
+ * throughput is best with particles passed in cell order.
+ * Blocks until the substep finishes on cuda_stream; because it reads the
+ * device status back, a call on a stream that is capturing is refused with
+ * MPM_ERR_ARG before any work is enqueued.  Errors: MPM_ERR_ARG (bad config,
+ * sizes beyond the scratch maximum, missing pointers, a capturing stream),
+ * MPM_ERR_OOM or MPM_ERR_CUDA (the scratch could not be loaded; a CUDA call
+ * failed), MPM_ERR_DOMAIN, MPM_ERR_NUMERIC; mpm_noalloc_last_error() gives
+ * the reason.
+ * The first call on a device (in each CUDA context) loads the library's
+ * module there, which reserves the scratch array, and looks up its address
+ * with cudaGetSymbolAddress; make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents; each
  * call clears what must start at zero, but calls that overlap on the GPU
  * (other streams, threads or processes on the same device) race on it.
@@ -354,6 +365,10 @@ int mpm_reset_stats(mpm_handle* h);
 int mpm_substep_noalloc(const mpm_config* cfg, int substep, const float* state_in,
                         const float* phi_bar, const float* mag, const float* field,
                         float* state_out, void* cuda_stream);
+/* Text of the last failure of mpm_substep_noalloc on the calling thread ("" if
+ * its last call succeeded).  Owned by the library; valid until the thread's
+ * next call. */
+const char* mpm_noalloc_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_CUDA", -3: "MPM_ERR
 EXPORTS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_forward", "mpm_backward",
            "mpm_forward_host", "mpm_backward_host", "mpm_read_state", "mpm_sort_particles",
            "mpm_set_option", "mpm_get_option", "mpm_autotune", "mpm_get_stats", "mpm_reset_stats",
-           "mpm_substep_noalloc", "mpm_set_boundaries", "mpm_set_field_gradient", "mpm_field_gradient_grad",
+           "mpm_substep_noalloc", "mpm_noalloc_last_error", "mpm_set_boundaries", "mpm_set_field_gradient", "mpm_field_gradient_grad",
            # design maps and optimiser step (mpm_design.h)
            "mpm_design_create", "mpm_design_destroy", "mpm_design_last_error", "mpm_design_forward",
            "mpm_design_backward", "mpm_adam_step"]
@@ -66,7 +66,7 @@ class mpm_config(ctypes.Structure):
 class mpm_stats(ctypes.Structure):
     _fields_ = [("launches", c_longlong), ("timed_launches", c_longlong * 4),
                 ("timed_ms", c_double * 4), ("timed_bytes", c_double * 4),
-                ("device_bytes", c_longlong)]
+                ("device_bytes", c_longlong), ("class_launches", c_longlong * 4)]
 
 
 class MpmError(RuntimeError):
@@ -113,6 +113,7 @@ def load():
             "mpm_get_stats": ([H, ctypes.POINTER(mpm_stats)], c_int),
             "mpm_reset_stats": ([H], c_int),
             "mpm_substep_noalloc": ([ctypes.POINTER(mpm_config), c_int, pf, pf, pf, pf, pf, vp], c_int),
+            "mpm_noalloc_last_error": ([], ctypes.c_char_p),
             "mpm_set_boundaries": ([H, c_int, ctypes.POINTER(mpm_boundary), pf, vp], c_int),
             "mpm_set_field_gradient": ([H, pf, vp], c_int),
             "mpm_field_gradient_grad": ([H, pf, vp], c_int),

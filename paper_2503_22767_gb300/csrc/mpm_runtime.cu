@@ -133,6 +133,7 @@ struct mpm_handle {
     bool capturing = false;
     int capture_pass = 0;
     long long graph_launches[2] = {0, 0};  // kernels inside each captured graph
+    long long graph_cls[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // per kernel class
     bool ran_graph[2] = {false, false};
 
     int tune_T = 0;  // > 0 while autotuning: passes stop after this many substeps
@@ -147,6 +148,7 @@ struct mpm_handle {
     std::vector<EventPair> events[kNumClasses];
     size_t ev_used[kNumClasses] = {0, 0, 0, 0};
     long long class_launch[kNumClasses] = {0, 0, 0, 0};
+    long long cls_issued[kNumClasses] = {0, 0, 0, 0};  // launches per class since the last reset
     long long timed_launches[kNumClasses] = {0, 0, 0, 0};
     double timed_ms[kNumClasses] = {0, 0, 0, 0};
     double timed_bytes[kNumClasses] = {0, 0, 0, 0};
@@ -242,6 +244,7 @@ template <typename F>
 int timed(mpm_handle* h, int cls, double bytes, cudaStream_t st, F&& launch) {
     bool time_it = h->timing_stride > 0 && (h->class_launch[cls] % h->timing_stride) == 0;
     h->class_launch[cls]++;
+    h->cls_issued[cls]++;
     h->launches++;
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (time_it && h->capturing) {
@@ -889,6 +892,8 @@ int run_pass(mpm_handle* h, int pass, cudaStream_t st) {
     if (!h->graphs) return body(st);
     if (!h->exec[pass]) {
         long long launches_before = h->launches;
+        long long cls_before[kNumClasses];
+        for (int c = 0; c < kNumClasses; ++c) cls_before[c] = h->cls_issued[c];
         MPM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
         h->capturing = true;
         h->capture_pass = pass;
@@ -909,9 +914,14 @@ int run_pass(mpm_handle* h, int pass, cudaStream_t st) {
         }
         h->graph_launches[pass] = h->launches - launches_before;
         h->launches = launches_before;
+        for (int c = 0; c < kNumClasses; ++c) {
+            h->graph_cls[pass][c] = h->cls_issued[c] - cls_before[c];
+            h->cls_issued[c] = cls_before[c];
+        }
     }
     MPM_CUDA(h, cudaGraphLaunch(h->exec[pass], st));
     h->launches += h->graph_launches[pass];
+    for (int c = 0; c < kNumClasses; ++c) h->cls_issued[c] += h->graph_cls[pass][c];
     h->ran_graph[pass] = true;
     return MPM_OK;
 }
@@ -1432,6 +1442,7 @@ int mpm_get_stats(const mpm_handle* h, mpm_stats* out) {
         out->timed_launches[c] = h->timed_launches[c];
         out->timed_ms[c] = h->timed_ms[c];
         out->timed_bytes[c] = h->timed_bytes[c];
+        out->class_launches[c] = h->cls_issued[c];
     }
     out->device_bytes = h->device_bytes;
     return MPM_OK;
@@ -1445,6 +1456,7 @@ int mpm_reset_stats(mpm_handle* h) {
         h->timed_ms[c] = 0.0;
         h->timed_bytes[c] = 0.0;
         h->class_launch[c] = 0;
+        h->cls_issued[c] = 0;
     }
     return MPM_OK;
 }

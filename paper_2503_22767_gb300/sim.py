@@ -233,6 +233,7 @@ class Simulator:
             "timed_ms": list(s.timed_ms),
             "timed_bytes": list(s.timed_bytes),
             "device_bytes": s.device_bytes,
+            "class_launches": list(s.class_launches),
         }
 
     def reset_stats(self):

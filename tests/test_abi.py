@@ -160,3 +160,21 @@ def test_design_and_adam_null_arguments_fail_cleanly(lib):
     assert lib.mpm_adam_step(0, None, None, None, None, 0, 0.1, 0.9, 0.999, 1e-8, 0.0, 1.0, None) == B.MPM_ERR_ARG
     assert lib.mpm_adam_step(0, None, None, None, None, 1, 0.1, 0.9, 0.999, 1e-8, 1.0, 0.0, None) == B.MPM_ERR_ARG
     assert lib.mpm_adam_step(0, None, None, None, None, 1, 0.1, 0.9, 0.999, 1e-8, 0.0, 1.0, None) == B.MPM_OK
+
+
+def test_noalloc_rejections_are_retrievable_on_host(lib):
+    """mpm_substep_noalloc checks its configuration on the host and gives the
+    reason through mpm_noalloc_last_error (no GPU work is enqueued)."""
+    counts = (ctypes.c_int * 1)(8)
+    c = B.mpm_config()
+    c.dim, c.grid_res, c.dt, c.n_steps = 3, 128, 1e-4, 5
+    c.n_instances, c.n_particles = 1, ctypes.cast(counts, B.P_int)
+    c.n_designs, c.design_of_instance = 1, None
+    c.E, c.nu, c.rho0, c.p_vol, c.simp_q, c.bound = 1e5, 0.3, 1e3, 1e-4, 3, 3
+    assert lib.mpm_substep_noalloc(ctypes.byref(c), 0, None, None, None, None, None, None) == B.MPM_ERR_ARG
+    assert b"scratch" in lib.mpm_noalloc_last_error()
+    c.grid_res = 16
+    assert lib.mpm_substep_noalloc(ctypes.byref(c), 5, None, None, None, None, None, None) == B.MPM_ERR_ARG
+    assert b"substep" in lib.mpm_noalloc_last_error()
+    assert lib.mpm_substep_noalloc(ctypes.byref(c), 0, None, None, None, None, None, None) == B.MPM_ERR_ARG
+    assert b"required" in lib.mpm_noalloc_last_error()

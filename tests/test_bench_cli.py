@@ -10,7 +10,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.parametrize("workload", ["beam2d_64", "walker2d_128"])
+@pytest.mark.parametrize("workload", ["beam2d_64", "walker2d_128", "walker3d_128"])
 def test_reference_arm_json_line(orc, workload):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0", "--workload", workload, "--cpu-sample-steps", "2"],
@@ -25,6 +25,7 @@ def test_reference_arm_json_line(orc, workload):
     assert out["impl"] == "reference" and out["value"] > 0 and out["higher_is_better"] is True
     assert out["config"]["workload"].startswith(workload)
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
+    assert out["cpu_baseline"]["cores"] >= 1
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["unit"] == out["unit"]
 
 

@@ -1,9 +1,13 @@
 """GPU (FP32, CUDA kernels through the C ABI) against the FP64 oracle.
 
 Tolerances (from the method's precision targets): particle state relative L2
-<= 1e-4 (positions, velocities, deformation gradients) over the stated
-horizons; gradients per design block: cosine >= 0.999 and relative L2 error
-<= 1e-3; the cell sort and its permutation bit-exact.
+<= 1e-4 over the stated horizons, asserted on the positions x, the
+displacement u = x - x0, the velocities v, the deformation gradient F and the
+strain F - I (x and F alone are dominated by x0 and I, so u and F - I are the
+ones that see an error in the motion); gradients per design block: cosine >=
+0.999 and relative L2 error <= 1e-3; the cell sort and its permutation
+bit-exact.  The long horizons run the oracle on every host core (its threaded
+passes equal the serial ones bit for bit).
 """
 import functools
 
@@ -11,6 +15,7 @@ import numpy as np
 import pytest
 
 from paper_2503_22767_gb300 import workloads as W
+from oracle_windows import oracle_states
 
 pytestmark = pytest.mark.gpu
 
@@ -61,19 +66,25 @@ def cosine(a, b):
     return float(a @ b / (na * nb))
 
 
-def assert_state(g, o, w, tol=STATE_TOL):
+def state_errors(g, o, w):
+    """Relative L2 errors of the GPU state against the oracle's."""
     d = w.cfg.dim
     x0 = w.x0.astype(np.float64)
-    errs = {
+    eye = np.eye(d)[:, :, None]
+    return {
         "x": rel_l2(g["x"], o["x"]),
-        "u": rel_l2(g["x"] - x0, o["x"] - x0),
+        "u": rel_l2(np.asarray(g["x"], np.float64) - x0, o["x"] - x0),
         "v": rel_l2(g["v"], o["v"]),
         "F": rel_l2(g["F"], o["F"]),
-        "F-I": rel_l2(g["F"] - np.eye(d)[:, :, None], o["F"] - np.eye(d)[:, :, None]),
+        "F-I": rel_l2(np.asarray(g["F"], np.float64) - eye, o["F"] - eye),
     }
+
+
+def assert_state(g, o, w, tol=STATE_TOL):
+    errs = state_errors(g, o, w)
     print(w.name, {k: f"{v:.2e}" for k, v in errs.items()})
     np.testing.assert_array_equal(g["x"], g["x_state"])
-    assert errs["x"] <= tol and errs["v"] <= tol and errs["F"] <= tol, errs
+    assert all(e <= tol for e in errs.values()), errs
     return errs
 
 
@@ -390,29 +401,52 @@ def test_autotune_picks_and_caches(tmp_path):
     sim2.close()
 
 
+# The five workload shapes at their stated horizons, or over at least two
+# checkpoint segments (so a segment crossing, with its sort and reorder, is
+# inside) where the FP64 oracle on a million particles cannot afford the
+# whole horizon: (full workload, forward horizon, gradient horizon, K, error
+# curve points).
 PRECISION_CASES = {
-    "C1 beam2d 64^2, 4,096 p, 200 steps": lambda: W.beam_2d(seed=0, per_axis=4),
-    "C2 walker2d 128^2, 30,000 p, first 400 steps": lambda: W.walker_2d(seed=0, n_steps=400),
-    "C3 plate3d 64^3, 3 x 200,000 p, first 20 steps": lambda: W.plate_3d(seed=0, n_steps=20),
-    "C4 walker3d 128^3, ~1,000,000 p, first 6 steps": lambda: W.walker_3d(seed=0, n_steps=6,
-                                                                              checkpoint_every=3),
-    "C5 batch 8 x walker2d 128^2, first 100 steps": lambda: W.walker_batch_2d(seed=0, n_instances=8,
-                                                                              n_steps=100),
+    "C1 beam2d 64^2, 4,096 p, 200 steps (full horizon)":
+        (lambda: W.beam_2d(seed=0, per_axis=4), 200, 200, 50, (1, 10, 50, 100, 200)),
+    "C2 walker2d 128^2, 30,000 p, 4,000 steps (full horizon), K = 100":
+        (lambda: W.walker_2d(seed=0), 4000, 4000, 100, (10, 100, 500, 1000, 2000, 4000)),
+    "C3 plate3d 64^3, 3 x 200,000 p, first 200 of 1,000 steps, K = 100; gradients over 100":
+        (lambda: W.plate_3d(seed=0), 200, 100, 100, (1, 10, 50, 100, 200)),
+    "C4 walker3d 128^3, ~1,000,000 p, first 200 of 5,000 steps, K = 100; gradients over 100":
+        (lambda: W.walker_3d(seed=0), 200, 100, 100, (1, 10, 50, 100, 200)),
+    "C5 batch 8 x walker2d 128^2, first 500 of 2,000 steps, K = 100; gradients over 200":
+        (lambda: W.walker_batch_2d(seed=0, n_instances=8), 500, 200, 100, (10, 100, 200, 500)),
 }
 
 
+@pytest.mark.slow
 @pytest.mark.parametrize("name", list(PRECISION_CASES))
 def test_precision_report(name):
     """FP32 (GPU) against FP64 (oracle) on the five workload shapes: relative
-    L2 error of positions, velocities, deformation gradients, loss and each
-    gradient block, printed as a table row; the tolerances hold."""
+    L2 error of x, u = x - x0, v, F and F - I at every point of an error
+    curve up to the forward horizon (one GPU forward per point, the oracle in
+    windows), then the loss and each gradient block at the gradient horizon.
+    Each point and the gradients are printed as table rows; the tolerances
+    hold at every point."""
     import oracle
-    w = PRECISION_CASES[name]()
-    g = run_gpu(w)
-    of = oracle.forward(w)
-    ob = oracle.backward(w, ckpt_every=max(1, w.cfg.n_steps // 4))
+    make, t_fwd, t_grad, K, curve = PRECISION_CASES[name]
+    full = make()
+    ref = oracle_states(W.with_steps(full, t_fwd), curve)
+    worst = {}
+    for h in curve:
+        g = run_gpu(W.with_steps(full, h, checkpoint_every=K), backward=False)
+        errs = state_errors(g, ref[h], W.with_steps(full, h))
+        print("CURVE |", name, "| step", h, "|", " | ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+        for k, v in errs.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    wg = W.with_steps(full, t_grad, checkpoint_every=min(K, t_grad))
+    g = run_gpu(wg)
+    with oracle.threads():
+        of = oracle.forward(wg)
+        ob = oracle.backward(wg, ckpt_every=max(1, min(K, t_grad) // 4))
     row = {
-        "x": rel_l2(g["x"], of["x"]), "v": rel_l2(g["v"], of["v"]), "F": rel_l2(g["F"], of["F"]),
+        **{f"{k} (worst on the curve)": v for k, v in worst.items()},
         "loss": rel_l2(g["loss"], of["loss"]),
         "g_phi": rel_l2(g["g_phi"], ob["g_phi"]), "g_mag": rel_l2(g["g_mag"], ob["g_mag"]),
         "g_field": rel_l2(g["g_field"], ob["g_field"]),
@@ -420,6 +454,6 @@ def test_precision_report(name):
     }
     print("PRECISION |", name, "|", " | ".join(f"{k} {v:.2e}" if k != "cos_min" else f"{k} {v:.7f}"
                                                 for k, v in row.items()))
-    assert row["x"] <= STATE_TOL and row["v"] <= STATE_TOL and row["F"] <= STATE_TOL
+    assert all(v <= STATE_TOL for v in worst.values()), worst
     assert row["cos_min"] >= GRAD_COS
     assert max(row["g_phi"], row["g_mag"], row["g_field"]) <= GRAD_REL

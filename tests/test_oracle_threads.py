@@ -69,3 +69,21 @@ def test_set_threads_reports_the_count(orc):
     assert n in (1, 4)  # 1 when the compiler has no OpenMP
     assert orc.set_threads(0) == 1
     orc.set_threads(1)
+
+
+@pytest.mark.parametrize("key", ["2d_floor", "3d_boxes_fgrad"])
+def test_windowed_oracle_run_equals_straight_run(orc, key):
+    """The error curves of the precision report run the oracle in windows,
+    each continuing from the last window's FP64 state: the states equal one
+    straight run's bit for bit."""
+    from oracle_windows import oracle_states
+
+    w = CASES[key]()
+    T = w.cfg.n_steps
+    points = sorted({1, T // 3, T // 2, T})
+    states = oracle_states(w, points, threads=3)
+    orc.set_threads(1)
+    for h in points:
+        o = orc.forward(W.with_steps(w, h))
+        for k in ("x", "v", "C", "F"):
+            np.testing.assert_array_equal(states[h][k], o[k], err_msg=f"{k} at {h}")

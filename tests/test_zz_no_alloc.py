@@ -1,12 +1,16 @@
-"""The allocation-free substep against the library's regular entry points.
+"""The allocation-free substep against the FP64 oracle and the regular entry
+points.
 
 ``mpm_substep_noalloc`` serves callers that must not call cudaMalloc, for
 example code running under a framework whose own pool allocator owns the
 device-memory budget. It keeps its grid scratch in a fixed array inside the
-library instead. This test runs it twice in a row (substep 0, then substep 1 on
-its own output) through the C ABI. The states must match ``mpm_forward`` over 1
-and 2 substeps read back with ``mpm_read_state``, within the parity
-tests' state tolerance. Device free memory must not change across a call.
+library instead. These tests run it twice in a row (substep 0, then substep 1
+on its own output) through the C ABI, into separate buffers and in place
+(state_out == state_in). The states must match the FP64 oracle and
+``mpm_forward`` (read back with ``mpm_read_state``) over 1 and 2 substeps,
+within the parity tests' state tolerance. Device free memory must not change
+across calls; the first call on a device is excluded from that check, since
+it may load the library's module and with it the scratch array.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test.
@@ -34,8 +38,8 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def _config_c(cfg, keep):
-    counts = (ctypes.c_int * 1)(cfg.n_total)
+def _config_c(cfg, keep, n=None):
+    counts = (ctypes.c_int * 1)(cfg.n_total if n is None else n)
     keep.append(counts)
     c = B.mpm_config()
     c.dim, c.grid_res, c.dt, c.n_steps = cfg.dim, cfg.res, cfg.dt, cfg.n_steps
@@ -50,7 +54,8 @@ def _config_c(cfg, keep):
     return c
 
 
-def _reference_state(w, n_steps):
+def _forward_state(w, n_steps):
+    """x, v, C, F after n_steps through mpm_forward + mpm_read_state."""
     wi = W.with_steps(w, n_steps)
     sim = Simulator(wi.cfg)
     sim.forward(_t(wi.x0), _t(wi.phi), _t(wi.mag), _t(wi.field),
@@ -61,8 +66,28 @@ def _reference_state(w, n_steps):
     return [a.cpu().numpy().astype(np.float64) for a in (x, v, C, F)]
 
 
+def _oracle_state(w, n_steps):
+    import oracle
+    o = oracle.forward(W.with_steps(w, n_steps))
+    return [o[k] for k in ("x", "v", "C", "F")]
+
+
 def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _errors(s, ref, d, n):
+    x, v, C, F = ref
+    eye = np.eye(d)[:, :, None]
+    got_E = s[2 * d + d * d:].reshape(d, d, n)
+    return {"x": _rel(s[:d], x), "v": _rel(s[d:2 * d], v),
+            "C": _rel(s[2 * d:2 * d + d * d].reshape(d, d, n), C),
+            "F": _rel(got_E + eye, F), "F-I": _rel(got_E, F - eye)}
+
+
+def _call(lib, c, step, s_in, phi, mag, field, s_out, stream):
+    return lib.mpm_substep_noalloc(ctypes.byref(c), step, B.fptr(s_in), B.fptr(phi), B.fptr(mag),
+                                   B.fptr(field), B.fptr(s_out), stream)
 
 
 CASES = {
@@ -75,8 +100,9 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("in_place", [False, True])
 @pytest.mark.parametrize("key", list(CASES))
-def test_substep_noalloc_matches_forward_twice(key):
+def test_substep_noalloc_matches_oracle_and_forward_twice(key, in_place):
     lib = B.load()
     w = CASES[key]()
     cfg = w.cfg
@@ -88,30 +114,45 @@ def test_substep_noalloc_matches_forward_twice(key):
     s0[:d] = w.x0
     if w.v0 is not None:
         s0[d:2 * d] = w.v0
-    state = [_t(s0), torch.empty((ncomp, n), device="cuda"), torch.empty((ncomp, n), device="cuda")]
+    if in_place:
+        buf = _t(s0)
+        state = [buf, buf, buf]
+    else:
+        state = [_t(s0), torch.empty((ncomp, n), device="cuda"), torch.empty((ncomp, n), device="cuda")]
     phi, mag, field = _t(w.phi), _t(w.mag), _t(w.field[0])
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
 
-    free_before = None
+    results = {}
+    free_before = None  # the first call may load the module and its scratch array
     for step in (0, 1):
-        st = lib.mpm_substep_noalloc(ctypes.byref(c), step, B.fptr(state[step]), B.fptr(phi),
-                                     B.fptr(mag), B.fptr(field), B.fptr(state[step + 1]), stream)
-        assert st == B.MPM_OK, B.STATUS_NAMES.get(st, st)
+        st = _call(lib, c, step, state[step], phi, mag, field, state[step + 1], stream)
+        assert st == B.MPM_OK, (B.STATUS_NAMES.get(st, st), lib.mpm_noalloc_last_error())
+        assert lib.mpm_noalloc_last_error() == b""
         torch.cuda.synchronize()
+        results[step + 1] = state[step + 1].cpu().numpy().astype(np.float64)
         free_now = torch.cuda.mem_get_info()[0]
         if free_before is not None:
             assert free_now == free_before, "device free memory changed across a call"
         free_before = free_now
 
     for step in (1, 2):
-        x, v, C, F = _reference_state(w, step)
-        s = state[step].cpu().numpy().astype(np.float64)
-        got_F = s[2 * d + d * d:].reshape(d, d, n) + np.eye(d)[:, :, None]
-        errs = {"x": _rel(s[:d], x), "v": _rel(s[d:2 * d], v),
-                "C": _rel(s[2 * d:2 * d + d * d].reshape(d, d, n), C), "F": _rel(got_F, F)}
-        print(key, step, errs)
-        assert all(e <= STATE_TOL for e in errs.values()), (step, errs)
+        s = results[step]
+        for name, ref in (("oracle", _oracle_state(w, step)), ("mpm_forward", _forward_state(w, step))):
+            errs = _errors(s, ref, d, n)
+            print(key, "in place" if in_place else "separate", step, name, errs)
+            assert all(e <= STATE_TOL for e in errs.values()), (name, step, errs)
+
+
+def test_substep_noalloc_no_particles():
+    lib = B.load()
+    w = CASES["2d_floor"]()
+    keep = []
+    c = _config_c(w.cfg, keep, n=0)
+    field = _t(w.field[0])
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.mpm_substep_noalloc(ctypes.byref(c), 0, None, None, None, B.fptr(field), None, stream)
+    assert st == B.MPM_OK, lib.mpm_noalloc_last_error()
 
 
 def test_substep_noalloc_rejects_oversized_grid():
@@ -122,3 +163,37 @@ def test_substep_noalloc_rejects_oversized_grid():
     c = _config_c(cfg, keep)
     st = lib.mpm_substep_noalloc(ctypes.byref(c), 0, None, None, None, None, None, None)
     assert st == B.MPM_ERR_ARG
+    assert b"262144" in lib.mpm_noalloc_last_error()
+
+
+def test_substep_noalloc_refuses_a_capturing_stream():
+    """The call reads the device status back and synchronises, so under
+    stream capture it returns MPM_ERR_ARG without enqueuing anything: the
+    caller's capture stays valid and its graph replays."""
+    lib = B.load()
+    w = CASES["2d_floor"]()
+    cfg = w.cfg
+    d, n = cfg.dim, cfg.n_total
+    keep = []
+    c = _config_c(cfg, keep)
+    s = torch.zeros((2 * d + 2 * d * d, n), device="cuda")
+    s[:d] = _t(w.x0)
+    phi, mag, field = _t(w.phi), _t(w.mag), _t(w.field[0])
+    out = torch.empty_like(s)
+    # a call outside any capture first (the first call on a device may load the module)
+    stream0 = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert _call(lib, c, 0, s, phi, mag, field, out, stream0) == B.MPM_OK
+    counter = torch.zeros(1, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        counter.add_(1.0)
+        cap = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        st = _call(lib, c, 0, s, phi, mag, field, out, cap)
+        counter.add_(1.0)
+    assert st == B.MPM_ERR_ARG
+    assert b"capturing" in lib.mpm_noalloc_last_error()
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(counter.item()) == 2.0
