@@ -52,10 +52,15 @@ WORKLOADS = {
 }
 
 
-def workload(name="walker3d_128", seed=0, substeps=None):
-    """A named workload; ``substeps`` shortens the horizon (profiling runs)."""
+def workload(name="walker3d_128", seed=0, substeps=None, checkpoint_every=None):
+    """A named workload; ``substeps`` shortens the horizon and
+    ``checkpoint_every`` overrides the segment length (profiling runs on a
+    few GB of device memory)."""
     make, full = WORKLOADS[name]
-    return make(seed, substeps if substeps else full)
+    w = make(seed, substeps if substeps else full)
+    if checkpoint_every:
+        w = W.with_steps(w, w.cfg.n_steps, checkpoint_every=checkpoint_every)
+    return w
 
 
 def workload_desc(w, name):
@@ -126,7 +131,7 @@ def load_peaks():
 # under profiles/ (traffic.json).  A figure is used only while the particle
 # kernels' sources hash to the value stored beside it, i.e. while the kernel
 # is the one the counters were taken on; otherwise traffic is null.
-KERNEL_SOURCES = ("particle_kernels.cuh", "mpm_device.cuh", "particle_io.cuh", "warp_box.cuh")
+KERNEL_SOURCES = ("particle_kernels.cuh", "mpm_device.cuh", "particle_io.cuh", "warp_scatter.cuh")
 
 
 def kernel_source_hash():
@@ -229,14 +234,14 @@ def run_ours(args):
     # A single instance runs as one replica per rank, seeded by rank.
     plan = None
     if world > 1:
-        full = workload(args.workload, seed=0, substeps=args.substeps)
+        full = workload(args.workload, seed=0, substeps=args.substeps, checkpoint_every=args.checkpoint_every)
         if full.cfg.n_instances >= world:
             from paper_2503_22767_gb300 import shard
             plan = shard.plan(full.cfg.counts, full.cfg.design_of_instance, world)
             w = shard.local_workload(full, plan, rank)
             total_ps = full.cfg.n_total * full.cfg.n_steps
     if plan is None:
-        w = workload(args.workload, seed=rank, substeps=args.substeps)
+        w = workload(args.workload, seed=rank, substeps=args.substeps, checkpoint_every=args.checkpoint_every)
         total_ps = w.cfg.n_total * w.cfg.n_steps * world
     cfg = w.cfg
     sim = Simulator(cfg)
@@ -263,7 +268,7 @@ def run_ours(args):
         tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
 
     if args.options:
-        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "tile": 5, "streams": 6, "pdl": 7, "adjoint_blocks": 8, "warp_box": 9}
+        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "streams": 6, "pdl": 7, "adjoint_blocks": 8, "grid_blocks": 10}
         for item in args.options.split(","):
             name, value = item.split("=")
             sim.set_option(keys[name.strip()], int(value))
@@ -646,7 +651,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.workload, substeps=args.substeps)
+    w = workload(args.workload, substeps=args.substeps, checkpoint_every=args.checkpoint_every)
     cores = host_cores()
     # each step is a window of the workload, sized so that the whole run
     # (warm-up included) stays within a few minutes
@@ -699,6 +704,8 @@ def main(argv=None):
                          "(names as in Simulator.options())")
     ap.add_argument("--substeps", type=int, default=0,
                     help="horizon of the timed workload (0: the configuration's full horizon)")
+    ap.add_argument("--checkpoint-every", type=int, default=0,
+                    help="checkpoint segment length (0: the configuration's own)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end iterations (default min(steps, 3))")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")

@@ -176,6 +176,16 @@ int mpm_backward_host(mpm_handle* h, const float* dloss, float* g_phi, float* g_
 int mpm_read_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* cuda_stream);
 
 /*
+ * The same state in the variables the library integrates (Eq. 21-22 written
+ * for them): the displacement u = x - x0 and the strain E = F - I, float32,
+ * input order, device pointers (each may be NULL): u, v [d][N]; C, E
+ * [d][d][N].  Small displacements and strains keep their full float32
+ * precision here, where x and F above are rounded next to x0 and I.
+ * Errors: MPM_ERR_STATE (no forward yet), MPM_ERR_CUDA.
+ */
+int mpm_read_state_strain(mpm_handle* h, float* u, float* v, float* C, float* E, void* cuda_stream);
+
+/*
  * The particle ordering used by the substep, exposed for checking: for
  * device positions x [d][N] (N = sum of n_particles, instances concatenated)
  * writes the cell key of every particle and the stable order by key
@@ -202,9 +212,6 @@ enum {
                               Default 1 (forward fused, adjoint separate) */
     MPM_OPT_GRAPHS = 4, /* 1 (default): each pass is captured once as a CUDA graph on an
                            internal stream and replayed on cuda_stream; 0: direct launches */
-    MPM_OPT_TILE = 5,   /* 1: the per-substep kernels stage the grid box of each CTA in
-                           shared memory and scatter through warp-aggregated shared-memory
-                           tiles; 0 (default): direct global gathers and vector atomics */
     MPM_OPT_STREAMS = 6, /* 2 (default): the backward pass recomputes checkpoint segment s-1
                             on a second stream while the adjoint of segment s runs (two
                             sets of segment buffers); 1: one stream */
@@ -212,13 +219,14 @@ enum {
                            launch, so a kernel's CTAs are scheduled while its predecessor
                            drains; 0: plain stream order */
     MPM_OPT_ADJOINT_BLOCKS = 8, /* register budget of the fused adjoint particle kernel, as
-                           resident 256-thread blocks per SM: 2 (default, <= 128 registers),
-                           3 (<= 80 registers: more warps to hide gather latency, at the
-                           cost of spills) or 4 (<= 64 registers; 2D only, 3D takes it as 3) */
-    MPM_OPT_WARP_BOX = 9 /* 1 (default in 3D): in the direct particle kernels, each fully
-                           active warp whose stencils fit a 128-node box loads that box into
-                           shared memory once, and its gathers read from there; 0 (default
-                           in 2D): every gather reads global memory */
+                           resident 256-thread blocks per SM: 2 (default in 2D, <= 128
+                           registers), 3 (default in 3D, <= 80 registers: more warps to hide
+                           gather latency, at the cost of spills) or 4 (<= 64 registers; 2D
+                           only, 3D takes it as 3) */
+    MPM_OPT_GRID_BLOCKS = 10 /* 3D: 1 (default): the P2G kernels list the blocks of 4x4x4
+                           nodes their stencils touch, and the grid operation and its
+                           reverse run over the listed blocks only; 0: over every node.
+                           No effect in 2D. */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);
@@ -276,8 +284,7 @@ int mpm_set_boundaries(mpm_handle* h, int n, const mpm_boundary* boxes, const fl
  * mpm_set_field_gradient copies grad (device, [n_instances][n_steps][dim][dim],
  * row-major per substep) into storage from mpm_create, or removes it (NULL).
  * It synchronises cuda_stream, and a following mpm_backward needs a new
- * mpm_forward.  With a gradient set, the shared-memory tiles
- * (MPM_OPT_TILE) are not used, and mpm_substep_noalloc stays uniform.
+ * mpm_forward.  mpm_substep_noalloc stays uniform.
  * mpm_field_gradient_grad copies dL/dG (same layout) after mpm_backward.
  * Errors: MPM_ERR_ARG, MPM_ERR_STATE (no gradient set, or no backward yet),
  * MPM_ERR_CUDA.
@@ -290,8 +297,8 @@ int mpm_field_gradient_grad(mpm_handle* h, float* g_grad, void* cuda_stream);
  * library).  Times forward + backward passes over the first sample_substeps
  * substeps (0 = two checkpoint segments) of the inputs staged by the last
  * mpm_forward, for every combination of block size {64, 128, 256}, grid
- * fusion {0, 1}, adjoint register budget {2, 3} and warp-staged gathers
- * {0, 1} (tiles off), and keeps the fastest.  With a
+ * fusion {0, 1} and adjoint register budget {2, 3, and 4 in 2D}, and keeps
+ * the fastest.  With a
  * non-NULL cache_path, results are read from and written to that JSON file,
  * keyed by dim, grid_res, particle count (rounded up to a power of 2),
  * instances and checkpoint interval; a cache hit applies the stored choice

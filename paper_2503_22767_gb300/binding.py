@@ -16,17 +16,18 @@ P_int = ctypes.POINTER(ctypes.c_int)
 
 MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM = 0, -1, -2, -3
 MPM_ERR_STATE, MPM_ERR_NUMERIC, MPM_ERR_DOMAIN, MPM_ERR_TIMEOUT = -4, -5, -6, -7
-MPM_OPT_TIMING, MPM_OPT_BLOCK, MPM_OPT_FUSE_GRID, MPM_OPT_GRAPHS, MPM_OPT_TILE, MPM_OPT_STREAMS = 1, 2, 3, 4, 5, 6
+MPM_OPT_TIMING, MPM_OPT_BLOCK, MPM_OPT_FUSE_GRID, MPM_OPT_GRAPHS, MPM_OPT_STREAMS = 1, 2, 3, 4, 6
 MPM_OPT_PDL = 7
 MPM_OPT_ADJOINT_BLOCKS = 8
-MPM_OPT_WARP_BOX = 9
+MPM_OPT_GRID_BLOCKS = 10
 STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_CUDA", -3: "MPM_ERR_OOM",
                 -4: "MPM_ERR_STATE", -5: "MPM_ERR_NUMERIC", -6: "MPM_ERR_DOMAIN",
                 -7: "MPM_ERR_TIMEOUT"}
 
 #: every function the header declares (checked by the tests)
 EXPORTS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_forward", "mpm_backward",
-           "mpm_forward_host", "mpm_backward_host", "mpm_read_state", "mpm_sort_particles",
+           "mpm_forward_host", "mpm_backward_host", "mpm_read_state", "mpm_read_state_strain",
+           "mpm_sort_particles",
            "mpm_set_option", "mpm_get_option", "mpm_autotune", "mpm_get_stats", "mpm_reset_stats",
            "mpm_substep_noalloc", "mpm_noalloc_last_error", "mpm_set_boundaries", "mpm_set_field_gradient", "mpm_field_gradient_grad",
            # design maps and optimiser step (mpm_design.h)
@@ -106,6 +107,7 @@ def load():
             "mpm_forward_host": ([H, pf, pf, pf, pf, pf, pf, pf, pf, vp], c_int),
             "mpm_backward_host": ([H, pf, pf, pf, pf, vp], c_int),
             "mpm_read_state": ([H, pf, pf, pf, pf, vp], c_int),
+            "mpm_read_state_strain": ([H, pf, pf, pf, pf, vp], c_int),
             "mpm_sort_particles": ([H, pf, pi, pi, vp], c_int),
             "mpm_set_option": ([H, c_int, c_longlong], c_int),
             "mpm_get_option": ([H, c_int, ctypes.POINTER(c_longlong)], c_int),

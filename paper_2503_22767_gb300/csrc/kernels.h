@@ -11,6 +11,10 @@ namespace mpm {
 // Buffers one particle kernel touches; unused members stay null.
 struct StepArgs {
     const float* s_in = nullptr;     // state read by the kernel (SoA, stride np)
+    // initial positions in the current order (stride np): the X slot of the
+    // state holds the displacement u = x - x0 and positions are x0 + u; null:
+    // the X slot holds x itself
+    const float* x0 = nullptr;
     float* s_out = nullptr;          // state written by G2P
     const float* s_aux = nullptr;    // adjoint: state of the G2P^T substep (x, F)
     const float4* V = nullptr;       // grid velocity of the G2P (or G2P^T) substep
@@ -39,6 +43,8 @@ struct StepArgs {
     const float4* VbarIn = nullptr;  // Vbar of the P2G^T substep
     float4* zero4 = nullptr;         // buffer the kernel clears for a later substep
     long long zero_n = 0;            // its length in float4
+    // 3D: the P2G part marks the node blocks its stencils touch (null: no marking)
+    ActiveBlocks blk;
 };
 
 // forward particle kernel: G2P of substep n_g2p and/or P2G of n_p2g.
@@ -68,12 +74,6 @@ extern template cudaError_t launch_adjoint_dim<2>(bool, bool, bool, bool, const 
                                                   int, cudaStream_t);
 extern template cudaError_t launch_adjoint_dim<3>(bool, bool, bool, bool, const Params&, const StepArgs&,
                                                   int, cudaStream_t);
-// Shared-memory tiled versions (kernels_tiled.cu): the forward kernel with
-// G2P (and P2G when a.acc is set), the adjoint kernel with P2G^T and G2P^T.
-cudaError_t launch_forward_tiled(int dim, bool write_all, bool fuse, const Params& P,
-                                 const StepArgs& a, int block, cudaStream_t st);
-cudaError_t launch_adjoint_tiled(int dim, bool fuse, bool fuse_v, const Params& P, const StepArgs& a,
-                                 int block, cudaStream_t st);
 // grid operation on every node of every instance: acc -> V; clears acc
 // (lean) or clears acc_next (store pass).
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,
@@ -81,24 +81,42 @@ cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4
 // grid adjoint: Vbar -> gadj (clears Vbar).
 cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, float4* Vbar,
                                 float4* gadj, int step, cudaStream_t st);
+// 3D, over the listed node blocks only (ctas persistent CTAs walk the list).
+// Grid operation: acc -> V; with clear_acc, also zeroes acc (the forward
+// pass, whose next P2G reuses it).
+cudaError_t launch_grid_blocks(const Params& P, float4* acc, float4* V, ActiveBlocks blk, bool clear_acc,
+                               int step, int ctas, cudaStream_t st);
+// Grid adjoint: Vbar -> gadj, zeroing Vbar.
+cudaError_t launch_grid_adjoint_blocks(const Params& P, const float4* acc, float4* Vbar, float4* gadj,
+                                       ActiveBlocks blk, int step, int ctas, cudaStream_t st);
+// Zeroes the flags of the listed blocks and, with acc, the n_sub
+// accumulators acc + k * acc_stride over them (the count and the warps'
+// boxes are left to the caller).
+cudaError_t launch_clear_blocks(const Params& P, float4* acc, long long acc_stride, ActiveBlocks blk, int n_sub,
+                                cudaStream_t st);
 
-// initial state from x0 / v0 (input order): C = 0, F = I, id = p.
+// initial state from x0 / v0 (input order): u = x - x0 = 0, C = 0, F = I,
+// id = p, and the current-order initial positions x0c (stride np).
 cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0,
-                              float* s, int* id, cudaStream_t st);
+                              float* s, int* id, float* x0c, cudaStream_t st);
 // dst[c][p] = src[c][perm[p]] for every component, id_dst[p] = id_src[perm[p]].
 cudaError_t launch_reorder(int ncomp, const Params& P, const float* src, float* dst,
                            const int* perm, const int* id_src, int* id_dst, cudaStream_t st);
 // adj_old[c][perm[p]] = adj_new[c][p]
 cudaError_t launch_unpermute(int ncomp, const Params& P, const float* src, float* dst,
                              const int* perm, cudaStream_t st);
-// out[c][id[p]] = s[c][p] for components [c0, c0 + ncomp), out stride n_total;
-// diag > 0 marks a diag x diag block stored as E = F - I (F is written).
+// out[c][id[p]] = s[c][p] (+ add[c][p] when add is set, stride np) for
+// components [c0, c0 + ncomp), out stride n_total; diag > 0 marks a diag x
+// diag block stored as E = F - I (F is written).
 cudaError_t launch_to_input_order(int ncomp, const Params& P, const float* s, int c0,
-                                  const int* id, float* out, cudaStream_t st, int diag = 0);
-// current-order design from the per-design arrays
+                                  const int* id, float* out, cudaStream_t st, int diag = 0,
+                                  const float* add = nullptr);
+// current-order design from the per-design arrays, and the current-order
+// initial positions x0c[c][p] = x0[c][id[p]] (x0 in input order, stride N)
 cudaError_t launch_gather_design(int dim, const Params& P, const int* id, const int* inst_off,
                                  const int* dbase, const float* phi_d, const float* mag_d,
-                                 long long nd, float* phi, float* mag, cudaStream_t st);
+                                 long long nd, float* phi, float* mag, const float* x0, float* x0c,
+                                 cudaStream_t st);
 // per-design gradients += current-order gradients
 cudaError_t launch_scatter_design_grad(int dim, const Params& P, const int* id,
                                        const int* inst_off, const int* dbase, const float* gphi,
@@ -106,10 +124,11 @@ cudaError_t launch_scatter_design_grad(int dim, const Params& P, const int* id,
                                        float* g_mag, cudaStream_t st);
 cudaError_t launch_instance_mass(const Params& P, const float* phi, const int* inst_off,
                                  float* Minst, cudaStream_t st);
-cudaError_t launch_loss(int dim, const Params& P, const float* s, const float* target,
+// (x0: current-order initial positions; the state holds displacements)
+cudaError_t launch_loss(int dim, const Params& P, const float* s, const float* x0, const float* target,
                         const int* id, const int* inst_off, const float* Minst, const float* mom,
                         float* loss_acc, float* loss_out, cudaStream_t st);
-cudaError_t launch_seed(int dim, const Params& P, const float* s, const float* target,
+cudaError_t launch_seed(int dim, const Params& P, const float* s, const float* x0, const float* target,
                         const int* id, const int* inst_off, const float* phi, const float* Minst,
                         const float* mom, const float* dloss, float* adj, float* gphi,
                         cudaStream_t st);
@@ -130,9 +149,10 @@ long long sort_key_space(int dim, int res, int n_inst);
 cudaError_t launch_scan_exclusive(const int* in, int* out, long long n, int* tmp, cudaStream_t st);
 long long sort_scan_tmp_len(long long n_keys);
 // keys, stable permutation perm[new] = old for positions x (component stride
-// xstride); flags kErrDomain for stencils outside the grid (keys clamp).
+// xstride), or x0 + x when x0 is set (same stride: x holds displacements);
+// flags kErrDomain for stencils outside the grid (keys clamp).
 cudaError_t launch_sort(int dim, const Params& P, const float* x, long long xstride,
                         const int* inst_off, SortBuffers& sb, int* perm, int* err,
-                        cudaStream_t st);
+                        cudaStream_t st, const float* x0 = nullptr);
 
 }  // namespace mpm

@@ -20,7 +20,7 @@ constexpr int block_edge() { return D == 2 ? 8 : 4; }
 
 template <int D>
 __global__ void __launch_bounds__(256) k_cell_key(Params P, const float* __restrict__ x,
-                                                  long long xstride,
+                                                  long long xstride, const float* __restrict__ x0,
                                                   const int* __restrict__ inst_off,
                                                   int* __restrict__ keys, int* __restrict__ slot,
                                                   int* __restrict__ counts, int* __restrict__ err) {
@@ -32,7 +32,9 @@ __global__ void __launch_bounds__(256) k_cell_key(Params P, const float* __restr
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        float fx = __fmul_rn(x[a * xstride + p], (float)P.res);
+        // the position (x0 + u in the displacement-form state, as the kernels form it)
+        const float xa = x0 ? __fadd_rn(x[a * xstride + p], x0[a * xstride + p]) : x[a * xstride + p];
+        float fx = __fmul_rn(xa, (float)P.res);
         float fb = floorf(__fsub_rn(fx, 0.5f));
         int b;
         if (fb >= 0.0f && fb <= (float)(P.res - 3)) {
@@ -164,15 +166,15 @@ long long sort_scan_tmp_len(long long n_keys) {
 
 cudaError_t launch_sort(int dim, const Params& P, const float* x, long long xstride,
                         const int* inst_off, SortBuffers& sb, int* perm, int* err,
-                        cudaStream_t st) {
+                        cudaStream_t st, const float* x0) {
     if (P.n_total == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(sb.counts, 0, sizeof(int) * sb.n_keys, st);
     if (e != cudaSuccess) return e;
     unsigned grid = (unsigned)((P.n_total + 255) / 256);
     if (dim == 2)
-        k_cell_key<2><<<grid, 256, 0, st>>>(P, x, xstride, inst_off, sb.keys, sb.slot, sb.counts, err);
+        k_cell_key<2><<<grid, 256, 0, st>>>(P, x, xstride, x0, inst_off, sb.keys, sb.slot, sb.counts, err);
     else
-        k_cell_key<3><<<grid, 256, 0, st>>>(P, x, xstride, inst_off, sb.keys, sb.slot, sb.counts, err);
+        k_cell_key<3><<<grid, 256, 0, st>>>(P, x, xstride, x0, inst_off, sb.keys, sb.slot, sb.counts, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = scan_exclusive(sb.counts, sb.offsets, sb.n_keys, sb.scan_tmp, st)) != cudaSuccess) return e;
     k_scatter_perm<<<grid, 256, 0, st>>>(P, sb.keys, sb.slot, sb.offsets, perm);

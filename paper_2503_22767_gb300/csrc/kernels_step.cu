@@ -75,18 +75,110 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
 
 
 // ---------------------------------------------------------------------------
+// the same over the listed node blocks only (3D)
+// ---------------------------------------------------------------------------
+// Persistent CTAs of 256 threads walk the list, four blocks of 64 nodes at a
+// time (one thread per node).  The list holds block ids, instance-major.
+struct BlockNode {
+    long long i;  // node index in the [inst][node] grid
+    int c[3];     // node coordinates
+    bool in;      // inside the grid (res need not be a multiple of the block edge)
+};
+
+__device__ __forceinline__ BlockNode block_node(const Params& P, int b, int t) {
+    const int nb = blocks_per_axis(P.res);
+    const int bpi = nb * nb * nb;
+    const int inst = b / bpi, lb = b - inst * bpi;
+    BlockNode n;
+    n.c[0] = (lb / (nb * nb)) * kBlockEdge + (t >> 4);
+    n.c[1] = ((lb / nb) % nb) * kBlockEdge + ((t >> 2) & 3);
+    n.c[2] = (lb % nb) * kBlockEdge + (t & 3);
+    n.in = n.c[0] < P.res && n.c[1] < P.res && n.c[2] < P.res;
+    n.i = (long long)inst * P.nodes + ((long long)n.c[0] * P.res + n.c[1]) * P.res + n.c[2];
+    return n;
+}
+
+__global__ void __launch_bounds__(256) k_grid_blocks(Params P, float4* __restrict__ acc, float4* __restrict__ V,
+                                                     ActiveBlocks blk, bool clear, int step) {
+    pdl_wait();
+    pdl_trigger();
+    const int n = *blk.count;
+    const int t = threadIdx.x & 63;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = blockIdx.x * 4 + (threadIdx.x >> 6); e < n; e += gridDim.x * 4) {
+        const int b = blk.list[e];
+        const BlockNode nd = block_node(P, b, t);
+        if (nd.in) {
+            const float4 g = acc[nd.i];
+            float4 out = zero;
+            if (g.x > 0.0f) {
+                float mv[3], v[3];
+                unpack3<3>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+                grid_velocity<3>(P, nd.c, g.x, mv, v, step);
+                out = make_float4(v[0], v[1], v[2], 0.0f);
+            }
+            V[nd.i] = out;
+            if (clear) acc[nd.i] = zero;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_grid_adjoint_blocks(Params P, const float4* __restrict__ acc,
+                                                             float4* __restrict__ Vbar, float4* __restrict__ gadj,
+                                                             ActiveBlocks blk, int step) {
+    pdl_wait();
+    pdl_trigger();
+    const int n = *blk.count;
+    const int t = threadIdx.x & 63;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = blockIdx.x * 4 + (threadIdx.x >> 6); e < n; e += gridDim.x * 4) {
+        const BlockNode nd = block_node(P, blk.list[e], t);
+        if (!nd.in) continue;
+        const float4 g = acc[nd.i];
+        float4 out = zero;
+        if (g.x > 0.0f) {
+            float mv[3], vb[3], mvb[3], mb;
+            unpack3<3>(make_float4(g.y, g.z, g.w, 0.0f), mv);
+            unpack3<3>(Vbar[nd.i], vb);
+            grid_velocity_adjoint<3>(P, nd.c, g.x, mv, vb, mb, mvb, step);
+            out = pack4<3>(mb, mvb);
+        }
+        Vbar[nd.i] = zero;
+        gadj[nd.i] = out;
+    }
+}
+
+// blockIdx.y: the accumulator (substep) this CTA clears over the listed
+// blocks; the CTAs of accumulator 0 also zero the flags
+__global__ void __launch_bounds__(256) k_clear_blocks(Params P, float4* __restrict__ acc, long long acc_stride,
+                                                      ActiveBlocks blk) {
+    const int k = blockIdx.y;
+    const int n = *blk.count;
+    const int t = threadIdx.x & 63;
+    for (int e = blockIdx.x * 4 + (threadIdx.x >> 6); e < n; e += gridDim.x * 4) {
+        const int b = blk.list[e];
+        if (acc) {
+            const BlockNode nd = block_node(P, b, t);
+            if (nd.in) acc[acc_stride * k + nd.i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (k == 0 && t == 0) blk.flag[b] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // helpers: init, permutations, design, loss and seeds
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void k_init_state(Params P, const float* __restrict__ x0, const float* __restrict__ v0,
-                             float* __restrict__ s, int* __restrict__ id) {
+                             float* __restrict__ s, int* __restrict__ id, float* __restrict__ x0c) {
     using L = Layout<D>;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P.n_total) return;
     const long long np = P.np, n = P.n_total;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-        s[(L::X + i) * np + p] = x0[i * n + p];
+        s[(L::X + i) * np + p] = 0.0f;  // displacement u = x - x0
+        x0c[i * np + p] = x0[i * n + p];
         s[(L::V + i) * np + p] = v0 ? v0[i * n + p] : 0.0f;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
@@ -116,14 +208,17 @@ __global__ void k_unpermute(Params P, int ncomp, const float* __restrict__ src,
 }
 
 // diag > 0: the components are a diag x diag block stored as E = F - I;
-// write F (add the identity on the diagonal).
+// write F (add the identity on the diagonal).  add: a current-order array
+// added component by component (x0 to displacements).
 __global__ void k_to_input_order(Params P, int ncomp, const float* __restrict__ s, int c0,
-                                 const int* __restrict__ id, float* __restrict__ out, int diag) {
+                                 const int* __restrict__ id, float* __restrict__ out, int diag,
+                                 const float* __restrict__ add) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P.n_total) return;
     int q = id[p];
     for (int c = 0; c < ncomp; ++c) {
         float val = s[(c0 + c) * P.np + p];
+        if (add) val = __fadd_rn(val, add[c * P.np + p]);
         if (diag > 0 && c % (diag + 1) == 0) val += 1.0f;
         out[(long long)c * P.n_total + q] = val;
     }
@@ -139,13 +234,19 @@ template <int D>
 __global__ void k_gather_design(Params P, const int* __restrict__ id, const int* __restrict__ inst_off,
                                 const int* __restrict__ dbase, const float* __restrict__ phi_d,
                                 const float* __restrict__ mag_d, long long nd,
-                                float* __restrict__ phi, float* __restrict__ mag) {
+                                float* __restrict__ phi, float* __restrict__ mag,
+                                const float* __restrict__ x0, float* __restrict__ x0c) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P.n_total) return;
-    long long di = design_index(id[p], inst_off, dbase, P.n_inst);
+    const int q = id[p];
+    long long di = design_index(q, inst_off, dbase, P.n_inst);
     phi[p] = phi_d[di];
 #pragma unroll
     for (int i = 0; i < D; ++i) mag[i * P.np + p] = mag_d[i * nd + di];
+    if (x0c) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) x0c[i * P.np + p] = x0[(long long)i * P.n_total + q];
+    }
 }
 
 template <int D>
@@ -174,9 +275,9 @@ __global__ void k_instance_mass(Params P, const float* __restrict__ phi,
 }
 
 template <int D>
-__global__ void k_loss_mse(Params P, const float* __restrict__ s, const float* __restrict__ target,
-                           const int* __restrict__ id, const int* __restrict__ inst_off,
-                           float* __restrict__ loss_acc) {
+__global__ void k_loss_mse(Params P, const float* __restrict__ s, const float* __restrict__ x0,
+                           const float* __restrict__ target, const int* __restrict__ id,
+                           const int* __restrict__ inst_off, float* __restrict__ loss_acc) {
     using L = Layout<D>;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     bool active = p < P.n_total;
@@ -186,7 +287,8 @@ __global__ void k_loss_mse(Params P, const float* __restrict__ s, const float* _
         int q = id[p];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            float e = s[(L::X + i) * P.np + p] - target[(long long)i * P.n_total + q];
+            const float x = __fadd_rn(s[(L::X + i) * P.np + p], x0[i * P.np + p]);
+            float e = x - target[(long long)i * P.n_total + q];
             e2[0] += e * e;
         }
     }
@@ -210,7 +312,8 @@ __global__ void k_loss_finalize(Params P, const int* __restrict__ inst_off,
 }
 
 template <int D>
-__global__ void k_seed(Params P, const float* __restrict__ s, const float* __restrict__ target,
+__global__ void k_seed(Params P, const float* __restrict__ s, const float* __restrict__ x0,
+                       const float* __restrict__ target,
                        const int* __restrict__ id, const int* __restrict__ inst_off,
                        const float* __restrict__ phi, const float* __restrict__ Minst,
                        const float* __restrict__ mom, const float* __restrict__ dloss,
@@ -237,7 +340,8 @@ __global__ void k_seed(Params P, const float* __restrict__ s, const float* __res
         int q = id[p];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            float e = s[(L::X + i) * np + p] - target[(long long)i * P.n_total + q];
+            const float x = __fadd_rn(s[(L::X + i) * np + p], x0[i * np + p]);
+            float e = x - target[(long long)i * P.n_total + q];
             adj[(L::X + i) * np + p] = 2.0f * e / (float)cnt * dl;
         }
     }
@@ -276,12 +380,29 @@ cudaError_t launch_grid_adjoint(int dim, const Params& P, const float4* acc, flo
     return launch_chain(P, k_grid_adjoint<3>, grid, dim3(256), st, P, acc, Vbar, gadj, step);
 }
 
+cudaError_t launch_grid_blocks(const Params& P, float4* acc, float4* V, ActiveBlocks blk, bool clear_acc,
+                               int step, int ctas, cudaStream_t st) {
+    return launch_chain(P, k_grid_blocks, dim3(ctas), dim3(256), st, P, acc, V, blk, clear_acc, step);
+}
+
+cudaError_t launch_grid_adjoint_blocks(const Params& P, const float4* acc, float4* Vbar, float4* gadj,
+                                       ActiveBlocks blk, int step, int ctas, cudaStream_t st) {
+    return launch_chain(P, k_grid_adjoint_blocks, dim3(ctas), dim3(256), st, P, acc, Vbar, gadj, blk, step);
+}
+
+cudaError_t launch_clear_blocks(const Params& P, float4* acc, long long acc_stride, ActiveBlocks blk, int n_sub,
+                                cudaStream_t st) {
+    if (n_sub <= 0) return cudaSuccess;
+    k_clear_blocks<<<dim3(32, n_sub), 256, 0, st>>>(P, acc, acc_stride, blk);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_state(int dim, const Params& P, const float* x0, const float* v0, float* s,
-                              int* id, cudaStream_t st) {
+                              int* id, float* x0c, cudaStream_t st) {
     if (P.n_total == 0) return cudaSuccess;
     dim3 grid(blocks_for(P.n_total, 256));
-    if (dim == 2) k_init_state<2><<<grid, 256, 0, st>>>(P, x0, v0, s, id);
-    else k_init_state<3><<<grid, 256, 0, st>>>(P, x0, v0, s, id);
+    if (dim == 2) k_init_state<2><<<grid, 256, 0, st>>>(P, x0, v0, s, id, x0c);
+    else k_init_state<3><<<grid, 256, 0, st>>>(P, x0, v0, s, id, x0c);
     return cudaGetLastError();
 }
 
@@ -300,19 +421,22 @@ cudaError_t launch_unpermute(int ncomp, const Params& P, const float* src, float
 }
 
 cudaError_t launch_to_input_order(int ncomp, const Params& P, const float* s, int c0,
-                                  const int* id, float* out, cudaStream_t st, int diag) {
+                                  const int* id, float* out, cudaStream_t st, int diag, const float* add) {
     if (P.n_total == 0) return cudaSuccess;
-    k_to_input_order<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, ncomp, s, c0, id, out, diag);
+    k_to_input_order<<<blocks_for(P.n_total, 256), 256, 0, st>>>(P, ncomp, s, c0, id, out, diag, add);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_design(int dim, const Params& P, const int* id, const int* inst_off,
                                  const int* dbase, const float* phi_d, const float* mag_d,
-                                 long long nd, float* phi, float* mag, cudaStream_t st) {
+                                 long long nd, float* phi, float* mag, const float* x0, float* x0c,
+                                 cudaStream_t st) {
     if (P.n_total == 0) return cudaSuccess;
     dim3 grid(blocks_for(P.n_total, 256));
-    if (dim == 2) k_gather_design<2><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, phi_d, mag_d, nd, phi, mag);
-    else k_gather_design<3><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, phi_d, mag_d, nd, phi, mag);
+    if (dim == 2)
+        k_gather_design<2><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, phi_d, mag_d, nd, phi, mag, x0, x0c);
+    else
+        k_gather_design<3><<<grid, 256, 0, st>>>(P, id, inst_off, dbase, phi_d, mag_d, nd, phi, mag, x0, x0c);
     return cudaGetLastError();
 }
 
@@ -336,26 +460,26 @@ cudaError_t launch_instance_mass(const Params& P, const float* phi, const int* i
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(int dim, const Params& P, const float* s, const float* target,
+cudaError_t launch_loss(int dim, const Params& P, const float* s, const float* x0, const float* target,
                         const int* id, const int* inst_off, const float* Minst, const float* mom,
                         float* loss_acc, float* loss_out, cudaStream_t st) {
     if (P.loss_kind == 0 && P.n_total > 0) {
         dim3 grid(blocks_for(P.n_total, 256));
-        if (dim == 2) k_loss_mse<2><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, loss_acc);
-        else k_loss_mse<3><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, loss_acc);
+        if (dim == 2) k_loss_mse<2><<<grid, 256, 0, st>>>(P, s, x0, target, id, inst_off, loss_acc);
+        else k_loss_mse<3><<<grid, 256, 0, st>>>(P, s, x0, target, id, inst_off, loss_acc);
     }
     k_loss_finalize<<<blocks_for(P.n_inst, 64), 64, 0, st>>>(P, inst_off, Minst, mom, loss_acc, loss_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed(int dim, const Params& P, const float* s, const float* target,
+cudaError_t launch_seed(int dim, const Params& P, const float* s, const float* x0, const float* target,
                         const int* id, const int* inst_off, const float* phi, const float* Minst,
                         const float* mom, const float* dloss, float* adj, float* gphi,
                         cudaStream_t st) {
     if (P.n_total == 0) return cudaSuccess;
     dim3 grid(blocks_for(P.n_total, 256));
-    if (dim == 2) k_seed<2><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, phi, Minst, mom, dloss, adj, gphi);
-    else k_seed<3><<<grid, 256, 0, st>>>(P, s, target, id, inst_off, phi, Minst, mom, dloss, adj, gphi);
+    if (dim == 2) k_seed<2><<<grid, 256, 0, st>>>(P, s, x0, target, id, inst_off, phi, Minst, mom, dloss, adj, gphi);
+    else k_seed<3><<<grid, 256, 0, st>>>(P, s, x0, target, id, inst_off, phi, Minst, mom, dloss, adj, gphi);
     return cudaGetLastError();
 }
 

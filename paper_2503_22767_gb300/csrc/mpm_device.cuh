@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 namespace mpm {
 
 constexpr float kMu0 = 1.25663706143591729e-6f;  // vacuum permeability 4 pi 1e-7
@@ -31,7 +33,6 @@ struct Params {
     float gravity[3];
     int pdl;  // per-substep kernels launched with programmatic dependent launch
     int adj_blocks;  // register budget of the adjoint particle kernel: 256-thread blocks per SM (2 or 3)
-    int box;         // 1: warps stage their stencil nodes in shared memory before gathering
     // solid boxes of Eq. 18 beyond the walls and a non-uniform applied field
     // (device memory), or null for neither.  One pointer keeps the parameter
     // block (and the transfer kernels' register allocation) as small as
@@ -69,6 +70,110 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // A hint to bring the line holding *p into L2 (the point of coherence, so it
 // is safe for data another kernel may still write); no register is used.
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+// The same into L1 (data no kernel writes while this one runs).
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// ---------------------------------------------------------------------------
+// active node blocks (3D): the grid operation and its reverse run only over
+// the blocks of kBlockEdge^3 nodes that some particle's stencil touches.
+// A list holds the blocks touched during the current checkpoint segment (it
+// only grows within the segment).  Each warp of 32 particles keeps the box of
+// base cells whose stencils it has listed (wbox); a substep whose particles
+// stay inside that box lists nothing, so most substeps cost the warp a few
+// reductions and one load.  Warps whose particles moved out of their box
+// list the blocks of the enlarged box.
+// ---------------------------------------------------------------------------
+constexpr int kBlockEdge = 4;
+
+struct ActiveBlocks {
+    int* flag = nullptr;   // [n_inst * blocks per instance]: 1 while the block is listed
+    int* list = nullptr;   // listed block ids (instance * blocks per instance + block)
+    int* count = nullptr;  // number of listed blocks
+    int4* wbox = nullptr;  // per warp: lo | (hi + 1) << 16 of the listed base cells per
+                           // axis (x, y, z); all zero = nothing listed yet
+};
+
+__host__ __device__ __forceinline__ int blocks_per_axis(int res) { return (res + kBlockEdge - 1) / kBlockEdge; }
+
+// Lists block b (on its first marking); every lane of the warp calls this,
+// with want = false where it has no block.  The warp appends its new blocks
+// with one atomic on the count.
+__device__ __forceinline__ void list_blocks(const ActiveBlocks& ab, bool want, int b) {
+    // a stale 0 from L1 only costs an atomic; the atomic swap decides
+    const bool mine = want && __ldcg(ab.flag + b) == 0 && atomicExch(ab.flag + b, 1) == 0;
+    const unsigned m = __ballot_sync(0xffffffffu, mine);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    int first = 0;
+    if (lane == __ffs(m) - 1) first = atomicAdd(ab.count, __popc(m));
+    first = __shfl_sync(0xffffffffu, first, __ffs(m) - 1);
+    if (mine) ab.list[first + __popc(m & ((1u << lane) - 1u))] = b;
+}
+
+// The rare part of mark_blocks, out of line so that its registers do not
+// burden the transfer kernels: list the blocks of the box lo..hi of base
+// cells (instance inst, or per lane when the warp spans two instances) and
+// record the box as this warp's.
+static __device__ __noinline__ void mark_blocks_slow(const ActiveBlocks& ab, bool active, int inst, int i_lo, int i_hi,
+                                              const int (&base)[3], const int (&lo)[3], const int (&hi)[3],
+                                              int res) {
+    const int nb = blocks_per_axis(res);
+    if (i_lo != i_hi) {
+        // a warp across two instances: each lane lists its own stencil's blocks
+        // (one or two blocks per axis), every substep
+        for (int c = 0; c < 8; ++c) {
+            const int i0 = base[0] / kBlockEdge + (c >> 2), i1 = base[1] / kBlockEdge + ((c >> 1) & 1);
+            const int i2 = base[2] / kBlockEdge + (c & 1);
+            const bool want = active && i0 <= (base[0] + 2) / kBlockEdge && i1 <= (base[1] + 2) / kBlockEdge &&
+                              i2 <= (base[2] + 2) / kBlockEdge;
+            list_blocks(ab, want, want ? (inst * nb + i0) * nb * nb + i1 * nb + i2 : 0);
+        }
+        return;
+    }
+    const int b0 = lo[0] / kBlockEdge, n0 = (hi[0] + 2) / kBlockEdge - b0 + 1;
+    const int b1 = lo[1] / kBlockEdge, n1 = (hi[1] + 2) / kBlockEdge - b1 + 1;
+    const int b2 = lo[2] / kBlockEdge, n2 = (hi[2] + 2) / kBlockEdge - b2 + 1;
+    const int total = n0 * n1 * n2;
+    const int lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < total; j0 += 32) {
+        const int j = j0 + lane;
+        const int i2 = j % n2, i1 = (j / n2) % n1, i0 = j / (n1 * n2);
+        list_blocks(ab, j < total, ((i_lo * nb + b0 + i0) * nb + b1 + i1) * nb + b2 + i2);
+    }
+    if (lane == 0) {
+        const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        ab.wbox[w] = make_int4(lo[0] | (hi[0] + 1) << 16, lo[1] | (hi[1] + 1) << 16, lo[2] | (hi[2] + 1) << 16, 0);
+    }
+}
+
+// Every lane of a warp calls this after its P2G, with the base node of its
+// stencil (active: the lane has a particle).  stored is this warp's wbox entry.
+__device__ __forceinline__ void mark_blocks(const ActiveBlocks& ab, bool active, int inst, const int (&base)[3],
+                                            int res, int4 stored) {
+    const unsigned full = 0xffffffffu;
+    const int i_lo = __reduce_min_sync(full, active ? inst : INT_MAX);
+    const int i_hi = __reduce_max_sync(full, active ? inst : INT_MIN);
+    if (i_lo > i_hi) return;  // no particle in this warp
+    int lo[3], hi[3];
+    const int st[3] = {stored.x, stored.y, stored.z};
+    bool covered = i_lo == i_hi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = __reduce_min_sync(full, active ? base[a] : INT_MAX);
+        hi[a] = __reduce_max_sync(full, active ? base[a] : INT_MIN);
+        covered = covered && st[a] != 0 && lo[a] >= (st[a] & 0xffff) && hi[a] + 1 <= (st[a] >> 16);
+    }
+    if (covered) return;
+    // the box grows to hold the old and the new cells
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (st[a] != 0) {
+            lo[a] = min(lo[a], st[a] & 0xffff);
+            hi[a] = max(hi[a], (st[a] >> 16) - 1);
+        }
+    }
+    mark_blocks_slow(ab, active, inst, i_lo, i_hi, base, lo, hi, res);
+}
 
 // Index of the instance owning particle p (instance ranges are contiguous
 // and survive the cell sort, whose key starts with the instance).

@@ -86,6 +86,8 @@ struct mpm_handle {
     float* adj2 = nullptr;
     float* phi_cur = nullptr;
     float* mag_cur = nullptr;
+    float* x0_fwd = nullptr;   // forward pass: initial positions in the current order [d][np]
+    float* x0_seg = nullptr;   // recomputation: the same per segment set [2][d][np]
     float* gphi_cur = nullptr;
     float* gmag_cur = nullptr;
     float* phi_d = nullptr;
@@ -116,10 +118,24 @@ struct mpm_handle {
     bool backward_done = false;
     float* d_bmotion = nullptr;          // their offsets and velocities per substep
 
+    // --- 3D: grid kernels over the listed node blocks (mpm::ActiveBlocks) ---
+    bool blocks = false;      // 3D: the P2G kernels mark and list the node blocks they touch
+    bool grid_blocks = true;  // option: the grid kernels walk the lists (else every node)
+    long long n_blocks = 0;   // node blocks over all instances
+    int grid_ctas = 0;        // persistent CTAs of the list-walking kernels
+    long long n_wbox = 0;     // warps of 32 particles
+    // lists (flags, list, count, per-warp boxes), each covering one checkpoint
+    // segment: 0 and 1 for the forward pass by segment parity, 2 and 3 for the
+    // two recomputation sets
+    int* blk_flag = nullptr;  // [4][n_blocks]
+    int* blk_list = nullptr;  // [4][n_blocks]
+    int* blk_count = nullptr; // [4]
+    int4* blk_wbox = nullptr; // [4][n_wbox]
+    bool seg_dirty = false;   // a backward pass ran over every node: the segment accumulators are not zero
+
     // --- options ---
     bool fuse_fwd = true;   // grid operation folded into the forward particle kernels
     bool fuse_adj = false;  // grid adjoint folded into the adjoint particle kernels
-    bool tile = false;      // shared-memory tiled transfers in the per-substep kernels
     bool graphs = true;   // replay the forward / backward passes as CUDA graphs
     bool v0_given = false;
 
@@ -434,8 +450,9 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     P.mu = (float)c->floor_mu;
     for (int i = 0; i < 3; ++i) P.gravity[i] = (float)c->gravity[i];
     P.pdl = 1;
-    P.adj_blocks = 2;
-    P.box = h->dim == 3 ? 1 : 0;  // measured: helps the 3D gathers, costs ~3% in 2D
+    // defaults as the autotuner picks them on the 2D and 3D workloads: the
+    // 80-register adjoint budget in 3D
+    P.adj_blocks = h->dim == 3 ? 3 : 2;
 
     const long long S = (long long)h->ncomp * h->np;
     const int d = h->dim;
@@ -464,6 +481,8 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->adj2, S);
     ALLOC(h->phi_cur, 2 * h->np);
     ALLOC(h->mag_cur, 2 * d * h->np);
+    ALLOC(h->x0_fwd, d * h->np);
+    ALLOC(h->x0_seg, 2 * d * h->np);
     ALLOC(h->gphi_cur, h->np);
     ALLOC(h->gmag_cur, d * h->np);
     ALLOC(h->phi_d, h->Nd);
@@ -494,11 +513,33 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->sb.counts, h->sb.n_keys);
     ALLOC(h->sb.offsets, h->sb.n_keys);
     ALLOC(h->sb.scan_tmp, h->sb.scan_tmp_len);
+    if (d == 3) {
+        const long long nb = mpm::blocks_per_axis(h->res);
+        h->blocks = true;
+        h->n_blocks = nb * nb * nb * h->n_inst;
+        int dev = 0, sms = 0;
+        MPM_CUDA(h, cudaGetDevice(&dev));
+        MPM_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        h->grid_ctas = 4 * std::max(1, sms);
+        h->n_wbox = h->np / 32;
+        ALLOC(h->blk_flag, 4 * h->n_blocks);
+        ALLOC(h->blk_list, 4 * h->n_blocks);
+        ALLOC(h->blk_count, 4);
+        ALLOC(h->blk_wbox, 4 * h->n_wbox);
+    }
 #undef ALLOC
     MPM_CUDA(h, cudaMemcpy(h->d_inst_off, h->inst_off.data(), sizeof(int) * (h->n_inst + 1),
                            cudaMemcpyHostToDevice));
     MPM_CUDA(h, cudaMemcpy(h->d_dbase, h->dbase.data(), sizeof(int) * h->n_inst,
                            cudaMemcpyHostToDevice));
+    if (h->blocks) {
+        // the recomputation finds its accumulators, flags and counts zero:
+        // every adjoint segment clears what its recomputation listed
+        MPM_CUDA(h, cudaMemset(h->seg_acc, 0, sizeof(float4) * 2 * h->total_nodes * h->K));
+        MPM_CUDA(h, cudaMemset(h->blk_flag, 0, sizeof(int) * 4 * h->n_blocks));
+        MPM_CUDA(h, cudaMemset(h->blk_count, 0, sizeof(int) * 4));
+        MPM_CUDA(h, cudaMemset(h->blk_wbox, 0, sizeof(int4) * 4 * h->n_wbox));
+    }
     // padding lanes of the state buffers stay finite
     MPM_CUDA(h, cudaMemset(h->stA, 0, sizeof(float) * S));
     MPM_CUDA(h, cudaMemset(h->stB, 0, sizeof(float) * S));
@@ -509,14 +550,9 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     return MPM_OK;
 }
 
-// The tiled kernels take the uniform field only; a field gradient uses the
-// direct kernels.
-// The tiled kernels carry no solid boxes and no field gradient: with either
-// set, the direct kernels run.
-bool use_tiles(const mpm_handle* h) { return h->tile && h->P.ext == nullptr; }
-
 StepArgs base_args(mpm_handle* h) {
     StepArgs a;
+    a.x0 = h->x0_fwd;
     a.phi = h->phi_cur;
     a.mag = h->mag_cur;
     a.field = h->field;
@@ -528,6 +564,29 @@ StepArgs base_args(mpm_handle* h) {
     a.gmag = h->gmag_cur;
     a.gfield = h->gfield_d;
     return a;
+}
+
+// node-block list i (3D): 0 and 1 for the forward pass, 2 + b for recomputation set b
+mpm::ActiveBlocks block_list(const mpm_handle* h, int i) {
+    mpm::ActiveBlocks b;
+    if (!h->blocks) return b;
+    b.flag = h->blk_flag + (long long)i * h->n_blocks;
+    b.list = h->blk_list + (long long)i * h->n_blocks;
+    b.count = h->blk_count + i;
+    b.wbox = h->blk_wbox + (long long)i * h->n_wbox;
+    return b;
+}
+
+// Empties list i: its flags (over the listed blocks), its count and the
+// warps' boxes; with acc, also zeroes n_sub accumulators (stride acc_stride)
+// over the listed blocks.
+int clear_list(mpm_handle* h, int i, float4* acc, long long acc_stride, int n_sub, cudaStream_t st) {
+    const mpm::ActiveBlocks b = block_list(h, i);
+    h->launches++;
+    MPM_CUDA(h, mpm::launch_clear_blocks(h->P, acc, acc_stride, b, std::max(1, n_sub), st));
+    MPM_CUDA(h, cudaMemsetAsync(b.count, 0, sizeof(int), st));
+    MPM_CUDA(h, cudaMemsetAsync(b.wbox, 0, sizeof(int4) * h->n_wbox, st));
+    return MPM_OK;
 }
 
 // copy src -> dst (device) unless they are the same buffer
@@ -552,6 +611,16 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
     MPM_CUDA(h, cudaMemsetAsync(h->loss_acc, 0, sizeof(float) * h->n_inst, st));
     if (fuse) MPM_CUDA(h, cudaMemsetAsync(h->acc3, 0, sizeof(float4) * 2 * G, st));
     else MPM_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(float4) * G, st));
+    // 3D with the grid kernel: the P2G kernels list the node blocks they
+    // touch, and the grid kernel walks the list.  Segment j uses list j & 1;
+    // its first P2G runs in the last kernel of segment j - 1, before the
+    // sort, so each list is emptied once the segment after it has begun.
+    const bool lists = h->blocks && !fuse && h->grid_blocks;
+    auto lean_blk = [&](int substep) { return block_list(h, (substep / h->K) & 1); };
+    if (lists) {
+        int rc0;
+        if ((rc0 = clear_list(h, 0, nullptr, 0, 1, st)) || (rc0 = clear_list(h, 1, nullptr, 0, 1, st))) return rc0;
+    }
 
     float* cur = h->stA;
     float* nxt = h->stB;
@@ -559,13 +628,15 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
     int* id_nxt = h->idB;
     const int T = h->tune_T > 0 ? std::min(h->T, h->tune_T) : h->T;
     const int n_seg = (T + h->K - 1) / h->K;
-    if ((rc = counted(h, 1, [&] { return mpm::launch_init_state(d, P, h->st_x0, h->st_v0, cur, id_cur, st); })))
+    if ((rc = counted(h, 1, [&] {
+             return mpm::launch_init_state(d, P, h->st_x0, h->st_v0, cur, id_cur, h->x0_fwd, st);
+         })))
         return rc;
     for (int seg = 0; seg < n_seg; ++seg) {
         const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T);
         // cell sort and reorder of the full state
         if ((rc = counted(h, 5, [&] {
-                 return mpm::launch_sort(d, P, cur, h->np, h->d_inst_off, h->sb, h->perm, h->d_err, st);
+                 return mpm::launch_sort(d, P, cur, h->np, h->d_inst_off, h->sb, h->perm, h->d_err, st, h->x0_fwd);
              })))
             return rc;
         if ((rc = counted(h, 1, [&] {
@@ -574,9 +645,16 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
             return rc;
         std::swap(cur, nxt);
         std::swap(id_cur, id_nxt);
+        // a new segment: the list of the last segment is done with, and the
+        // warps' boxes of this segment's list describe the old particle order
+        if (lists && seg > 0) {
+            if ((rc = clear_list(h, (seg - 1) & 1, nullptr, 0, 1, st))) return rc;
+            MPM_CUDA(h, cudaMemsetAsync(block_list(h, seg & 1).wbox, 0, sizeof(int4) * h->n_wbox, st));
+        }
         if ((rc = counted(h, 1, [&] {
                  return mpm::launch_gather_design(d, P, id_cur, h->d_inst_off, h->d_dbase, h->phi_d,
-                                                  h->mag_d, h->Nd, h->phi_cur, h->mag_cur, st);
+                                                  h->mag_d, h->Nd, h->phi_cur, h->mag_cur, h->st_x0,
+                                                  h->x0_fwd, st);
              })))
             return rc;
         MPM_CUDA(h, cudaMemcpyAsync(h->ck_state + S * seg, cur, sizeof(float) * S,
@@ -595,6 +673,7 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
             a.s_in = cur;
             a.acc = fuse ? acc3(0) : h->acc;
             a.n_p2g = 0;
+            if (lists) a.blk = lean_blk(0);
             if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
                      return mpm::launch_forward(d, false, true, false, fuse, P, a, h->block, st);
                  })))
@@ -602,6 +681,8 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
         }
         for (int n = s0; n < s1; ++n) {
             if (!fuse && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
+                              if (lists)
+                                  return mpm::launch_grid_blocks(P, h->acc, h->V, lean_blk(n), true, n, h->grid_ctas, st);
                               return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, n, st);
                           })))
                 return rc;
@@ -621,16 +702,16 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
                 a.acc = h->acc;
             }
             if (!p2g) a.acc = nullptr;
+            if (lists && p2g) a.blk = lean_blk(n + 1);
             if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, all ? kFusedStore : kFused), st, [&] {
-                     return use_tiles(h) ? mpm::launch_forward_tiled(d, all, fuse, P, a, h->block, st)
-                                    : mpm::launch_forward(d, true, p2g, all, fuse, P, a, h->block, st);
+                     return mpm::launch_forward(d, true, p2g, all, fuse, P, a, h->block, st);
                  })))
                 return rc;
             std::swap(cur, nxt);
         }
     }
     if ((rc = counted(h, 2, [&] {
-             return mpm::launch_loss(d, P, cur, h->target, id_cur, h->d_inst_off, h->Minst, h->mom,
+             return mpm::launch_loss(d, P, cur, h->x0_fwd, h->target, id_cur, h->d_inst_off, h->Minst, h->mom,
                                      h->loss_acc, h->st_loss, st);
          })))
         return rc;
@@ -652,6 +733,8 @@ struct SegSet {
     float4* V;      // [K] grid velocities
     float* phi;     // current-order design of the segment
     float* mag;
+    float* x0;      // current-order initial positions of the segment
+    int list_id;    // 3D: its node-block list (block_list)
 };
 
 SegSet seg_set(mpm_handle* h, int b) {
@@ -663,6 +746,8 @@ SegSet seg_set(mpm_handle* h, int b) {
     ss.V = h->seg_V + (long long)b * G * h->K;
     ss.phi = h->phi_cur + (long long)b * h->np;
     ss.mag = h->mag_cur + (long long)b * h->dim * h->np;
+    ss.x0 = h->x0_seg + (long long)b * h->dim * h->np;
+    ss.list_id = 2 + b;
     return ss;
 }
 
@@ -682,16 +767,22 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
                                 cudaMemcpyDeviceToDevice, st));
     if ((rc = counted(h, 1, [&] {
              return mpm::launch_gather_design(d, P, id_seg, h->d_inst_off, h->d_dbase, h->phi_d,
-                                              h->mag_d, h->Nd, ss.phi, ss.mag, st);
+                                              h->mag_d, h->Nd, ss.phi, ss.mag, h->st_x0, ss.x0, st);
          })))
         return rc;
-    MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * G * ((fuse_rec && Ks >= 2) ? 2 : 1), st));
+    // with node-block lists, the accumulators are zero where the last use of
+    // this set listed blocks (its adjoint cleared them), and zero elsewhere since
+    const bool lists = h->blocks && h->grid_blocks;
+    if (!lists)
+        MPM_CUDA(h, cudaMemsetAsync(gacc(0), 0, sizeof(float4) * G * ((fuse_rec && Ks >= 2) ? 2 : 1), st));
     StepArgs a = base_args(h);
     a.phi = ss.phi;
     a.mag = ss.mag;
+    a.x0 = ss.x0;
     a.s_in = state(0);
     a.acc = gacc(0);
     a.n_p2g = s0;
+    if (lists) a.blk = block_list(h, ss.list_id);
     if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFirstP2G), st, [&] {
              return mpm::launch_forward(d, false, true, false, fuse_rec, P, a, h->block, st);
          })))
@@ -701,17 +792,22 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
         const bool p2g = k + 1 < Ks;
         float4* next_acc = p2g ? gacc(k + 1) : nullptr;
         if (!fuse_rec && (rc = timed(h, kGrid, 48.0 * G, st, [&] {
+                          if (lists)
+                              return mpm::launch_grid_blocks(P, gacc(k), gV(k), block_list(h, ss.list_id), false, n,
+                                                             h->grid_ctas, st);
                           return mpm::launch_grid(d, P, gacc(k), gV(k), next_acc, false, n, st);
                       })))
             return rc;
         a = base_args(h);
         a.phi = ss.phi;
         a.mag = ss.mag;
+        a.x0 = ss.x0;
         a.s_in = state(k);
         a.s_out = state(k + 1);
         a.acc = next_acc;
         a.n_g2p = n;
         a.n_p2g = n + 1;
+        if (p2g && lists) a.blk = block_list(h, ss.list_id);
         if (fuse_rec) {
             a.accG = gacc(k);
             a.zero4 = k + 2 < Ks ? gacc(k + 2) : nullptr;
@@ -720,8 +816,7 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
             a.V = gV(k);
         }
         if ((rc = timed(h, kFwdParticle, h->N * particle_bytes(d, kFwdParticle, kFusedStore), st, [&] {
-                 return use_tiles(h) ? mpm::launch_forward_tiled(d, true, fuse_rec, P, a, h->block, st)
-                                : mpm::launch_forward(d, true, p2g, true, fuse_rec, P, a, h->block, st);
+                 return mpm::launch_forward(d, true, p2g, true, fuse_rec, P, a, h->block, st);
              })))
             return rc;
     }
@@ -744,10 +839,18 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
     auto gacc = [&](int k) { return ss.acc + G * k; };
     auto gV = [&](int k) { return ss.V + G * k; };
     auto vb3 = [&](int i) { return h->Vbar3 + G * (((i % 3) + 3) % 3); };
+    // the grid adjoint of substep n = s0 + k: over the node blocks its P2G listed (3D), or every node
+    auto grid_adjoint = [&](int k, int n) {
+        if (h->blocks && h->grid_blocks)
+            return mpm::launch_grid_adjoint_blocks(P, gacc(k), h->Vbar, h->gadj, block_list(h, ss.list_id), n,
+                                                   h->grid_ctas, st);
+        return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, n, st);
+    };
     auto args = [&]() {
         StepArgs a = base_args(h);
         a.phi = ss.phi;
         a.mag = ss.mag;
+        a.x0 = ss.x0;
         a.adj = adj;
         a.mom = h->mom;
         return a;
@@ -758,7 +861,7 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
     // --- adjoint of the state at the segment end ---
     if (s1 == T) {
         if ((rc = counted(h, 1, [&] {
-                 return mpm::launch_seed(d, P, state(Ks), h->target, id_seg, h->d_inst_off, ss.phi,
+                 return mpm::launch_seed(d, P, state(Ks), ss.x0, h->target, id_seg, h->d_inst_off, ss.phi,
                                          h->Minst, h->mom, h->dloss, adj, h->gphi_cur, st);
              })))
             return rc;
@@ -788,9 +891,7 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
         return rc;
     for (int k = Ks - 1; k >= 1; --k) {
         const int n = s0 + k;
-        if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
-                          return mpm::launch_grid_adjoint(d, P, gacc(k), h->Vbar, h->gadj, n, st);
-                      })))
+        if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] { return grid_adjoint(k, n); })))
             return rc;
         a = args();
         a.s_in = state(k);
@@ -809,14 +910,11 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
         if (fuse_v) a.accG = gacc(k - 1);
         else a.V = gV(k - 1);
         if ((rc = timed(h, kAdjParticle, h->N * particle_bytes(d, kAdjParticle, kFused), st, [&] {
-                 return use_tiles(h) ? mpm::launch_adjoint_tiled(d, fuse, fuse_v, P, a, h->block, st)
-                                : mpm::launch_adjoint(d, true, true, fuse, fuse_v, P, a, h->block, st);
+                 return mpm::launch_adjoint(d, true, true, fuse, fuse_v, P, a, h->block, st);
              })))
             return rc;
     }
-    if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] {
-                      return mpm::launch_grid_adjoint(d, P, gacc(0), h->Vbar, h->gadj, s0, st);
-                  })))
+    if (!fuse && (rc = timed(h, kGridAdj, 64.0 * G, st, [&] { return grid_adjoint(0, s0); })))
         return rc;
     a = args();
     a.s_in = state(0);
@@ -833,10 +931,17 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
              return mpm::launch_adjoint(d, true, false, fuse, fuse_v, P, a, h->block, st);
          })))
         return rc;
-    return counted(h, 1, [&] {
-        return mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase, h->gphi_cur,
-                                               h->gmag_cur, h->Nd, h->gphi_d, h->gmag_d, st);
-    });
+    if ((rc = counted(h, 1, [&] {
+             return mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase, h->gphi_cur,
+                                                    h->gmag_cur, h->Nd, h->gphi_d, h->gmag_d, st);
+         })))
+        return rc;
+    if (h->blocks && h->grid_blocks) {
+        // leave this segment set as its next recomputation expects it: the
+        // accumulators zero over the listed blocks, flags and counts zero
+        if ((rc = clear_list(h, ss.list_id, ss.acc, G, Ks, st))) return rc;
+    }
+    return MPM_OK;
 }
 
 int backward_pass(mpm_handle* h, cudaStream_t st) {
@@ -963,7 +1068,7 @@ int forward_impl(mpm_handle* h, const float* x0, const float* v0, const float* p
     if ((rc = dcopy(h, loss_out, h->st_loss, sizeof(float) * h->n_inst, st))) return rc;
     if (x_out) {
         h->launches++;
-        MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, x_out, st));
+        MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, x_out, st, 0, h->x0_fwd));
     }
     rc = finish(h, 0, st);
     if (rc != MPM_OK) return rc;
@@ -978,7 +1083,17 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
     const int d = h->dim;
     int rc;
     if ((rc = dcopy(h, h->dloss, dloss, sizeof(float) * h->n_inst, st))) return rc;
+    if (h->blocks && h->grid_blocks && h->seg_dirty) {
+        // the last backward pass ran over every node and left the segment
+        // accumulators set; the lists expect them zero
+        MPM_CUDA(h, cudaMemsetAsync(h->seg_acc, 0, sizeof(float4) * 2 * h->total_nodes * h->K, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->blk_flag + 2 * h->n_blocks, 0, sizeof(int) * 2 * h->n_blocks, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->blk_count + 2, 0, sizeof(int) * 2, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->blk_wbox + 2 * h->n_wbox, 0, sizeof(int4) * 2 * h->n_wbox, st));
+        h->seg_dirty = false;
+    }
     if ((rc = run_pass(h, 1, st))) return rc;
+    if (h->blocks && !h->grid_blocks) h->seg_dirty = true;
     if (g_phi && (rc = dcopy(h, g_phi, h->gphi_d, sizeof(float) * h->Nd, st))) return rc;
     if (g_mag && (rc = dcopy(h, g_mag, h->gmag_d, sizeof(float) * d * h->Nd, st))) return rc;
     if (g_field && (rc = dcopy(h, g_field, h->gfield_d, sizeof(float) * h->n_inst * h->T * d, st)))
@@ -992,7 +1107,7 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
 // autotuner: time candidate launch configurations, keep the fastest
 // ---------------------------------------------------------------------------
 struct TuneChoice {
-    int block, fuse, tile, adj, box;
+    int block, fuse, adj;
     double ms;
 };
 
@@ -1017,9 +1132,9 @@ bool cache_lookup(const char* path, const std::string& sig, TuneChoice* out) {
         if (!p) continue;
         TuneChoice c{};
         if (std::sscanf(p + key.size(),
-                        "{\"block\": %d, \"fuse\": %d, \"tile\": %d, \"adj\": %d, \"box\": %d, \"ms\": %lf}",
-                        &c.block, &c.fuse, &c.tile, &c.adj, &c.box, &c.ms) == 6 &&
-            c.adj >= 2 && c.adj <= 4 && (c.box == 0 || c.box == 1)) {
+                        "{\"block\": %d, \"fuse\": %d, \"adj\": %d, \"ms\": %lf}",
+                        &c.block, &c.fuse, &c.adj, &c.ms) == 4 &&
+            c.adj >= 2 && c.adj <= 4) {
             *out = c;
             found = true;
         }
@@ -1044,8 +1159,8 @@ void cache_store(const char* path, const std::string& sig, const TuneChoice& c) 
     }
     char buf[512];
     std::snprintf(buf, sizeof buf,
-                  "  \"%s\": {\"block\": %d, \"fuse\": %d, \"tile\": %d, \"adj\": %d, \"box\": %d, \"ms\": %.4f}",
-                  sig.c_str(), c.block, c.fuse, c.tile, c.adj, c.box, c.ms);
+                  "  \"%s\": {\"block\": %d, \"fuse\": %d, \"adj\": %d, \"ms\": %.4f}",
+                  sig.c_str(), c.block, c.fuse, c.adj, c.ms);
     lines.push_back(buf);
     std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
@@ -1062,9 +1177,7 @@ void apply_choice(mpm_handle* h, const TuneChoice& c) {
     h->block = c.block;
     h->fuse_fwd = (c.fuse & 1) != 0;
     h->fuse_adj = (c.fuse & 2) != 0;
-    h->tile = c.tile != 0;
     h->P.adj_blocks = c.adj;
-    h->P.box = c.box;
 }
 
 int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cudaStream_t st,
@@ -1090,9 +1203,9 @@ int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cu
         for (int fuse : {0, 1}) {
             // register budgets: 2 and 3 blocks per SM, and 4 in 2D
             const int n_adj = h->dim == 2 ? 3 : 2;
-            for (int cand = 0; cand < 2 * n_adj; ++cand) {
-                const int adj = 2 + cand % n_adj, box = cand / n_adj;
-                TuneChoice c{block, fuse, 0, adj, box, 0.0};
+            for (int cand = 0; cand < n_adj; ++cand) {
+                const int adj = 2 + cand;
+                TuneChoice c{block, fuse, adj, 0.0};
                 apply_choice(h, c);
                 h->tune_T = sample;
                 // first run captures the graphs; then time the best of 3
@@ -1119,6 +1232,7 @@ int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cu
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (h->blocks && !h->grid_blocks) h->seg_dirty = true;
     h->tune_T = 0;
     h->timing_stride = saved_timing;
     h->graphs = saved_graphs;
@@ -1268,10 +1382,24 @@ int mpm_read_state(mpm_handle* h, float* x, float* v, float* C, float* F, void* 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int d = h->dim;
     const Params& P = h->P;
-    if (x) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, x, st));
+    if (x) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, x, st, 0, h->x0_fwd));
     if (v) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, d, h->id_cur, v, st));
     if (C) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d, h->id_cur, C, st));
     if (F) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d + d * d, h->id_cur, F, st, d));
+    MPM_CUDA(h, cudaStreamSynchronize(st));
+    return MPM_OK;
+}
+
+int mpm_read_state_strain(mpm_handle* h, float* u, float* v, float* C, float* E, void* cuda_stream) {
+    if (!h) return MPM_ERR_ARG;
+    if (!h->forward_done) return fail(h, MPM_ERR_STATE, "no forward result to read");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int d = h->dim;
+    const Params& P = h->P;
+    if (u) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, 0, h->id_cur, u, st));
+    if (v) MPM_CUDA(h, mpm::launch_to_input_order(d, P, h->cur, d, h->id_cur, v, st));
+    if (C) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d, h->id_cur, C, st));
+    if (E) MPM_CUDA(h, mpm::launch_to_input_order(d * d, P, h->cur, 2 * d + d * d, h->id_cur, E, st));
     MPM_CUDA(h, cudaStreamSynchronize(st));
     return MPM_OK;
 }
@@ -1373,15 +1501,10 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             h->fuse_fwd = (value & 1) != 0;
             h->fuse_adj = (value & 2) != 0;
             return MPM_OK;
-        case MPM_OPT_TILE:
-            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "tile must be 0 or 1");
-            if (h->tile != (value == 1)) drop_graphs(h);
-            h->tile = value == 1;
-            return MPM_OK;
-        case MPM_OPT_WARP_BOX:
-            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "warp box must be 0 or 1");
-            if (h->P.box != (int)value) drop_graphs(h);
-            h->P.box = (int)value;
+        case MPM_OPT_GRID_BLOCKS:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "grid blocks must be 0 or 1");
+            if (h->grid_blocks != (value == 1)) drop_graphs(h);
+            h->grid_blocks = value == 1;
             return MPM_OK;
         case MPM_OPT_ADJOINT_BLOCKS:
             if (value < 2 || value > 4) return fail(h, MPM_ERR_ARG, "adjoint blocks must be 2, 3 or 4");
@@ -1426,11 +1549,10 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_BLOCK: *value = h->block; return MPM_OK;
         case MPM_OPT_FUSE_GRID: *value = (h->fuse_fwd ? 1 : 0) | (h->fuse_adj ? 2 : 0); return MPM_OK;
         case MPM_OPT_GRAPHS: *value = h->graphs ? 1 : 0; return MPM_OK;
-        case MPM_OPT_TILE: *value = h->tile ? 1 : 0; return MPM_OK;
         case MPM_OPT_STREAMS: *value = h->two_streams ? 2 : 1; return MPM_OK;
         case MPM_OPT_PDL: *value = h->P.pdl; return MPM_OK;
         case MPM_OPT_ADJOINT_BLOCKS: *value = h->P.adj_blocks; return MPM_OK;
-        case MPM_OPT_WARP_BOX: *value = h->P.box; return MPM_OK;
+        case MPM_OPT_GRID_BLOCKS: *value = h->grid_blocks ? 1 : 0; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

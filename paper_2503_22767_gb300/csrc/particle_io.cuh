@@ -80,6 +80,18 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ s, int base, 
     for (int a = 0; a < D; ++a) v[a] = s[(long long)(base + a) * np + p];
 }
 
+// Position of particle p: the X slot of the state plus x0 (the state holds
+// the displacement u = x - x0; x0 null: the slot holds x itself).
+template <int D>
+__device__ __forceinline__ void load_position(const float* __restrict__ s, const float* __restrict__ x0,
+                                              long long np, int p, float (&x)[D]) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float u = s[(long long)a * np + p];
+        x[a] = x0 ? __fadd_rn(u, __ldg(x0 + (long long)a * np + p)) : u;
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void load_mat(const float* __restrict__ s, int base, long long np, int p,
                                          float (&M)[D][D]) {

@@ -23,7 +23,7 @@
 
 #include "kernels.h"
 #include "particle_io.cuh"
-#include "warp_box.cuh"
+#include "warp_scatter.cuh"
 
 namespace mpm {
 
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
     // the P2G scatter is aggregated over the lanes of one cell (scatter_aggregated)
     constexpr bool AGG = P2G && aggregate_scatter<D>();
     // per warp (dynamic shared memory, warp_slots<D, P2G>() float4 per
-    // warp): the staged gather box of G2P, then the scatter slab of P2G
+    // warp): the scatter slab of P2G
     constexpr int kSlots = warp_slots<D, P2G>();
     extern __shared__ float4 s_warp[];
     float4* sm = s_warp + (threadIdx.x >> 5) * kSlots;
@@ -69,10 +69,20 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
     const long long np = P.np;
     int flags = 0;
-    float x[D], v[D], C[D][D], F[D][D];
+    // x: the X slot (the displacement u = x - x0 when a.x0 is set); every
+    // stencil and field evaluation uses the position x0 + u (pos below)
+    // xo: x0 (0 without a.x0), loaded with the state for G2P and again after
+    // the G2P node loop for P2G, so that it holds no registers in the loop
+    float x[D], v[D], C[D][D], F[D][D], xo[D];
     float phi = 0.0f, mp = 0.0f;
+    auto position = [&](float (&pos)[D]) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) pos[i] = __fadd_rn(x[i], xo[i]);
+    };
     auto load_state = [&]() {
         load_vec<D>(a.s_in, L::X, np, p, x);
+#pragma unroll
+        for (int i = 0; i < D; ++i) xo[i] = a.x0 ? __ldg(a.x0 + (long long)i * np + p) : 0.0f;
         load_mat<D>(a.s_in, L::F, np, p, F);
         phi = a.phi[p];
         mp = phi * P.rho0 * P.p_vol;  // Eq. 33
@@ -91,20 +101,12 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
         Stencil<D> s;
 #pragma unroll
         for (int i = 0; i < D; ++i) s.base[i] = 0;
-        if (active && !make_stencil<D>(x, P, s)) flags |= kErrDomain;
-        const float4* __restrict__ Vg = FUSE ? a.accG : a.V;
-        const WarpBox<D> box = warp_box<D>(s.base, active, inst, P.box != 0);
-        if (box.use) {
-            const float4* __restrict__ Vb = Vg + (long long)box.inst * P.nodes;
-            stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
-                const float4 g = __ldg(Vb + node);
-                if (!FUSE) return g;
-                float mv[D], gv[D];
-                unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                grid_velocity<D, EXT>(P, c, g.x, mv, gv, a.n_g2p);  // Eq. 16-18 once per node
-                return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
-            });
+        if (active) {
+            float pos[D];
+            position(pos);
+            if (!make_stencil<D>(pos, P, s)) flags |= kErrDomain;
         }
+        const float4* __restrict__ Vg = FUSE ? a.accG : a.V;
         if (active) {
             const float4* __restrict__ Vi = Vg + (long long)inst * P.nodes;
             // Eq. 19-20 with x_i - x_p = (o - r) dx for stencil offset o:
@@ -119,58 +121,50 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
             // (hv = sum w_l V, hv2 = sum o_l w_l V), then each row is weighted
             // by the product pw of the other axes' weights.
             const int nb = base_node<D>(s, P.res);
-            const int sb = box.use ? box_slot<D>(box, s.base) : 0;
             float hv[D], hv2[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) hv[i] = hv2[i] = 0.0f;
-            // the node loop, compiled once with the warp box and once without, so a
-            // warp runs a branch-free copy (and the instruction cache holds one)
-            auto node_loop = [&](auto box_c) {
-                constexpr bool kBox = decltype(box_c)::value;
 #pragma unroll
-                for (int k = 0; k < stencil_size<D>(); ++k) {
-                    const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
-                    const int ol = stencil_offset<D>(k, D - 1);
-                    float gv[D];
-                    if (kBox) {
-                        unpack3<D>(sm[sb + box_offset<D>(k)], gv);
-                    } else {
-                        NodeTerm<D> t;
-                        t.node = nb + node_offset<D>(k, P.res);
+            for (int k = 0; k < stencil_size<D>(); ++k) {
+                const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
+                const int ol = stencil_offset<D>(k, D - 1);
+                float gv[D];
+                NodeTerm<D> t;
+                t.node = nb + node_offset<D>(k, P.res);
 #pragma unroll
-                        for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
-                        node_velocity<D, FUSE, EXT>(Vi, t, P, gv, a.n_g2p);
-                    }
-                    const float wl = s.w[D - 1][ol];
+                for (int e = 0; e < D; ++e) t.c[e] = s.base[e] + stencil_offset<D>(k, e);
+                node_velocity<D, FUSE, EXT>(Vi, t, P, gv, a.n_g2p);
+                const float wl = s.w[D - 1][ol];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float wv = wl * gv[i];
+                    hv[i] = ol == 0 ? wv : hv[i] + wv;
+                    if (ol == 0) hv2[i] = 0.0f;
+                    else hv2[i] = add_offset(hv2[i], ol, wv);
+                }
+                if (ol == 2) {  // the row is complete
+                    const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
 #pragma unroll
                     for (int i = 0; i < D; ++i) {
-                        const float wv = wl * gv[i];
-                        hv[i] = ol == 0 ? wv : hv[i] + wv;
-                        if (ol == 0) hv2[i] = 0.0f;
-                        else hv2[i] = add_offset(hv2[i], ol, wv);
-                    }
-                    if (ol == 2) {  // the row is complete
-                        const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
-#pragma unroll
-                        for (int i = 0; i < D; ++i) {
-                            const float hp = pw * hv[i];
-                            v[i] += hp;
-                            C[i][D - 1] += pw * hv2[i];
-                            C[i][0] = add_offset(C[i][0], o0, hp);
-                            if (D == 3) C[i][1 % D] = add_offset(C[i][1 % D], om, hp);
-                        }
+                        const float hp = pw * hv[i];
+                        v[i] += hp;
+                        C[i][D - 1] += pw * hv2[i];
+                        C[i][0] = add_offset(C[i][0], o0, hp);
+                        if (D == 3) C[i][1 % D] = add_offset(C[i][1 % D], om, hp);
                     }
                 }
-            };
-            if (box.use) node_loop(std::true_type{});
-            else node_loop(std::false_type{});
+            }
+            if (P2G && a.x0) {  // x0 again for the P2G position; the load overlaps the G2P tail
+#pragma unroll
+                for (int i = 0; i < D; ++i) xo[i] = reload(a.x0 + (long long)i * np + p);
+            }
             float Fn[D][D];
             const float c4 = 4.0f * P.inv_dx;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
 #pragma unroll
                 for (int j = 0; j < D; ++j) C[i][j] = c4 * (C[i][j] - v[i] * s.r[j]);
-                x[i] += P.dt * v[i];                              // Eq. 21
+                x[i] += P.dt * v[i];                              // Eq. 21 (on u = x - x0)
             }
             // Eq. 22 in strain form: E' = E + dt C (I + E)
 #pragma unroll
@@ -200,12 +194,16 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
             warp_add_per_instance<1>(mom_x, inst, a.mom + (long long)a.n_g2p * P.n_inst, 1);
     }
     if (P2G) {
+        // this warp's box of listed cells, read after the scatter (3D)
+        if (D == 3 && a.blk.flag != nullptr) prefetch_l1(a.blk.wbox + (p >> 5));
         Stencil<D> s;
         float A[D][D], u[D];
         int nb = 0;
         float4* __restrict__ ai = a.acc + (long long)(active ? inst : 0) * P.nodes;
         if (active) {
-            if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
+            float pos[D];
+            position(pos);
+            if (!make_stencil<D>(pos, P, s)) flags |= kErrDomain;
             StressParts<D> S;
             stress_parts<D>(F, phi, P, S);
             if (!(S.J > 0.0f)) flags |= kErrNumeric;
@@ -217,7 +215,7 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
             }
             if (EXT && P.ext->fgrad) {
                 const float* Gn = P.ext->fgrad + ((long long)inst * P.n_steps + a.n_p2g) * D * D;
-                field_at_particle<D>(Gn, x, Ba);
+                field_at_particle<D>(Gn, pos, Ba);
                 // body force of the non-uniform field, folded into the momentum
                 // m v (f and m both vanish with phi, so m > 0 whenever f != 0)
                 float f[D];
@@ -280,6 +278,11 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
                 }
                 return pack4<D>(w * mp, mv);
             });
+            // the warp lists the node blocks its stencils reach beyond its box
+            // (a.blk is uniform over the launch, so the whole warp takes part)
+            if constexpr (D == 3) {
+                if (a.blk.flag != nullptr) mark_blocks(a.blk, active, inst, s.base, P.res, a.blk.wbox[p >> 5]);
+            }
         } else if (active) {
             float pw = 0.0f, Ug[D];  // per row: product of the other axes' weights, u + dx A o
 #pragma unroll
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     float Cn[D][D];  // C of state n (= m+1), needed by G2P^T
     float x_n[D], v_n[D], F_n[D][D], phi_n = 0.0f;  // state n and design (P2G^T)
     auto load_state_n = [&]() {
-        load_vec<D>(a.s_in, L::X, np, p, x_n);
+        load_position<D>(a.s_in, a.x0, np, p, x_n);  // the position x0 + u
         load_vec<D>(a.s_in, L::V, np, p, v_n);
         load_mat<D>(a.s_in, L::C, np, p, Cn);
         load_mat<D>(a.s_in, L::F, np, p, F_n);
@@ -366,11 +369,8 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     pdl_trigger();
     clear_buffer(a);
     if (P2GT && !kEarly && active) load_state_n();
-    // warps with every lane active may stage their stencil nodes (the staging
-    // runs inside the per-particle branches)
-    const bool full_warp = __ballot_sync(0xffffffffu, active) == 0xffffffffu;
     // per warp (dynamic shared memory, warp_slots<D, G2PT>() float4 per
-    // warp): the staged gather boxes, then the scatter slab of G2P^T
+    // warp): the scatter slab of G2P^T
     constexpr bool AGG = G2PT && aggregate_scatter<D>();
     constexpr int kSlots = warp_slots<D, G2PT>();
     extern __shared__ float4 s_warp[];
@@ -444,20 +444,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
             }
             const float4* __restrict__ gi = (FUSE ? a.accP : a.gadj) + (long long)inst * P.nodes;
             const float4* __restrict__ vbi = FUSE ? a.VbarIn + (long long)inst * P.nodes : nullptr;
-            const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
-            if (box.use)
-                stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
-                    const float4 g = __ldg(gi + node);
-                    if (!FUSE) return g;
-                    // grid adjoint (reverse of Eq. 16-18) once per node
-                    float mv[D], vbv[D], mbv, mvb[D];
-                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                    unpack3<D>(__ldg(vbi + node), vbv);
-                    grid_velocity_adjoint<D, EXT>(P, c, g.x, mv, vbv, mbv, mvb, a.n_p2g);
-                    return make_float4(mbv, mvb[0], mvb[1], D == 3 ? mvb[D - 1] : 0.0f);
-                });
             const int nb = base_node<D>(s, P.res);
-            const int sb = box.use ? box_slot<D>(box, s.base) : 0;
             float S0[D], T[D][D], mbs = 0.0f, xg[D];
             // partial sums over the last axis (h*) and, in 3D, the middle axis (l*)
             float Ug[D], hv[D], hv2[D], hm = 0.0f, ha = 0.0f, hb = 0.0f, la = 0.0f, lb = 0.0f, lc = 0.0f;
@@ -467,10 +454,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
 #pragma unroll
                 for (int j = 0; j < D; ++j) T[i][j] = 0.0f;
             }
-            // the node loop, compiled once with the warp box and once without, so a
-            // warp runs a branch-free copy (and the instruction cache holds one)
-            auto node_loop = [&](auto box_c) {
-                constexpr bool kBox = decltype(box_c)::value;
+            auto node_loop = [&]() {
 #pragma unroll
                 for (int k = 0; k < stencil_size<D>(); ++k) {
                     const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
@@ -487,10 +471,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     }
                     float4 g;
                     float mvb[D];
-                    if (kBox) {
-                        g = sm[sb + box_offset<D>(k)];
-                        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mvb);
-                    } else if (FUSE) {
+                    if (FUSE) {
                         const int node = nb + node_offset<D>(k, P.res);
                         g = __ldg(gi + node);
                         // grid adjoint (reverse of Eq. 16-18) of this node, on the fly
@@ -554,8 +535,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     }
                 }
             };
-            if (box.use) node_loop(std::true_type{});
-            else node_loop(std::false_type{});
+            node_loop();
             // The node loop needs none of C, E, the stress (all used for A
             // before it) and Fbar of state n: they are read again, and the
             // stress recomputed, here, so their registers are free during the
@@ -688,7 +668,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                 load_mat<D>(a.s_in, L::C, np, p, Cn);
             }
             float x[D], F[D][D];
-            load_vec<D>(a.s_aux, L::X, np, p, x);
+            load_position<D>(a.s_aux, a.x0, np, p, x);  // the position x0 + u
             load_mat<D>(a.s_aux, L::F, np, p, F);
             if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
             // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
@@ -710,16 +690,6 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                 }
             store_mat<D>(a.adj, L::F, np, p, Fo);  // complete: the stencil sums add nothing to it
             const float4* __restrict__ Vi = (FUSE_V ? a.accG : a.V) + (long long)inst * P.nodes;
-            const WarpBox<D> box = warp_box<D>(s.base, true, inst, P.box != 0 && full_warp);
-            if (box.use)
-                stage_box<D>(box, P.res, sm, [&](const int (&c)[D], int node) {
-                    const float4 g = __ldg(Vi + node);
-                    if (!FUSE_V) return g;
-                    float mv[D], gv[D];
-                    unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                    grid_velocity<D, EXT>(P, c, g.x, mv, gv, a.n_p2g - 1);  // Eq. 16-18 once per node
-                    return make_float4(gv[0], gv[1], D == 3 ? gv[D - 1] : 0.0f, 0.0f);
-                });
             // Eq. 19-20 reversed (v' = sum w V, C' = kappa sum w V dpos^T) with
             // dpos = (o - r) dx: the node's velocity adjoint is w sv,
             //   sv = vt + kappa Ct dpos = q + kappa dx Ct o,  q = vt - kappa dx Ct r,
@@ -738,14 +708,10 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                 q[i] = vt[i] - kdx * cr;
             }
             nb = base_node<D>(s, P.res);
-            const int sb = box.use ? box_slot<D>(box, s.base) : 0;
             float xg[D], vs[D], Sg[D], hv[D], pw = 0.0f, ha = 0.0f, hb = 0.0f, la = 0.0f, lb = 0.0f, lc = 0.0f;
 #pragma unroll
             for (int i = 0; i < D; ++i) xg[i] = vs[i] = Sg[i] = hv[i] = 0.0f;
-            // the node loop, compiled once with the warp box and once without, so a
-            // warp runs a branch-free copy (and the instruction cache holds one)
-            auto node_loop = [&](auto box_c) {
-                constexpr bool kBox = decltype(box_c)::value;
+            auto node_loop = [&]() {
 #pragma unroll
                 for (int k = 0; k < stencil_size<D>(); ++k) {
                     const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
@@ -763,9 +729,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     }
                     const int node = nb + node_offset<D>(k, P.res);
                     float gv[D];
-                    if (kBox) {
-                        unpack3<D>(sm[sb + box_offset<D>(k)], gv);
-                    } else {
+                    {
                         NodeTerm<D> t;
                         t.node = node;
 #pragma unroll
@@ -810,8 +774,7 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
                     }
                 }
             };
-            if (box.use) node_loop(std::true_type{});
-            else node_loop(std::false_type{});
+            node_loop();
             // kappa Ct^T vs = (dC vs) / dx
 #pragma unroll
             for (int c = 0; c < D; ++c) {

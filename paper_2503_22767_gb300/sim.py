@@ -157,6 +157,20 @@ class Simulator:
         self._check(st, "mpm_read_state")
         return x, v, C, F
 
+    def read_state_strain(self):
+        """Final (u, v, C, E) of the last forward, input order: the displacement
+        u = x - x0 and the strain E = F - I as the library integrates them."""
+        d, N = self.d, self.N
+        dev = torch.device("cuda", torch.cuda.current_device())
+        u = torch.empty((d, N), device=dev)
+        v = torch.empty((d, N), device=dev)
+        C = torch.empty((d, d, N), device=dev)
+        E = torch.empty((d, d, N), device=dev)
+        st = self.lib.mpm_read_state_strain(self.handle, B.fptr(u), B.fptr(v), B.fptr(C), B.fptr(E),
+                                            _stream())
+        self._check(st, "mpm_read_state_strain")
+        return u, v, C, E
+
     def sort(self, x):
         """Cell keys and stable permutation of positions x [d][N] (device)."""
         x = _dev(x, (self.d, self.N), "x")
@@ -202,7 +216,7 @@ class Simulator:
         return g
 
     def autotune(self, cache_path=None, sample_substeps=0):
-        """Pick block size, grid fusion, the adjoint register budget and warp-staged gathers by timing them on the inputs
+        """Pick block size, grid fusion and the adjoint register budget by timing them on the inputs
         of the last forward (see mpm_autotune); returns the chosen options.
         The forward result is overwritten: run forward again afterwards."""
         path = cache_path.encode() if cache_path else None
@@ -213,9 +227,9 @@ class Simulator:
     def options(self):
         out = {}
         for name, key in (("block", B.MPM_OPT_BLOCK), ("fuse_grid", B.MPM_OPT_FUSE_GRID),
-                          ("tile", B.MPM_OPT_TILE), ("graphs", B.MPM_OPT_GRAPHS),
+                          ("graphs", B.MPM_OPT_GRAPHS),
                           ("streams", B.MPM_OPT_STREAMS), ("pdl", B.MPM_OPT_PDL),
-                          ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS), ("warp_box", B.MPM_OPT_WARP_BOX)):
+                          ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS), ("grid_blocks", B.MPM_OPT_GRID_BLOCKS)):
             v = ctypes.c_longlong()
             self._check(self.lib.mpm_get_option(self.handle, key, ctypes.byref(v)), "mpm_get_option")
             out[name] = v.value

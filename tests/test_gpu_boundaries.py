@@ -120,14 +120,14 @@ def test_boundaries_match_oracle(key):
     _check(run_gpu(w), o, ob, w)
 
 
-@pytest.mark.parametrize("fuse,tile,box", [(1, 0, 1), (3, 0, 0), (3, 1, 0), (0, 1, 0)])
+@pytest.mark.parametrize("fuse,streams,gb", [(1, 2, 1), (3, 2, 0), (3, 1, 0), (0, 1, 0), (0, 2, 1)])
 @pytest.mark.parametrize("key", ["clamp2d", "box3d"])
-def test_boundaries_in_every_execution_mode(key, fuse, tile, box):
-    """The grid operation (and its reverse) runs in the grid kernels, inside
-    the particle kernels (grid fusion) and in warp-staged boxes; with tiles
-    requested the runtime runs the direct kernels."""
+def test_boundaries_in_every_execution_mode(key, fuse, streams, gb):
+    """The grid operation (and its reverse) runs in the grid kernels (in 3D
+    over the listed node blocks or every node) or inside the particle kernels
+    (grid fusion), on one stream or two: the same results."""
     w, o, ob = _oracle(key)
-    _check(run_gpu(w, {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_TILE: tile, B.MPM_OPT_WARP_BOX: box}), o, ob, w)
+    _check(run_gpu(w, {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_STREAMS: streams, B.MPM_OPT_GRID_BLOCKS: gb}), o, ob, w)
 
 
 def test_set_boundaries_validates_and_invalidates_the_forward():

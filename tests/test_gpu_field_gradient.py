@@ -91,13 +91,13 @@ def test_field_gradient_matches_oracle(key):
     _check(run_gpu(w), o, ob, w)
 
 
-@pytest.mark.parametrize("fuse,tile,box", [(1, 0, 1), (3, 0, 0), (0, 1, 0), (0, 0, 1)])
+@pytest.mark.parametrize("fuse,streams,gb", [(1, 2, 1), (3, 2, 0), (0, 1, 0), (0, 2, 1)])
 @pytest.mark.parametrize("key", ["tiny2d", "tiny3d"])
-def test_field_gradient_in_every_execution_mode(key, fuse, tile, box):
-    """Grid fusion, warp-staged gathers, and tiles (which fall back to the
-    direct kernels with a field gradient) give the same results."""
+def test_field_gradient_in_every_execution_mode(key, fuse, streams, gb):
+    """Grid fusion, one stream or two, (3D) grid kernels over listed node
+    blocks or every node: the same results."""
     w, o, ob = _oracle(key)
-    _check(run_gpu(w, {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_TILE: tile, B.MPM_OPT_WARP_BOX: box}), o, ob, w)
+    _check(run_gpu(w, {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_STREAMS: streams, B.MPM_OPT_GRID_BLOCKS: gb}), o, ob, w)
 
 
 def test_field_gradient_entry_points_state():

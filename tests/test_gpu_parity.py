@@ -40,8 +40,9 @@ def run_gpu(w, backward=True, block=None, options=None):
     loss, x = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), target=_t(w.target),
                           v0=_t(w.v0), want_x=True)
     xs, v, C, F = sim.read_state()
+    u, _, _, E = sim.read_state_strain()
     out = dict(loss=loss.cpu().numpy().astype(np.float64), x=x.cpu().numpy(), x_state=xs.cpu().numpy(),
-               v=v.cpu().numpy(), C=C.cpu().numpy(), F=F.cpu().numpy())
+               v=v.cpu().numpy(), C=C.cpu().numpy(), F=F.cpu().numpy(), u=u.cpu().numpy(), E=E.cpu().numpy())
     if backward:
         g_phi, g_mag, g_field = sim.backward(torch.ones(w.cfg.n_instances, device="cuda"))
         out.update(g_phi=g_phi.cpu().numpy(), g_mag=g_mag.cpu().numpy(), g_field=g_field.cpu().numpy())
@@ -67,16 +68,18 @@ def cosine(a, b):
 
 
 def state_errors(g, o, w):
-    """Relative L2 errors of the GPU state against the oracle's."""
+    """Relative L2 errors of the GPU state against the oracle's: x and F as
+    read back (x0 + u and I + E rounded to float32), and the displacement u
+    and strain E = F - I in which the library integrates."""
     d = w.cfg.dim
     x0 = w.x0.astype(np.float64)
     eye = np.eye(d)[:, :, None]
     return {
         "x": rel_l2(g["x"], o["x"]),
-        "u": rel_l2(np.asarray(g["x"], np.float64) - x0, o["x"] - x0),
+        "u": rel_l2(g["u"], o["x"] - x0),
         "v": rel_l2(g["v"], o["v"]),
         "F": rel_l2(g["F"], o["F"]),
-        "F-I": rel_l2(np.asarray(g["F"], np.float64) - eye, o["F"] - eye),
+        "F-I": rel_l2(g["E"], o["F"] - eye),
     }
 
 
@@ -84,6 +87,8 @@ def assert_state(g, o, w, tol=STATE_TOL):
     errs = state_errors(g, o, w)
     print(w.name, {k: f"{v:.2e}" for k, v in errs.items()})
     np.testing.assert_array_equal(g["x"], g["x_state"])
+    # x and F as read back are x0 + u and I + E rounded once
+    np.testing.assert_array_equal(g["x"], (w.x0 + g["u"]).astype(np.float32))
     assert all(e <= tol for e in errs.values()), errs
     return errs
 
@@ -321,19 +326,19 @@ def test_block_size_does_not_change_results(block):
     assert_grads(g, ob, w)
 
 
-@pytest.mark.parametrize("fuse,graphs,tile", [(3, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 0),
-                                               (1, 1, 0), (2, 1, 0), (3, 0, 0)])
+@pytest.mark.parametrize("fuse,graphs,mix", [(3, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 0),
+                                              (1, 1, 0), (2, 1, 0), (3, 0, 0)])
 @pytest.mark.parametrize("key", ["walker2d_128_s0.5_300", "walker3d_48_s0.25_60", "plate3d_32_3tasks_60"])
-def test_execution_modes(key, fuse, graphs, tile):
+def test_execution_modes(key, fuse, graphs, mix):
     """Grid operation fused into the particle kernels or not, passes replayed
-    as CUDA graphs or launched directly, shared-memory tiles or direct global
-    transfers, one or two streams, PDL on or off, each adjoint register
-    budget (2, 3, 4 blocks per SM), warp-staged or direct gathers: same
-    results, twice in a row."""
+    as CUDA graphs or launched directly, one or two streams, PDL on or off,
+    each adjoint register budget (2, 3, 4 blocks per SM), and (3D) grid
+    kernels over the listed node blocks or over every node: same results,
+    twice in a row."""
     w, of, ob = _oracle(key)
-    sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs, B.MPM_OPT_TILE: tile,
-                B.MPM_OPT_STREAMS: 1 + (fuse + graphs + tile) % 2, B.MPM_OPT_PDL: (fuse + tile) % 2,
-                B.MPM_OPT_ADJOINT_BLOCKS: 2 + (fuse + graphs) % 3, B.MPM_OPT_WARP_BOX: (fuse + graphs + 1) % 2}
+    sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs,
+                B.MPM_OPT_STREAMS: 1 + (fuse + graphs + mix) % 2, B.MPM_OPT_PDL: (fuse + mix) % 2,
+                B.MPM_OPT_ADJOINT_BLOCKS: 2 + (fuse + graphs) % 3, B.MPM_OPT_GRID_BLOCKS: (graphs + mix + 1) % 2}
     for _ in range(2):
         g = run_gpu(w, options=sim_opts)
         assert_state(g, of, w)
@@ -384,9 +389,9 @@ def test_autotune_picks_and_caches(tmp_path):
     entries = json.load(open(cache))
     assert len(entries) == 1
     (entry,) = entries.values()
-    assert entry["block"] == chosen["block"] and entry["tile"] == chosen["tile"]
+    assert entry["block"] == chosen["block"] and "tile" not in entry
     assert entry["adj"] == chosen["adjoint_blocks"] and entry["adj"] in (2, 3, 4)
-    assert entry["box"] == chosen["warp_box"] and entry["fuse"] in (0, 1)
+    assert "box" not in entry and entry["fuse"] in (0, 1)
     with pytest.raises(B.MpmError):  # the tuning runs invalidated the forward result
         sim.backward(torch.ones(1, device="cuda"))
     loss, x = sim.forward(_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field), want_x=True)

@@ -86,15 +86,15 @@ def run_gpu(w, options=None):
     return out
 
 
-@pytest.mark.parametrize("block,box,adj", [(256, 1, 2), (64, 0, 3), (128, 1, 3)])
+@pytest.mark.parametrize("block,gb,adj", [(256, 1, 2), (64, 0, 3), (128, 1, 3)])
 @pytest.mark.parametrize("key", ["dense27", "massless", "translating"])
-def test_grouped_scatter_matches_oracle(key, block, box, adj):
+def test_grouped_scatter_matches_oracle(key, block, gb, adj):
     w, o, ob = _oracle(key)
     if key == "translating":  # the premise: particles did cross cells after the one sort
         base0 = np.floor(w.x0 * w.cfg.res - 0.5)
         base1 = np.floor(o["x"] * w.cfg.res - 0.5)
         assert np.mean(np.any(base0 != base1, axis=0)) > 0.5
-    g = run_gpu(w, {B.MPM_OPT_BLOCK: block, B.MPM_OPT_WARP_BOX: box, B.MPM_OPT_ADJOINT_BLOCKS: adj,
+    g = run_gpu(w, {B.MPM_OPT_BLOCK: block, B.MPM_OPT_GRID_BLOCKS: gb, B.MPM_OPT_ADJOINT_BLOCKS: adj,
                     B.MPM_OPT_FUSE_GRID: 0})
     for k in ("x", "v", "F"):
         assert rel_l2(g[k], o[k]) <= STATE_TOL, (key, k, rel_l2(g[k], o[k]))

@@ -55,21 +55,24 @@ def _config_c(cfg, keep, n=None):
 
 
 def _forward_state(w, n_steps):
-    """x, v, C, F after n_steps through mpm_forward + mpm_read_state."""
+    """x, v, C and E = F - I after n_steps through mpm_forward and
+    mpm_read_state / mpm_read_state_strain."""
     wi = W.with_steps(w, n_steps)
     sim = Simulator(wi.cfg)
     sim.forward(_t(wi.x0), _t(wi.phi), _t(wi.mag), _t(wi.field),
                 target=None if wi.target is None else _t(wi.target),
                 v0=None if wi.v0 is None else _t(wi.v0))
-    x, v, C, F = sim.read_state()
+    x, v, C, _ = sim.read_state()
+    _, _, _, E = sim.read_state_strain()
     sim.close()
-    return [a.cpu().numpy().astype(np.float64) for a in (x, v, C, F)]
+    return [a.cpu().numpy().astype(np.float64) for a in (x, v, C, E)]
 
 
 def _oracle_state(w, n_steps):
     import oracle
     o = oracle.forward(W.with_steps(w, n_steps))
-    return [o[k] for k in ("x", "v", "C", "F")]
+    d = w.cfg.dim
+    return [o["x"], o["v"], o["C"], o["F"] - np.eye(d)[:, :, None]]
 
 
 def _rel(a, b):
@@ -77,12 +80,11 @@ def _rel(a, b):
 
 
 def _errors(s, ref, d, n):
-    x, v, C, F = ref
-    eye = np.eye(d)[:, :, None]
+    """Relative L2 errors of the state s (x, v, C, E = F - I) against ref."""
+    x, v, C, E = ref
     got_E = s[2 * d + d * d:].reshape(d, d, n)
     return {"x": _rel(s[:d], x), "v": _rel(s[d:2 * d], v),
-            "C": _rel(s[2 * d:2 * d + d * d].reshape(d, d, n), C),
-            "F": _rel(got_E + eye, F), "F-I": _rel(got_E, F - eye)}
+            "C": _rel(s[2 * d:2 * d + d * d].reshape(d, d, n), C), "F-I": _rel(got_E, E)}
 
 
 def _call(lib, c, step, s_in, phi, mag, field, s_out, stream):
