@@ -110,11 +110,12 @@ __device__ __forceinline__ void list_blocks(const ActiveBlocks& ab, bool want, i
     if (mine) ab.list[first + __popc(m & ((1u << lane) - 1u))] = b;
 }
 
-// The rare part of mark_blocks, out of line so that its registers do not
-// burden the transfer kernels: list the blocks of the box lo..hi of base
+// The rare part of mark_blocks: list the blocks of the box lo..hi of base
 // cells (instance inst, or per lane when the warp spans two instances) and
-// record the box as this warp's.
-static __device__ __noinline__ void mark_blocks_slow(const ActiveBlocks& ab, bool active, int inst, int i_lo, int i_hi,
+// record the box as this warp's.  (Inlined: as an out-of-line call its
+// calling convention cost the 3D forward kernel 18 us per launch on 1M
+// particles, although the call itself is rare.)
+__device__ __forceinline__ void mark_blocks_slow(const ActiveBlocks& ab, bool active, int inst, int i_lo, int i_hi,
                                               const int (&base)[3], const int (&lo)[3], const int (&hi)[3],
                                               int res) {
     const int nb = blocks_per_axis(res);
