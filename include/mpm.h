@@ -223,10 +223,21 @@ enum {
                            registers), 3 (default in 3D, <= 80 registers: more warps to hide
                            gather latency, at the cost of spills) or 4 (<= 64 registers; 2D
                            only, 3D takes it as 3) */
-    MPM_OPT_GRID_BLOCKS = 10 /* 3D: 1 (default): the P2G kernels list the blocks of 4x4x4
+    MPM_OPT_GRID_BLOCKS = 10, /* 3D: 1 (default): the P2G kernels list the blocks of 4x4x4
                            nodes their stencils touch, and the grid operation and its
                            reverse run over the listed blocks only; 0: over every node.
                            No effect in 2D. */
+    MPM_OPT_PERSISTENT = 11, /* 1: each checkpoint segment of each pass (forward, recomputation,
+                           adjoint) runs as one persistent cooperative launch whose CTAs walk
+                           the substeps, with grid-wide barriers between the grid and the
+                           particle phases, instead of two dependent launches per substep.
+                           Runs the grid operation separately (MPM_OPT_FUSE_GRID is ignored)
+                           and the backward pass on one stream.  Not with solid boxes or a
+                           field gradient, nor in 3D without MPM_OPT_GRID_BLOCKS: those keep
+                           the chained launches.  0 (default): chained launches */
+    MPM_OPT_SPIN_LIMIT = 12 /* polls (>= 1) a persistent kernel's barrier wait makes before it
+                           gives up, sets the timeout flag and returns: the call then fails
+                           with MPM_ERR_TIMEOUT and the handle stays usable (default 2^22) */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);

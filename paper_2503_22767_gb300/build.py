@@ -20,8 +20,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmpm.so")
-SOURCES = ["kernels_particle2.cu", "kernels_forward3.cu", "kernels_adjoint3.cu", "kernels_step.cu",
-           "kernels_sort.cu", "mpm_runtime.cu", "mpm_noalloc.cu", "mpm_design.cu"]
+SOURCES = ["kernels_particle2.cu", "kernels_forward3.cu", "kernels_adjoint3.cu", "kernels_persist2.cu",
+           "kernels_persist3.cu", "kernels_step.cu", "kernels_sort.cu", "mpm_runtime.cu", "mpm_noalloc.cu",
+           "mpm_design.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", INCLUDE, "-I", CSRC]

@@ -133,6 +133,36 @@ cudaError_t launch_seed(int dim, const Params& P, const float* s, const float* x
                         const float* mom, const float* dloss, float* adj, float* gphi,
                         cudaStream_t st);
 
+// ---- persistent passes (kernels_persist.cuh) ----
+enum class PersistKind { kLean, kStore, kAdjoint };
+// One checkpoint segment [s0, s1) of a pass in one cooperative launch.
+struct PersistArgs {
+    StepArgs base;                      // the fields every substep shares
+    int s0 = 0, s1 = 0, T = 0;          // segment and horizon
+    bool first_p2g = false;             // lean: start with the P2G of substep s0
+    float* st[2] = {nullptr, nullptr};  // lean: the two state buffers (st[0] holds state s0)
+    float* state = nullptr;             // store / adjoint: state k of the segment at state + k S
+    long long S = 0;
+    float4* acc = nullptr;              // lean: the accumulator; store / adjoint: that of substep s0 (+ k G)
+    float4* V = nullptr;                // the same for the grid velocity
+    long long G = 0;
+    ActiveBlocks blk;                   // 3D: the segment's node-block list
+    ActiveBlocks blk_next;              // lean: the next segment's list (the last P2G)
+    unsigned* bar = nullptr;            // grid barrier {arrivals, generation}, zero at launch
+    long long spin_limit = 0;           // polls before a barrier wait gives up (kErrTimeout)
+};
+// lists must be true in 3D and false in 2D; at most max_ctas CTAs (0: as
+// many as are resident at once, capped by the particles).
+cudaError_t launch_persist(int dim, PersistKind kind, bool lists, const Params& P, const PersistArgs& pa, int block,
+                           int max_ctas, cudaStream_t st);
+template <int D>
+cudaError_t launch_persist_dim(PersistKind kind, bool lists, const Params& P, const PersistArgs& pa, int block,
+                               int max_ctas, cudaStream_t st);
+extern template cudaError_t launch_persist_dim<2>(PersistKind, bool, const Params&, const PersistArgs&, int, int,
+                                                  cudaStream_t);
+extern template cudaError_t launch_persist_dim<3>(PersistKind, bool, const Params&, const PersistArgs&, int, int,
+                                                  cudaStream_t);
+
 // ---- sort (kernels_sort.cu) ----
 struct SortBuffers {
     int* keys = nullptr;       // [N]

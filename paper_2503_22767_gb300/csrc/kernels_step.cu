@@ -10,6 +10,7 @@
 // with component stride P.np: x[D], v[D], C[D][D], E[D][D] with E = F - I.
 #include "kernels.h"
 #include "mpm_device.cuh"
+#include "grid_phase.cuh"
 #include "particle_io.cuh"
 
 namespace mpm {
@@ -30,21 +31,9 @@ __global__ void __launch_bounds__(256) k_grid(Params P, float4* __restrict__ acc
     pdl_trigger();
     const int local = blockIdx.x * blockDim.x + threadIdx.x;
     if (local >= P.nodes) return;
-    const long long i = (long long)blockIdx.y * P.nodes + local;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 g = acc[i];
-    float4 out = zero;
-    if (g.x > 0.0f) {
-        int c[D];
-        node_coords<D>(local, P.res, c);
-        float mv[D], v[D];
-        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-        grid_velocity<D>(P, c, g.x, mv, v, step);
-        out = make_float4(v[0], v[1 % D], D == 3 ? v[2 % D] : 0.0f, 0.0f);
-    }
-    V[i] = out;
-    if (clear_acc) acc[i] = zero;
-    if (acc_next) acc_next[i] = zero;
+    int c[D];
+    node_coords<D>(local, P.res, c);
+    grid_node<D>(P, acc, V, acc_next, clear_acc, step, (long long)blockIdx.y * P.nodes + local, c);
 }
 
 template <int D>
@@ -55,71 +44,25 @@ __global__ void __launch_bounds__(256) k_grid_adjoint(Params P, const float4* __
     pdl_trigger();
     const int local = blockIdx.x * blockDim.x + threadIdx.x;
     if (local >= P.nodes) return;
-    const long long i = (long long)blockIdx.y * P.nodes + local;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 g = acc[i];
-    float4 out = zero;
-    if (g.x > 0.0f) {
-        const float4 vb4 = Vbar[i];
-        int c[D];
-        node_coords<D>(local, P.res, c);
-        float mv[D], vb[D], mvb[D], mb;
-        unpack3<D>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-        unpack3<D>(vb4, vb);
-        grid_velocity_adjoint<D>(P, c, g.x, mv, vb, mb, mvb, step);
-        out = pack4<D>(mb, mvb);
-    }
-    Vbar[i] = zero;
-    gadj[i] = out;
+    int c[D];
+    node_coords<D>(local, P.res, c);
+    grid_adjoint_node<D>(P, acc, Vbar, gadj, step, (long long)blockIdx.y * P.nodes + local, c);
 }
-
 
 // ---------------------------------------------------------------------------
 // the same over the listed node blocks only (3D)
 // ---------------------------------------------------------------------------
 // Persistent CTAs of 256 threads walk the list, four blocks of 64 nodes at a
 // time (one thread per node).  The list holds block ids, instance-major.
-struct BlockNode {
-    long long i;  // node index in the [inst][node] grid
-    int c[3];     // node coordinates
-    bool in;      // inside the grid (res need not be a multiple of the block edge)
-};
-
-__device__ __forceinline__ BlockNode block_node(const Params& P, int b, int t) {
-    const int nb = blocks_per_axis(P.res);
-    const int bpi = nb * nb * nb;
-    const int inst = b / bpi, lb = b - inst * bpi;
-    BlockNode n;
-    n.c[0] = (lb / (nb * nb)) * kBlockEdge + (t >> 4);
-    n.c[1] = ((lb / nb) % nb) * kBlockEdge + ((t >> 2) & 3);
-    n.c[2] = (lb % nb) * kBlockEdge + (t & 3);
-    n.in = n.c[0] < P.res && n.c[1] < P.res && n.c[2] < P.res;
-    n.i = (long long)inst * P.nodes + ((long long)n.c[0] * P.res + n.c[1]) * P.res + n.c[2];
-    return n;
-}
-
 __global__ void __launch_bounds__(256) k_grid_blocks(Params P, float4* __restrict__ acc, float4* __restrict__ V,
                                                      ActiveBlocks blk, bool clear, int step) {
     pdl_wait();
     pdl_trigger();
     const int n = *blk.count;
     const int t = threadIdx.x & 63;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int e = blockIdx.x * 4 + (threadIdx.x >> 6); e < n; e += gridDim.x * 4) {
-        const int b = blk.list[e];
-        const BlockNode nd = block_node(P, b, t);
-        if (nd.in) {
-            const float4 g = acc[nd.i];
-            float4 out = zero;
-            if (g.x > 0.0f) {
-                float mv[3], v[3];
-                unpack3<3>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-                grid_velocity<3>(P, nd.c, g.x, mv, v, step);
-                out = make_float4(v[0], v[1], v[2], 0.0f);
-            }
-            V[nd.i] = out;
-            if (clear) acc[nd.i] = zero;
-        }
+        const BlockNode nd = block_node(P, blk.list[e], t);
+        if (nd.in) grid_node<3>(P, acc, V, nullptr, clear, step, nd.i, nd.c);
     }
 }
 
@@ -130,21 +73,9 @@ __global__ void __launch_bounds__(256) k_grid_adjoint_blocks(Params P, const flo
     pdl_trigger();
     const int n = *blk.count;
     const int t = threadIdx.x & 63;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int e = blockIdx.x * 4 + (threadIdx.x >> 6); e < n; e += gridDim.x * 4) {
         const BlockNode nd = block_node(P, blk.list[e], t);
-        if (!nd.in) continue;
-        const float4 g = acc[nd.i];
-        float4 out = zero;
-        if (g.x > 0.0f) {
-            float mv[3], vb[3], mvb[3], mb;
-            unpack3<3>(make_float4(g.y, g.z, g.w, 0.0f), mv);
-            unpack3<3>(Vbar[nd.i], vb);
-            grid_velocity_adjoint<3>(P, nd.c, g.x, mv, vb, mb, mvb, step);
-            out = pack4<3>(mb, mvb);
-        }
-        Vbar[nd.i] = zero;
-        gadj[nd.i] = out;
+        if (nd.in) grid_adjoint_node<3>(P, acc, Vbar, gadj, step, nd.i, nd.c);
     }
 }
 
@@ -364,6 +295,12 @@ cudaError_t launch_adjoint(int dim, bool p2gt, bool g2pt, bool fuse, bool fuse_v
                            const StepArgs& a, int block, cudaStream_t st) {
     return dim == 2 ? launch_adjoint_dim<2>(p2gt, g2pt, fuse, fuse_v, P, a, block, st)
                     : launch_adjoint_dim<3>(p2gt, g2pt, fuse, fuse_v, P, a, block, st);
+}
+
+cudaError_t launch_persist(int dim, PersistKind kind, bool lists, const Params& P, const PersistArgs& pa, int block,
+                           int max_ctas, cudaStream_t st) {
+    return dim == 2 ? launch_persist_dim<2>(kind, lists, P, pa, block, max_ctas, st)
+                    : launch_persist_dim<3>(kind, lists, P, pa, block, max_ctas, st);
 }
 
 cudaError_t launch_grid(int dim, const Params& P, float4* acc, float4* V, float4* acc_next,

@@ -115,7 +115,7 @@ __device__ __forceinline__ void list_blocks(const ActiveBlocks& ab, bool want, i
 // record the box as this warp's.  (Inlined: as an out-of-line call its
 // calling convention cost the 3D forward kernel 18 us per launch on 1M
 // particles, although the call itself is rare.)
-__device__ __forceinline__ void mark_blocks_slow(const ActiveBlocks& ab, bool active, int inst, int i_lo, int i_hi,
+__device__ __forceinline__ void mark_blocks_slow(const ActiveBlocks& ab, long long w, bool active, int inst, int i_lo, int i_hi,
                                               const int (&base)[3], const int (&lo)[3], const int (&hi)[3],
                                               int res) {
     const int nb = blocks_per_axis(res);
@@ -142,15 +142,15 @@ __device__ __forceinline__ void mark_blocks_slow(const ActiveBlocks& ab, bool ac
         list_blocks(ab, j < total, ((i_lo * nb + b0 + i0) * nb + b1 + i1) * nb + b2 + i2);
     }
     if (lane == 0) {
-        const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         ab.wbox[w] = make_int4(lo[0] | (hi[0] + 1) << 16, lo[1] | (hi[1] + 1) << 16, lo[2] | (hi[2] + 1) << 16, 0);
     }
 }
 
 // Every lane of a warp calls this after its P2G, with the base node of its
-// stencil (active: the lane has a particle).  stored is this warp's wbox entry.
-__device__ __forceinline__ void mark_blocks(const ActiveBlocks& ab, bool active, int inst, const int (&base)[3],
-                                            int res, int4 stored) {
+// stencil (active: the lane has a particle).  w: the warp's index (its
+// particles are 32w .. 32w + 31); stored: its wbox entry.
+__device__ __forceinline__ void mark_blocks(const ActiveBlocks& ab, long long w, bool active, int inst,
+                                            const int (&base)[3], int res, int4 stored) {
     const unsigned full = 0xffffffffu;
     const int i_lo = __reduce_min_sync(full, active ? inst : INT_MAX);
     const int i_hi = __reduce_max_sync(full, active ? inst : INT_MIN);
@@ -173,7 +173,7 @@ __device__ __forceinline__ void mark_blocks(const ActiveBlocks& ab, bool active,
             hi[a] = max(hi[a], (st[a] >> 16) - 1);
         }
     }
-    mark_blocks_slow(ab, active, inst, i_lo, i_hi, base, lo, hi, res);
+    mark_blocks_slow(ab, w, active, inst, i_lo, i_hi, base, lo, hi, res);
 }
 
 // Index of the instance owning particle p (instance ranges are contiguous

@@ -133,6 +133,11 @@ struct mpm_handle {
     int4* blk_wbox = nullptr; // [4][n_wbox]
     bool seg_dirty = false;   // a backward pass ran over every node: the segment accumulators are not zero
 
+    // --- persistent passes (MPM_OPT_PERSISTENT) ---
+    bool persistent = false;
+    long long spin_limit = 1LL << 22;  // polls before a grid-barrier wait gives up
+    unsigned* bar = nullptr;           // grid barrier of the persistent kernels
+
     // --- options ---
     bool fuse_fwd = true;   // grid operation folded into the forward particle kernels
     bool fuse_adj = false;  // grid adjoint folded into the adjoint particle kernels
@@ -505,6 +510,7 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     ALLOC(h->st_xout, d * h->N);
     ALLOC(h->st_loss, h->n_inst);
     ALLOC(h->d_err, 1);
+    ALLOC(h->bar, 2);
     ALLOC(h->perm, h->np);
     h->sb.n_keys = mpm::sort_key_space(d, h->res, h->n_inst);
     h->sb.scan_tmp_len = mpm::sort_scan_tmp_len(h->sb.n_keys);
@@ -566,6 +572,23 @@ StepArgs base_args(mpm_handle* h) {
     return a;
 }
 
+// The persistent passes run when asked for, without solid boxes or a field
+// gradient (which they do not carry), and in 3D with the node-block lists.
+bool use_persist(const mpm_handle* h) {
+    return h->persistent && h->P.ext == nullptr && (h->dim == 2 || (h->blocks && h->grid_blocks));
+}
+
+// one persistent launch: the barrier is zeroed first
+int persist(mpm_handle* h, mpm::PersistKind kind, int cls, double bytes, mpm::PersistArgs& pa, cudaStream_t st) {
+    pa.bar = h->bar;
+    pa.spin_limit = h->spin_limit;
+    MPM_CUDA(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), st));
+    // 256-thread CTAs: the barrier's cost grows with the CTAs that arrive at it
+    return timed(h, cls, bytes, st, [&] {
+        return mpm::launch_persist(h->dim, kind, h->dim == 3, h->P, pa, 256, 0, st);
+    });
+}
+
 // node-block list i (3D): 0 and 1 for the forward pass, 2 + b for recomputation set b
 mpm::ActiveBlocks block_list(const mpm_handle* h, int i) {
     mpm::ActiveBlocks b;
@@ -602,7 +625,8 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
     const Params& P = h->P;
     const long long S = (long long)h->ncomp * h->np;
     const long long G = h->total_nodes;
-    const bool fuse = h->fuse_fwd;
+    const bool persistent = use_persist(h);
+    const bool fuse = h->fuse_fwd && !persistent;
     auto acc3 = [&](int i) { return h->acc3 + G * (i % 3); };
     int rc;
     MPM_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
@@ -665,11 +689,33 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
                                     cudaMemcpyDeviceToDevice, st));
         StepArgs a = base_args(h);
         a.mom = h->mom;
-        if (seg == 0) {
-            if ((rc = counted(h, 1, [&] {
-                     return mpm::launch_instance_mass(P, h->phi_cur, h->d_inst_off, h->Minst, st);
-                 })))
+        if (seg == 0 && (rc = counted(h, 1, [&] {
+                             return mpm::launch_instance_mass(P, h->phi_cur, h->d_inst_off, h->Minst, st);
+                         })))
+            return rc;
+        if (persistent) {
+            // the whole segment in one cooperative launch
+            mpm::PersistArgs pa;
+            pa.base = a;
+            pa.s0 = s0;
+            pa.s1 = s1;
+            pa.T = T;
+            pa.first_p2g = seg == 0;
+            pa.st[0] = cur;
+            pa.st[1] = nxt;
+            pa.acc = h->acc;
+            pa.V = h->V;
+            if (lists) {
+                pa.blk = lean_blk(s0);
+                pa.blk_next = lean_blk(s1);
+            }
+            if ((rc = persist(h, mpm::PersistKind::kLean, kFwdParticle,
+                              h->N * (s1 - s0) * particle_bytes(d, kFwdParticle, kFused), pa, st)))
                 return rc;
+            if ((s1 - s0) & 1) std::swap(cur, nxt);  // the final state is in st[(s1 - s0) & 1]
+            continue;
+        }
+        if (seg == 0) {
             a.s_in = cur;
             a.acc = fuse ? acc3(0) : h->acc;
             a.n_p2g = 0;
@@ -756,7 +802,8 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
     const Params& P = h->P;
     const long long S = (long long)h->ncomp * h->np;
     const long long G = h->total_nodes;
-    const bool fuse_rec = h->fuse_fwd;
+    const bool persistent = use_persist(h);
+    const bool fuse_rec = h->fuse_fwd && !persistent;
     const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T), Ks = s1 - s0;
     const int* id_seg = h->ck_id + h->np * seg;
     auto state = [&](int k) { return ss.state + S * k; };
@@ -779,6 +826,21 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
     a.phi = ss.phi;
     a.mag = ss.mag;
     a.x0 = ss.x0;
+    if (persistent) {
+        mpm::PersistArgs pa;
+        pa.base = a;
+        pa.s0 = s0;
+        pa.s1 = s1;
+        pa.T = T;
+        pa.state = ss.state;
+        pa.S = S;
+        pa.acc = ss.acc;
+        pa.V = ss.V;
+        pa.G = G;
+        if (lists) pa.blk = block_list(h, ss.list_id);
+        return persist(h, mpm::PersistKind::kStore, kFwdParticle,
+                       h->N * Ks * particle_bytes(d, kFwdParticle, kFusedStore), pa, st);
+    }
     a.s_in = state(0);
     a.acc = gacc(0);
     a.n_p2g = s0;
@@ -823,16 +885,33 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
     return MPM_OK;
 }
 
+// The end of a segment's adjoint: design gradients back to input order, and
+// the segment set left as its next recomputation expects it (3D lists: the
+// accumulators zero over the listed blocks, flags and counts zero).
+int finish_adjoint_segment(mpm_handle* h, const int* id_seg, const SegSet& ss, int Ks, cudaStream_t st) {
+    const Params& P = h->P;
+    int rc;
+    if ((rc = counted(h, 1, [&] {
+             return mpm::launch_scatter_design_grad(h->dim, P, id_seg, h->d_inst_off, h->d_dbase, h->gphi_cur,
+                                                    h->gmag_cur, h->Nd, h->gphi_d, h->gmag_d, st);
+         })))
+        return rc;
+    if (h->blocks && h->grid_blocks && (rc = clear_list(h, ss.list_id, ss.acc, h->total_nodes, Ks, st)))
+        return rc;
+    return MPM_OK;
+}
+
 int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj, float* adj_next,
                     cudaStream_t st) {
     const int d = h->dim;
     const Params& P = h->P;
     const long long S = (long long)h->ncomp * h->np;
     const long long G = h->total_nodes;
-    const bool fuse = h->fuse_adj;  // grid adjoint evaluated inside the adjoint kernels
+    const bool persistent = use_persist(h);
+    const bool fuse = h->fuse_adj && !persistent;  // grid adjoint evaluated inside the adjoint kernels
     // G2P^T needs the grid velocity: stored by the grid kernel, or (fused
     // recomputation) recovered from the stored accumulator
-    const bool fuse_v = fuse || h->fuse_fwd;
+    const bool fuse_v = fuse || (h->fuse_fwd && !persistent);
     const int s0 = seg * h->K, s1 = std::min(s0 + h->K, T), Ks = s1 - s0;
     const int* id_seg = h->ck_id + h->np * seg;
     auto state = [&](int k) { return ss.state + S * k; };
@@ -870,6 +949,25 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
                  return mpm::launch_unpermute(h->ncomp, P, adj_next, adj, h->ck_perm + h->np * (seg + 1), st);
              })))
             return rc;
+    }
+    if (persistent) {
+        mpm::PersistArgs pa;
+        pa.base = args();
+        pa.base.Vbar = h->Vbar;
+        pa.base.gadj = h->gadj;
+        pa.s0 = s0;
+        pa.s1 = s1;
+        pa.T = T;
+        pa.state = ss.state;
+        pa.S = S;
+        pa.acc = ss.acc;
+        pa.V = ss.V;
+        pa.G = G;
+        if (h->blocks) pa.blk = block_list(h, ss.list_id);
+        if ((rc = persist(h, mpm::PersistKind::kAdjoint, kAdjParticle,
+                          h->N * Ks * particle_bytes(d, kAdjParticle, kFused), pa, st)))
+            return rc;
+        return finish_adjoint_segment(h, id_seg, ss, Ks, st);
     }
     // G2P^T of the last substep of the segment
     StepArgs a = args();
@@ -931,17 +1029,7 @@ int adjoint_segment(mpm_handle* h, int seg, int T, const SegSet& ss, float* adj,
              return mpm::launch_adjoint(d, true, false, fuse, fuse_v, P, a, h->block, st);
          })))
         return rc;
-    if ((rc = counted(h, 1, [&] {
-             return mpm::launch_scatter_design_grad(d, P, id_seg, h->d_inst_off, h->d_dbase, h->gphi_cur,
-                                                    h->gmag_cur, h->Nd, h->gphi_d, h->gmag_d, st);
-         })))
-        return rc;
-    if (h->blocks && h->grid_blocks) {
-        // leave this segment set as its next recomputation expects it: the
-        // accumulators zero over the listed blocks, flags and counts zero
-        if ((rc = clear_list(h, ss.list_id, ss.acc, G, Ks, st))) return rc;
-    }
-    return MPM_OK;
+    return finish_adjoint_segment(h, id_seg, ss, Ks, st);
 }
 
 int backward_pass(mpm_handle* h, cudaStream_t st) {
@@ -954,13 +1042,14 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
     MPM_CUDA(h, cudaMemsetAsync(h->gfield_d, 0, sizeof(float) * h->n_inst * h->T * d, st));
     if (h->ext_host.fgrad)
         MPM_CUDA(h, cudaMemsetAsync(h->d_gfgrad, 0, sizeof(float) * h->n_inst * h->T * d * d, st));
-    if (h->fuse_adj) MPM_CUDA(h, cudaMemsetAsync(h->Vbar3, 0, sizeof(float4) * 3 * G, st));
+    if (h->fuse_adj && !use_persist(h)) MPM_CUDA(h, cudaMemsetAsync(h->Vbar3, 0, sizeof(float4) * 3 * G, st));
     else MPM_CUDA(h, cudaMemsetAsync(h->Vbar, 0, sizeof(float4) * G, st));
     const int T = h->tune_T > 0 ? std::min(h->T, h->tune_T) : h->T;
     const int n_seg = (T + h->K - 1) / h->K;
     float* adj = h->adj;
     float* adj_next = h->adj2;
-    if (!h->two_streams || n_seg < 2) {
+    // (the persistent kernels each take the whole GPU: one stream)
+    if (!h->two_streams || n_seg < 2 || use_persist(h)) {
         for (int seg = n_seg - 1; seg >= 0; --seg) {
             const SegSet ss = seg_set(h, 0);
             if ((rc = recompute_segment(h, seg, T, ss, st))) return rc;
@@ -1033,6 +1122,9 @@ int run_pass(mpm_handle* h, int pass, cudaStream_t st) {
 
 int finish(mpm_handle* h, int pass, cudaStream_t st) {
     int rc = check_device_flags(h, st);
+    // a pass that stopped early (a timed-out barrier) may leave the segment
+    // accumulators and lists set: the next backward pass clears them in full
+    if (rc != MPM_OK && h->blocks) h->seg_dirty = true;
     if (h->ran_graph[pass]) {
         h->ran_graph[pass] = false;
         int r2 = collect_graph_timing(h, pass);
@@ -1501,6 +1593,16 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             h->fuse_fwd = (value & 1) != 0;
             h->fuse_adj = (value & 2) != 0;
             return MPM_OK;
+        case MPM_OPT_PERSISTENT:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "persistent must be 0 or 1");
+            if (h->persistent != (value == 1)) drop_graphs(h);
+            h->persistent = value == 1;
+            return MPM_OK;
+        case MPM_OPT_SPIN_LIMIT:
+            if (value < 1) return fail(h, MPM_ERR_ARG, "spin limit must be >= 1");
+            if (h->spin_limit != value) drop_graphs(h);
+            h->spin_limit = value;
+            return MPM_OK;
         case MPM_OPT_GRID_BLOCKS:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "grid blocks must be 0 or 1");
             if (h->grid_blocks != (value == 1)) drop_graphs(h);
@@ -1553,6 +1655,8 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_PDL: *value = h->P.pdl; return MPM_OK;
         case MPM_OPT_ADJOINT_BLOCKS: *value = h->P.adj_blocks; return MPM_OK;
         case MPM_OPT_GRID_BLOCKS: *value = h->grid_blocks ? 1 : 0; return MPM_OK;
+        case MPM_OPT_PERSISTENT: *value = h->persistent ? 1 : 0; return MPM_OK;
+        case MPM_OPT_SPIN_LIMIT: *value = h->spin_limit; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

@@ -43,12 +43,16 @@ namespace {
 
 inline int particle_blocks(long long n, int block) { return (int)((n + block - 1) / block); }
 
-// 3D: at most 64 registers (32 warps per SM) to keep more gathers in flight
+// The forward step of particle p (G2P of substep a.n_g2p and/or P2G of
+// a.n_p2g); every lane of a warp calls it together, with particles
+// 32w .. 32w + 31 (w = p / 32).  sm: this warp's warp_slots<D, P2G>()
+// float4 of shared memory (the scatter slab of P2G).
 // EXT: P.ext is set (solid boxes or a non-uniform field); without it the
-// kernel carries no code for the field gradient.
-template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT>
-__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksForward2)
-    k_forward(Params P, StepArgs a) {
+// code for them is left out.  CHAIN: the kernel is one launch of a chain
+// with programmatic dependent launch (k_forward); a persistent kernel calls
+// this between its own grid-wide barriers instead.
+template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT, bool CHAIN>
+__device__ __forceinline__ void forward_particle(const Params& P, const StepArgs& a, int p, float4* sm) {
     using L = Layout<D>;
     // Early loads: with the grid operation in its own kernel, this kernel's
     // predecessor is that grid kernel, which writes none of the particle
@@ -56,15 +60,9 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
     // triggers its dependents, so when this kernel starts, the particle
     // kernel before the grid kernel has completed, and the state loads can
     // overlap the grid kernel's tail.
-    constexpr bool kEarly = G2P && !FUSE;
+    constexpr bool kEarly = CHAIN && G2P && !FUSE;
     // the P2G scatter is aggregated over the lanes of one cell (scatter_aggregated)
     constexpr bool AGG = P2G && aggregate_scatter<D>();
-    // per warp (dynamic shared memory, warp_slots<D, P2G>() float4 per
-    // warp): the scatter slab of P2G
-    constexpr int kSlots = warp_slots<D, P2G>();
-    extern __shared__ float4 s_warp[];
-    float4* sm = s_warp + (threadIdx.x >> 5) * kSlots;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
     const long long np = P.np;
@@ -92,9 +90,11 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
         }
     };
     if (kEarly && active) load_state();
-    pdl_wait();
-    pdl_trigger();
-    if (FUSE) clear_buffer(a);
+    if (CHAIN) {
+        pdl_wait();
+        pdl_trigger();
+        if (FUSE) clear_buffer(a);
+    }
     if (!kEarly && active) load_state();
     if (G2P) {
         float mom_x[1] = {0.0f};
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
             // the warp lists the node blocks its stencils reach beyond its box
             // (a.blk is uniform over the launch, so the whole warp takes part)
             if constexpr (D == 3) {
-                if (a.blk.flag != nullptr) mark_blocks(a.blk, active, inst, s.base, P.res, a.blk.wbox[p >> 5]);
+                if (a.blk.flag != nullptr) mark_blocks(a.blk, p >> 5, active, inst, s.base, P.res, a.blk.wbox[p >> 5]);
             }
         } else if (active) {
             float pw = 0.0f, Ug[D];  // per row: product of the other axes' weights, u + dx A o
@@ -312,6 +312,15 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
     if (flags) atomicOr(a.err, flags);
 }
 
+// 3D: at most 64 registers (32 warps per SM) to keep more gathers in flight
+template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT>
+__global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksForward2)
+    k_forward(Params P, StepArgs a) {
+    extern __shared__ float4 s_warp[];
+    forward_particle<D, G2P, P2G, WRITE_ALL, FUSE, EXT, true>(
+        P, a, blockIdx.x * blockDim.x + threadIdx.x, s_warp + (threadIdx.x >> 5) * warp_slots<D, P2G>());
+}
+
 
 // ---------------------------------------------------------------------------
 // adjoint particle kernel
@@ -324,14 +333,15 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
 // FUSE: P2G^T evaluates the grid adjoint per stencil node from (accP, VbarIn);
 // FUSE_V: G2P^T takes the grid velocity from accG through the grid operation.
 // EXT: P.ext is set (solid boxes or a non-uniform field), as in k_forward.
-template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, int MINB, bool EXT>
-__global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
+// CHAIN and the calling convention as in forward_particle; sm: this warp's
+// warp_slots<D, G2PT>() float4 (the scatter slab of G2P^T).
+template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, bool EXT, bool CHAIN>
+__device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs& a, int p, float4* sm) {
     using L = Layout<D>;
     // Early loads as in k_forward: the fused kernel without grid-adjoint
     // fusion follows the grid adjoint kernel, which writes none of the
     // particle arrays of state n, the partial adjoint or the design.
-    constexpr bool kEarly = P2GT && G2PT && !FUSE;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr bool kEarly = CHAIN && P2GT && G2PT && !FUSE;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
     const long long np = P.np;
@@ -365,16 +375,13 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
             prefetch_l2(a.gmag + (long long)c * np + p);
         }
     }
-    pdl_wait();
-    pdl_trigger();
-    clear_buffer(a);
+    if (CHAIN) {
+        pdl_wait();
+        pdl_trigger();
+        clear_buffer(a);
+    }
     if (P2GT && !kEarly && active) load_state_n();
-    // per warp (dynamic shared memory, warp_slots<D, G2PT>() float4 per
-    // warp): the scatter slab of G2P^T
     constexpr bool AGG = G2PT && aggregate_scatter<D>();
-    constexpr int kSlots = warp_slots<D, G2PT>();
-    extern __shared__ float4 s_warp[];
-    float4* sm = s_warp + (threadIdx.x >> 5) * kSlots;
     float bab[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) bab[i] = 0.0f;
@@ -814,6 +821,13 @@ __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
         }
     }
     if (flags) atomicOr(a.err, flags);
+}
+
+template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, int MINB, bool EXT>
+__global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
+    extern __shared__ float4 s_warp[];
+    adjoint_particle<D, P2GT, G2PT, FUSE, FUSE_V, EXT, true>(
+        P, a, blockIdx.x * blockDim.x + threadIdx.x, s_warp + (threadIdx.x >> 5) * warp_slots<D, G2PT>());
 }
 
 

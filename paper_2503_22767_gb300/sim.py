@@ -229,7 +229,8 @@ class Simulator:
         for name, key in (("block", B.MPM_OPT_BLOCK), ("fuse_grid", B.MPM_OPT_FUSE_GRID),
                           ("graphs", B.MPM_OPT_GRAPHS),
                           ("streams", B.MPM_OPT_STREAMS), ("pdl", B.MPM_OPT_PDL),
-                          ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS), ("grid_blocks", B.MPM_OPT_GRID_BLOCKS)):
+                          ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS), ("grid_blocks", B.MPM_OPT_GRID_BLOCKS),
+                          ("persistent", B.MPM_OPT_PERSISTENT)):
             v = ctypes.c_longlong()
             self._check(self.lib.mpm_get_option(self.handle, key, ctypes.byref(v)), "mpm_get_option")
             out[name] = v.value
