@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256, kPersistBlocks) k_persist_adjoint(Params 
         a.s_aux = pa.state + pa.S * (Ks - 1);
         a.n_p2g = pa.s1;
         a.V = pa.V + pa.G * (Ks - 1);
-        particle_phase(P, [&](int p) { adjoint_particle<D, false, true, false, false, false, false>(P, a, p, sm); });
+        particle_phase(P, [&](int p) { adjoint_particle<D, false, true, false, false, false, false, false>(P, a, p, sm); });
         if (!grid_barrier(pa.bar, pa.spin_limit, err)) return;
     }
     for (int k = Ks - 1; k >= 0; --k) {
@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(256, kPersistBlocks) k_persist_adjoint(Params 
         if (k >= 1) {
             a.s_aux = pa.state + pa.S * (k - 1);
             a.V = pa.V + pa.G * (k - 1);
-            particle_phase(P, [&](int p) { adjoint_particle<D, true, true, false, false, false, false>(P, a, p, sm); });
+            particle_phase(P, [&](int p) { adjoint_particle<D, true, true, false, false, false, false, false>(P, a, p, sm); });
         } else {
-            particle_phase(P, [&](int p) { adjoint_particle<D, true, false, false, false, false, false>(P, a, p, sm); });
+            particle_phase(P, [&](int p) { adjoint_particle<D, true, false, false, false, false, false, false>(P, a, p, sm); });
         }
         if (!grid_barrier(pa.bar, pa.spin_limit, err)) return;
     }

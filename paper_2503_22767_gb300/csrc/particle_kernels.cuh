@@ -334,8 +334,10 @@ __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksF
 // FUSE_V: G2P^T takes the grid velocity from accG through the grid operation.
 // EXT: P.ext is set (solid boxes or a non-uniform field), as in k_forward.
 // CHAIN and the calling convention as in forward_particle; sm: this warp's
-// warp_slots<D, G2PT>() float4 (the scatter slab of G2P^T).
-template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, bool EXT, bool CHAIN>
+// warp_slots<D, G2PT>() float4 (the scatter slab of G2P^T).  RELIEF: the
+// register budget is tight (80 registers or fewer), so the state and stress
+// of P2G^T are reloaded and recomputed after its node loop.
+template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, bool EXT, bool CHAIN, bool RELIEF>
 __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs& a, int p, float4* sm) {
     using L = Layout<D>;
     // Early loads as in k_forward: the fused kernel without grid-adjoint
@@ -544,14 +546,19 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
             };
             node_loop();
             // The node loop needs none of C, E, the stress (all used for A
-            // before it) and Fbar of state n: they are read again, and the
-            // stress recomputed, here, so their registers are free during the
-            // loop (the recomputation is cheaper than the spills).
-            reload_mat<D>(a.s_in, L::C, np, p, Cn);
-            reload_mat<D>(a.s_in, L::F, np, p, F);
+            // before it) and Fbar of state n.  Under a tight register budget
+            // (RELIEF) they are read again, and the stress recomputed, here, so
+            // their registers are free during the loop (the recomputation is
+            // cheaper than the spills); with registers to spare they stay live.
+            if (RELIEF) {
+                reload_mat<D>(a.s_in, L::C, np, p, Cn);
+                reload_mat<D>(a.s_in, L::F, np, p, F);
+            }
             load_mat<D>(a.adj, L::F, np, p, Fb);
-            stress_parts<D>(F, phi, P, S);
-            piola<D>(S, Br, Ba, Pk);
+            if (RELIEF) {
+                stress_parts<D>(F, phi, P, S);
+                piola<D>(S, Br, Ba, Pk);
+            }
             // grad w is (dw along its own axis) / dx times the other weights;
             // A^T S0 = (dA S0) / dx
 #pragma unroll
@@ -826,7 +833,7 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
 template <int D, bool P2GT, bool G2PT, bool FUSE, bool FUSE_V, int MINB, bool EXT>
 __global__ void __launch_bounds__(256, MINB) k_adjoint(Params P, StepArgs a) {
     extern __shared__ float4 s_warp[];
-    adjoint_particle<D, P2GT, G2PT, FUSE, FUSE_V, EXT, true>(
+    adjoint_particle<D, P2GT, G2PT, FUSE, FUSE_V, EXT, true, (MINB >= 3)>(
         P, a, blockIdx.x * blockDim.x + threadIdx.x, s_warp + (threadIdx.x >> 5) * warp_slots<D, G2PT>());
 }
 
