@@ -13,20 +13,29 @@ namespace mpm {
 // The cell-sorted particles of one cell (8 per cell in 3D at the
 // configurations' densities) share their base node, and so every stencil
 // node; issued one per lane, their float4 atomics reach L2 as separate
-// same-address updates.  Here the lanes of one base node (found with one
-// __match_any_sync) sum their contributions in shared memory first, slab by
-// slab of kAggSlab stencil nodes: every lane writes its node values, then the
-// j-th lane of a group of g sums nodes j, j + g, ... of the slab over the
-// group (in lane order) and issues one atomic per node.  A group of one
-// issues exactly the per-lane atomics.
+// same-address updates.  Here the lanes of one base node (a group, found with
+// one __match_any_sync) sum their contributions in shared memory first, slab
+// by slab of kAggSlab stencil nodes: every lane writes its node values, then
+// each quarter-warp takes one group and sums the group's value of one slab
+// node per lane (in lane order), and issues one atomic per node.  A warp with
+// G groups thus needs ceil(G / 4) passes per slab, whatever the group sizes:
+// once a deforming body leaves cells with uneven particle counts, a warp holds
+// groups of 1 to 15 lanes, and the pass count no longer follows the smallest
+// group (with a group of one lane, one lane summing every node of the slab
+// for its group took eight passes).  A group of one issues exactly the
+// per-lane atomics.
 // ---------------------------------------------------------------------------
-// Nodes per slab: 8, so that a group of 8 lanes (8 particles per cell in 3D)
-// sums one node per lane and slab (27 = 8 + 8 + 8 + 3).  A lane's slots are 9
-// float4 apart (144 bytes, 36 banks): the 8 lanes of one quarter-warp store
-// then hit disjoint banks, where a 128-byte stride would put all on the same 4.
+// Nodes per slab: 8, one per lane of a quarter-warp (27 = 8 + 8 + 8 + 3).  A
+// lane's slots are 9 float4 apart (144 bytes, 36 banks), so the 8 lanes of a
+// quarter-warp storing their values hit disjoint banks, and a quarter-warp
+// summing one group reads 8 consecutive float4 of one lane's slots.
 constexpr int kAggSlab = 8;
 constexpr int kAggStride = 9;
-constexpr int kAggSlots = kAggStride * 32;  // float4 per warp
+constexpr int kAggValueSlots = kAggStride * 32;  // float4 of node values per warp
+// after the values: per group, its lanes (32 x unsigned) and the address of
+// its base node (32 x float4*): 384 bytes = 24 float4
+constexpr int kAggTableSlots = 24;
+constexpr int kAggSlots = kAggValueSlots + kAggTableSlots;  // float4 per warp
 
 // 3D only: with 4 particles per cell in 2D the exchange cost more than the
 // atomics it saved on every 2D workload measured (2D locomotion 15.8 -> 17.4
@@ -44,6 +53,20 @@ __host__ __device__ constexpr int warp_slots() {
     return SCATTER && aggregate_scatter<D>() ? kAggSlots : 0;
 }
 
+// Offset of stencil node k (last axis fastest, k < 3^D) from the base node on
+// a grid of res nodes per axis (res2 = res^2): k / 9, (k / 3) % 3 and k % 3
+// by multiply and shift (exact for k < 27).
+template <int D>
+__device__ __forceinline__ int stencil_node_offset(int k, int res, int res2) {
+    if (D == 3) {
+        const int a0 = (k * 57) >> 9, r = k - 9 * a0;
+        const int a1 = (r * 11) >> 5;
+        return a0 * res2 + a1 * res + (r - 3 * a1);
+    }
+    const int a0 = (k * 11) >> 5;
+    return a0 * res + (k - 3 * a0);
+}
+
 // Every lane of the warp calls this; a lane without a particle passes
 // active = false (its values are not read).  value(k) gives the float4 that
 // stencil node k (last axis fastest) receives from this lane's particle; it
@@ -57,10 +80,21 @@ __device__ __forceinline__ void scatter_aggregated(int nb, int inst, bool active
     const unsigned long long key =
         active ? (((unsigned long long)(unsigned)inst << 32) | (unsigned)nb) : ~0ull - (unsigned)lane;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int g = __popc(peers);
-    const int j = __popc(peers & ((1u << lane) - 1u));
+    // the groups of active lanes, numbered by their lowest lane
+    const bool leader = active && lane == __ffs(peers) - 1;
+    const unsigned leaders = __ballot_sync(0xffffffffu, leader);
+    const int G = __popc(leaders);
+    unsigned* g_lanes = reinterpret_cast<unsigned*>(sm + kAggValueSlots);
+    float4** g_base = reinterpret_cast<float4**>(g_lanes + 32);
+    __syncwarp();  // the table's readers in an earlier call are done
+    if (leader) {
+        const int gi = __popc(leaders & ((1u << lane) - 1u));
+        g_lanes[gi] = peers;
+        g_base[gi] = grid + nb;
+    }
     float4* mine = sm + lane * kAggStride;
     constexpr int kNodes = D == 3 ? 27 : 9;
+    const int res2 = res * res;
 #pragma unroll
     for (int k0 = 0; k0 < kNodes; k0 += kAggSlab) {
         const int nk = kNodes - k0 < kAggSlab ? kNodes - k0 : kAggSlab;  // nodes in this slab
@@ -69,22 +103,20 @@ __device__ __forceinline__ void scatter_aggregated(int nb, int inst, bool active
         for (int n = 0; n < kAggSlab; ++n)
             if (n < nk) mine[n] = value(k0 + n);
         __syncwarp();
-        if (active) {
-            for (int n = j; n < nk; n += g) {
-                // the sum in lane order, two components per packed add
-                float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
-                auto add = [&](const float4& c) {
-                    a01 = __fadd2_rn(a01, make_float2(c.x, c.y));
-                    a23 = __fadd2_rn(a23, make_float2(c.z, c.w));
-                };
-                // (a version that summed consecutive-lane groups at fixed offsets,
-                // unrolled, ran 7 us slower per 3D forward launch)
-                for (unsigned q = peers; q; q &= q - 1u) add(sm[(__ffs(q) - 1) * kAggStride + n]);
-                const float4 acc = make_float4(a01.x, a01.y, a23.x, a23.y);
-                const int k = k0 + n;
-                const int off = D == 3 ? ((k / 9) * res + (k / 3) % 3) * res + k % 3 : (k / 3) * res + k % 3;
-                atomicAdd(grid + nb + off, acc);
+        // item t = (group t / nk, slab node t % nk): a quarter-warp per group
+        // in full slabs
+        for (int t = lane; t < G * nk; t += 32) {
+            const int gi = t / nk, n = t - gi * nk;
+            const unsigned pm = g_lanes[gi];
+            // the sum in lane order, two components per packed add
+            float2 a01 = make_float2(0.0f, 0.0f), a23 = make_float2(0.0f, 0.0f);
+            for (unsigned q = pm; q; q &= q - 1u) {
+                const float4 c = sm[(__ffs(q) - 1) * kAggStride + n];
+                a01 = __fadd2_rn(a01, make_float2(c.x, c.y));
+                a23 = __fadd2_rn(a23, make_float2(c.z, c.w));
             }
+            atomicAdd(g_base[gi] + stencil_node_offset<D>(k0 + n, res, res2),
+                      make_float4(a01.x, a01.y, a23.x, a23.y));
         }
     }
 }
