@@ -264,7 +264,7 @@ __device__ __forceinline__ void forward_particle(const Params& P, const StepArgs
         }
         if constexpr (AGG) {
             // node (o0, .., ol) receives w (mp, u + A o), w = (w0 w1) w2 as below
-            scatter_aggregated<D>(nb, inst, active, ai, P.res, sm, [&](int k) {
+            scatter_aggregated<D>(nb, inst, active, a.acc, P.nodes, P.res, sm, [&](int k) {
                 const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
                 const int ol = stencil_offset<D>(k, D - 1);
                 const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];
@@ -811,7 +811,7 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
         }
         if constexpr (AGG) {
             // node (o0, .., ol) receives w sv, sv = q + kappa dx Ct o, as above
-            scatter_aggregated<D>(nb, inst, active, Vbi, P.res, sm, [&](int k) {
+            scatter_aggregated<D>(nb, inst, active, a.Vbar, P.nodes, P.res, sm, [&](int k) {
                 const int o0 = stencil_offset<D>(k, 0), om = stencil_offset<D>(k, 1 % D);
                 const int ol = stencil_offset<D>(k, D - 1);
                 const float pw = D == 2 ? s.w[0][o0] : s.w[0][o0] * s.w[1 % D][om];

@@ -32,8 +32,8 @@ namespace mpm {
 constexpr int kAggSlab = 8;
 constexpr int kAggStride = 9;
 constexpr int kAggValueSlots = kAggStride * 32;  // float4 of node values per warp
-// after the values: per group, its lanes (32 x unsigned) and the address of
-// its base node (32 x float4*): 384 bytes = 24 float4
+// after the values: per group, its lanes (32 x unsigned) and the element
+// offset of its base node from grid0 (32 x long long): 384 bytes = 24 float4
 constexpr int kAggTableSlots = 24;
 constexpr int kAggSlots = kAggValueSlots + kAggTableSlots;  // float4 per warp
 
@@ -70,11 +70,13 @@ __device__ __forceinline__ int stencil_node_offset(int k, int res, int res2) {
 // Every lane of the warp calls this; a lane without a particle passes
 // active = false (its values are not read).  value(k) gives the float4 that
 // stencil node k (last axis fastest) receives from this lane's particle; it
-// is called with every k < 3^D.  grid is the instance's grid, nb the base
-// node, sm this warp's kAggSlots slots.
+// is called with every k < 3^D.  grid0 is instance 0's grid (instance i's
+// starts nodes further on each), nb the base node, sm this warp's kAggSlots
+// slots.  (The atomics address grid0 plus an offset read from the group
+// table, so that they stay global-memory atomics.)
 template <int D, typename Value>
-__device__ __forceinline__ void scatter_aggregated(int nb, int inst, bool active, float4* __restrict__ grid, int res,
-                                                   float4* sm, Value value) {
+__device__ __forceinline__ void scatter_aggregated(int nb, int inst, bool active, float4* __restrict__ grid0,
+                                                   long long nodes, int res, float4* sm, Value value) {
     const int lane = threadIdx.x & 31;
     // instances are < 2^16 and node indices < 2^31, so no active key is ~0 - lane
     const unsigned long long key =
@@ -85,12 +87,12 @@ __device__ __forceinline__ void scatter_aggregated(int nb, int inst, bool active
     const unsigned leaders = __ballot_sync(0xffffffffu, leader);
     const int G = __popc(leaders);
     unsigned* g_lanes = reinterpret_cast<unsigned*>(sm + kAggValueSlots);
-    float4** g_base = reinterpret_cast<float4**>(g_lanes + 32);
+    long long* g_base = reinterpret_cast<long long*>(g_lanes + 32);
     __syncwarp();  // the table's readers in an earlier call are done
     if (leader) {
         const int gi = __popc(leaders & ((1u << lane) - 1u));
         g_lanes[gi] = peers;
-        g_base[gi] = grid + nb;
+        g_base[gi] = (long long)inst * nodes + nb;
     }
     float4* mine = sm + lane * kAggStride;
     constexpr int kNodes = D == 3 ? 27 : 9;
@@ -115,7 +117,7 @@ __device__ __forceinline__ void scatter_aggregated(int nb, int inst, bool active
                 a01 = __fadd2_rn(a01, make_float2(c.x, c.y));
                 a23 = __fadd2_rn(a23, make_float2(c.z, c.w));
             }
-            atomicAdd(g_base[gi] + stencil_node_offset<D>(k0 + n, res, res2),
+            atomicAdd(grid0 + (g_base[gi] + stencil_node_offset<D>(k0 + n, res, res2)),
                       make_float4(a01.x, a01.y, a23.x, a23.y));
         }
     }
