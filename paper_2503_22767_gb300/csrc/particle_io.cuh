@@ -73,11 +73,14 @@ __device__ __forceinline__ void reload_mat(const float* __restrict__ s, int base
         for (int b = 0; b < D; ++b) M[a][b] = reload(s + (long long)(base + a * D + b) * np + p);
 }
 
+// The particle state is read once per kernel (a streaming read, evict-first),
+// so that it does not push the stencil nodes the gathers reuse out of L1
+// (3D locomotion, 1M particles: forward 97.6 -> 95.2 us per launch).
 template <int D>
 __device__ __forceinline__ void load_vec(const float* __restrict__ s, int base, long long np, int p,
                                          float (&v)[D]) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = s[(long long)(base + a) * np + p];
+    for (int a = 0; a < D; ++a) v[a] = __ldcs(s + (long long)(base + a) * np + p);
 }
 
 // Position of particle p: the X slot of the state plus x0 (the state holds
@@ -87,7 +90,7 @@ __device__ __forceinline__ void load_position(const float* __restrict__ s, const
                                               long long np, int p, float (&x)[D]) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const float u = s[(long long)a * np + p];
+        const float u = __ldcs(s + (long long)a * np + p);
         x[a] = x0 ? __fadd_rn(u, __ldg(x0 + (long long)a * np + p)) : u;
     }
 }
@@ -98,7 +101,7 @@ __device__ __forceinline__ void load_mat(const float* __restrict__ s, int base, 
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int b = 0; b < D; ++b) M[a][b] = s[(long long)(base + a * D + b) * np + p];
+        for (int b = 0; b < D; ++b) M[a][b] = __ldcs(s + (long long)(base + a * D + b) * np + p);
 }
 
 template <int D>
