@@ -268,7 +268,8 @@ def run_ours(args):
         tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
 
     if args.options:
-        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "streams": 6, "pdl": 7, "adjoint_blocks": 8, "grid_blocks": 10, "persistent": 11}
+        keys = {"block": 2, "fuse_grid": 3, "graphs": 4, "streams": 6, "pdl": 7, "adjoint_blocks": 8, "grid_blocks": 10, "persistent": 11,
+                "scatter_2d": 13}
         for item in args.options.split(","):
             name, value = item.split("=")
             sim.set_option(keys[name.strip()], int(value))

@@ -235,9 +235,14 @@ enum {
                            and the backward pass on one stream.  Not with solid boxes or a
                            field gradient, nor in 3D without MPM_OPT_GRID_BLOCKS: those keep
                            the chained launches.  0 (default): chained launches */
-    MPM_OPT_SPIN_LIMIT = 12 /* polls (>= 1) a persistent kernel's barrier wait makes before it
+    MPM_OPT_SPIN_LIMIT = 12, /* polls (>= 1) a persistent kernel's barrier wait makes before it
                            gives up, sets the timeout flag and returns: the call then fails
                            with MPM_ERR_TIMEOUT and the handle stays usable (default 2^22) */
+    MPM_OPT_SCATTER_2D = 13 /* 2D P2G of the fused forward particle kernel (Eq. 14-15): 1: the
+                           lanes of a warp that share a base node sum their node values in
+                           shared memory and issue one atomic per node (as 3D always does);
+                           0 (default): one float4 atomic per particle and node.  Without
+                           solid boxes or a field gradient only; no effect in 3D. */
 };
 /* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
 int mpm_set_option(mpm_handle* h, int key, long long value);
@@ -308,9 +313,9 @@ int mpm_field_gradient_grad(mpm_handle* h, float* g_grad, void* cuda_stream);
  * library).  Times forward + backward passes over the first sample_substeps
  * substeps (0 = two checkpoint segments) of the inputs staged by the last
  * mpm_forward, for every combination of block size {64, 128, 256}, grid
- * fusion {0, 1} and adjoint register budget {2, 3, and 4 in 2D}, and keeps
- * the fastest.  With a
- * non-NULL cache_path, results are read from and written to that JSON file,
+ * fusion {0, 1}, adjoint register budget {2, 3, and 4 in 2D} and, in 2D, the
+ * P2G scatter {per-lane, aggregated} (MPM_OPT_SCATTER_2D), and keeps the
+ * fastest.  With a non-NULL cache_path, results are read from and written to that JSON file,
  * keyed by dim, grid_res, particle count (rounded up to a power of 2),
  * instances and checkpoint interval; a cache hit applies the stored choice
  * without timing.  The tuning runs overwrite the forward result: call

@@ -33,6 +33,7 @@ struct Params {
     float gravity[3];
     int pdl;  // per-substep kernels launched with programmatic dependent launch
     int adj_blocks;  // register budget of the adjoint particle kernel: 256-thread blocks per SM (2 or 3)
+    int agg2;        // 2D: the fused forward kernel's P2G scatter is aggregated over same-node lanes
     // solid boxes of Eq. 18 beyond the walls and a non-uniform applied field
     // (device memory), or null for neither.  One pointer keeps the parameter
     // block (and the transfer kernels' register allocation) as small as

@@ -458,6 +458,7 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     // defaults as the autotuner picks them on the 2D and 3D workloads: the
     // 80-register adjoint budget in 3D
     P.adj_blocks = h->dim == 3 ? 3 : 2;
+    P.agg2 = 0;
 
     const long long S = (long long)h->ncomp * h->np;
     const int d = h->dim;
@@ -1199,7 +1200,7 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
 // autotuner: time candidate launch configurations, keep the fastest
 // ---------------------------------------------------------------------------
 struct TuneChoice {
-    int block, fuse, adj;
+    int block, fuse, adj, agg;  // agg: MPM_OPT_SCATTER_2D (2D)
     double ms;
 };
 
@@ -1224,9 +1225,9 @@ bool cache_lookup(const char* path, const std::string& sig, TuneChoice* out) {
         if (!p) continue;
         TuneChoice c{};
         if (std::sscanf(p + key.size(),
-                        "{\"block\": %d, \"fuse\": %d, \"adj\": %d, \"ms\": %lf}",
-                        &c.block, &c.fuse, &c.adj, &c.ms) == 4 &&
-            c.adj >= 2 && c.adj <= 4) {
+                        "{\"block\": %d, \"fuse\": %d, \"adj\": %d, \"agg\": %d, \"ms\": %lf}",
+                        &c.block, &c.fuse, &c.adj, &c.agg, &c.ms) == 5 &&
+            c.adj >= 2 && c.adj <= 4 && (c.agg == 0 || c.agg == 1)) {
             *out = c;
             found = true;
         }
@@ -1251,8 +1252,8 @@ void cache_store(const char* path, const std::string& sig, const TuneChoice& c) 
     }
     char buf[512];
     std::snprintf(buf, sizeof buf,
-                  "  \"%s\": {\"block\": %d, \"fuse\": %d, \"adj\": %d, \"ms\": %.4f}",
-                  sig.c_str(), c.block, c.fuse, c.adj, c.ms);
+                  "  \"%s\": {\"block\": %d, \"fuse\": %d, \"adj\": %d, \"agg\": %d, \"ms\": %.4f}",
+                  sig.c_str(), c.block, c.fuse, c.adj, c.agg, c.ms);
     lines.push_back(buf);
     std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
@@ -1270,6 +1271,7 @@ void apply_choice(mpm_handle* h, const TuneChoice& c) {
     h->fuse_fwd = (c.fuse & 1) != 0;
     h->fuse_adj = (c.fuse & 2) != 0;
     h->P.adj_blocks = c.adj;
+    h->P.agg2 = c.agg;
 }
 
 int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cudaStream_t st,
@@ -1293,11 +1295,12 @@ int autotune_impl(mpm_handle* h, const char* cache_path, int sample_substeps, cu
     int rc = MPM_OK;
     for (int block : {64, 128, 256}) {
         for (int fuse : {0, 1}) {
-            // register budgets: 2 and 3 blocks per SM, and 4 in 2D
+            // register budgets: 2 and 3 blocks per SM, and 4 in 2D; in 2D
+            // also the P2G scatter with and without aggregation
             const int n_adj = h->dim == 2 ? 3 : 2;
-            for (int cand = 0; cand < n_adj; ++cand) {
-                const int adj = 2 + cand;
-                TuneChoice c{block, fuse, adj, 0.0};
+            for (int cand = 0; cand < n_adj * (h->dim == 2 ? 2 : 1); ++cand) {
+                const int adj = 2 + cand % n_adj, agg = cand / n_adj;
+                TuneChoice c{block, fuse, adj, agg, 0.0};
                 apply_choice(h, c);
                 h->tune_T = sample;
                 // first run captures the graphs; then time the best of 3
@@ -1613,6 +1616,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (h->P.adj_blocks != (int)value) drop_graphs(h);
             h->P.adj_blocks = (int)value;
             return MPM_OK;
+        case MPM_OPT_SCATTER_2D:
+            if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "scatter_2d must be 0 or 1");
+            if (h->P.agg2 != (int)value) drop_graphs(h);
+            h->P.agg2 = (int)value;
+            return MPM_OK;
         case MPM_OPT_PDL:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "pdl must be 0 or 1");
             if (h->P.pdl != (int)value) drop_graphs(h);
@@ -1657,6 +1665,7 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_GRID_BLOCKS: *value = h->grid_blocks ? 1 : 0; return MPM_OK;
         case MPM_OPT_PERSISTENT: *value = h->persistent ? 1 : 0; return MPM_OK;
         case MPM_OPT_SPIN_LIMIT: *value = h->spin_limit; return MPM_OK;
+        case MPM_OPT_SCATTER_2D: *value = h->P.agg2; return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

@@ -50,8 +50,10 @@ inline int particle_blocks(long long n, int block) { return (int)((n + block - 1
 // EXT: P.ext is set (solid boxes or a non-uniform field); without it the
 // code for them is left out.  CHAIN: the kernel is one launch of a chain
 // with programmatic dependent launch (k_forward); a persistent kernel calls
-// this between its own grid-wide barriers instead.
-template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT, bool CHAIN>
+// this between its own grid-wide barriers instead.  AGG_P2G: the P2G scatter
+// is aggregated over the lanes of one base node (scatter_aggregated).
+template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT, bool CHAIN,
+          bool AGG_P2G = aggregate_scatter<D>()>
 __device__ __forceinline__ void forward_particle(const Params& P, const StepArgs& a, int p, float4* sm) {
     using L = Layout<D>;
     // Early loads: with the grid operation in its own kernel, this kernel's
@@ -62,7 +64,7 @@ __device__ __forceinline__ void forward_particle(const Params& P, const StepArgs
     // overlap the grid kernel's tail.
     constexpr bool kEarly = CHAIN && G2P && !FUSE;
     // the P2G scatter is aggregated over the lanes of one cell (scatter_aggregated)
-    constexpr bool AGG = P2G && aggregate_scatter<D>();
+    constexpr bool AGG = P2G && AGG_P2G;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
     const long long np = P.np;
@@ -313,12 +315,12 @@ __device__ __forceinline__ void forward_particle(const Params& P, const StepArgs
 }
 
 // 3D: at most 64 registers (32 warps per SM) to keep more gathers in flight
-template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT>
+template <int D, bool G2P, bool P2G, bool WRITE_ALL, bool FUSE, bool EXT, bool AGG = aggregate_scatter<D>()>
 __global__ void __launch_bounds__(256, D == 3 ? kMinBlocksForward3 : kMinBlocksForward2)
     k_forward(Params P, StepArgs a) {
     extern __shared__ float4 s_warp[];
-    forward_particle<D, G2P, P2G, WRITE_ALL, FUSE, EXT, true>(
-        P, a, blockIdx.x * blockDim.x + threadIdx.x, s_warp + (threadIdx.x >> 5) * warp_slots<D, P2G>());
+    forward_particle<D, G2P, P2G, WRITE_ALL, FUSE, EXT, true, AGG>(
+        P, a, blockIdx.x * blockDim.x + threadIdx.x, s_warp + (threadIdx.x >> 5) * warp_slots<D, P2G, AGG>());
 }
 
 
@@ -856,6 +858,13 @@ static cudaError_t forward_d(bool g2p, bool p2g, bool all, const Params& P, cons
         if (ext) {
             if (all) return go(k_forward<D, true, true, true, FUSE, true>, smem_p2g);
             return go(k_forward<D, true, true, false, FUSE, true>, smem_p2g);
+        }
+        if constexpr (D == 2) {
+            if (P.agg2) {  // the aggregated 2D P2G (Params::agg2)
+                const size_t smem_agg = warps * warp_slots<D, true, true>() * sizeof(float4);
+                if (all) return go(k_forward<D, true, true, true, FUSE, false, true>, smem_agg);
+                return go(k_forward<D, true, true, false, FUSE, false, true>, smem_agg);
+            }
         }
         if (all) return go(k_forward<D, true, true, true, FUSE, false>, smem_p2g);
         return go(k_forward<D, true, true, false, FUSE, false>, smem_p2g);

@@ -37,20 +37,22 @@ constexpr int kAggValueSlots = kAggStride * 32;  // float4 of node values per wa
 constexpr int kAggTableSlots = 24;
 constexpr int kAggSlots = kAggValueSlots + kAggTableSlots;  // float4 per warp
 
-// 3D only: with 4 particles per cell in 2D the exchange cost more than the
-// atomics it saved on every 2D workload measured (2D locomotion 15.8 -> 17.4
-// ms per design iteration); in 3D it took the forward kernel from 98 to 59 us
-// per launch (600,000 particles).
+// Always in 3D (the forward kernel went from 98 to 59 us per launch on
+// 600,000 particles).  In 2D, with 4 particles per cell, it pays only for
+// large launches: the forward P2G of the 64-walker batch (1.5M particles) went
+// from 81 to 72 us, while the single 30,000-particle walker lost 10% per
+// design iteration and the 2D G2P^T lost on both.  2D P2G takes it per handle
+// (Params::agg2, chosen by the autotuner); 2D G2P^T never does.
 template <int D>
 __host__ __device__ constexpr bool aggregate_scatter() {
     return D == 3;
 }
 
-// float4 slots of dynamic shared memory per warp of a particle kernel that
-// runs the aggregated scatter (none otherwise)
-template <int D, bool SCATTER>
+// float4 slots of dynamic shared memory per warp of a particle kernel whose
+// scatter is aggregated (AGG), none otherwise
+template <int D, bool SCATTER, bool AGG = aggregate_scatter<D>()>
 __host__ __device__ constexpr int warp_slots() {
-    return SCATTER && aggregate_scatter<D>() ? kAggSlots : 0;
+    return SCATTER && AGG ? kAggSlots : 0;
 }
 
 // Offset of stencil node k (last axis fastest, k < 3^D) from the base node on

@@ -230,7 +230,7 @@ class Simulator:
                           ("graphs", B.MPM_OPT_GRAPHS),
                           ("streams", B.MPM_OPT_STREAMS), ("pdl", B.MPM_OPT_PDL),
                           ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS), ("grid_blocks", B.MPM_OPT_GRID_BLOCKS),
-                          ("persistent", B.MPM_OPT_PERSISTENT)):
+                          ("persistent", B.MPM_OPT_PERSISTENT), ("scatter_2d", B.MPM_OPT_SCATTER_2D)):
             v = ctypes.c_longlong()
             self._check(self.lib.mpm_get_option(self.handle, key, ctypes.byref(v)), "mpm_get_option")
             out[name] = v.value

@@ -31,6 +31,13 @@ def test_header_and_binding_agree():
     assert _declared_functions() == sorted(B.EXPORTS)
 
 
+def test_option_keys_agree():
+    """Every MPM_OPT_* key of the header has the same value in the binding."""
+    text = open(os.path.join(ROOT, "include", "mpm.h")).read()
+    keys = dict((k, int(v)) for k, v in re.findall(r"\b(MPM_OPT_\w+)\s*=\s*(\d+)", text))
+    assert keys and {k: getattr(B, k, None) for k in keys} == keys
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in _declared_functions():
         assert hasattr(lib, name), name

@@ -332,13 +332,14 @@ def test_block_size_does_not_change_results(block):
 def test_execution_modes(key, fuse, graphs, mix):
     """Grid operation fused into the particle kernels or not, passes replayed
     as CUDA graphs or launched directly, one or two streams, PDL on or off,
-    each adjoint register budget (2, 3, 4 blocks per SM), and (3D) grid
-    kernels over the listed node blocks or over every node: same results,
-    twice in a row."""
+    each adjoint register budget (2, 3, 4 blocks per SM), (3D) grid kernels
+    over the listed node blocks or over every node, and (2D) the P2G scatter
+    per lane or aggregated: same results, twice in a row."""
     w, of, ob = _oracle(key)
     sim_opts = {B.MPM_OPT_FUSE_GRID: fuse, B.MPM_OPT_GRAPHS: graphs,
                 B.MPM_OPT_STREAMS: 1 + (fuse + graphs + mix) % 2, B.MPM_OPT_PDL: (fuse + mix) % 2,
-                B.MPM_OPT_ADJOINT_BLOCKS: 2 + (fuse + graphs) % 3, B.MPM_OPT_GRID_BLOCKS: (graphs + mix + 1) % 2}
+                B.MPM_OPT_ADJOINT_BLOCKS: 2 + (fuse + graphs) % 3, B.MPM_OPT_GRID_BLOCKS: (graphs + mix + 1) % 2,
+                B.MPM_OPT_SCATTER_2D: (fuse + graphs) % 2}
     for _ in range(2):
         g = run_gpu(w, options=sim_opts)
         assert_state(g, of, w)
