@@ -9,7 +9,9 @@ ones that see an error in the motion); gradients per design block: cosine >=
 bit-exact.  The long horizons run the oracle on every host core (its threaded
 passes equal the serial ones bit for bit).
 """
+import ctypes
 import functools
+import os
 
 import numpy as np
 import pytest
@@ -346,6 +348,60 @@ def test_execution_modes(key, fuse, graphs, mix):
         assert_grads(g, ob, w)
 
 
+
+@pytest.mark.parametrize("resident,streams,gb", [(1, 2, 1), (2, 2, 1), (3, 2, 1), (1, 1, 0), (3, 1, 1), (2, 2, 0)])
+@pytest.mark.parametrize("key", ["walker2d_128_s0.5_300", "walker3d_48_s0.25_60"])
+def test_resident_segments_match_oracle(key, resident, streams, gb):
+    """MPM_OPT_RESIDENT_SEGMENTS: the forward pass stores the last r of the
+    three checkpoint segments and the backward pass skips their
+    recomputation (one stream or two; 3D grid kernels over listed blocks or
+    every node): the same results as the oracle, twice in a row."""
+    w, of, ob = _oracle(key)
+    opts = {B.MPM_OPT_RESIDENT_SEGMENTS: resident, B.MPM_OPT_STREAMS: streams, B.MPM_OPT_GRID_BLOCKS: gb}
+    for _ in range(2):
+        g = run_gpu(w, options=opts)
+        assert_state(g, of, w)
+        assert_grads(g, ob, w)
+
+
+def test_resident_segments_forward_twice_and_option_changes():
+    """Two forward passes before one backward, a resident count above the
+    number of segments (capped), a change of the count (which drops the last
+    forward), and a switch between listed blocks and every node: the handle
+    keeps giving the oracle's results."""
+    w, of, ob = _oracle("walker3d_48_s0.25_60")
+    args = (_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field))
+    kw = dict(target=_t(w.target), v0=_t(w.v0), want_x=True)
+    sim = Simulator(w.cfg, options={B.MPM_OPT_RESIDENT_SEGMENTS: 7})
+    assert sim.options()["resident_segments"] == 3  # three segments of 25 substeps
+    seg_bytes = ctypes.c_longlong()
+    assert sim.lib.mpm_get_option(sim.handle, B.MPM_OPT_SEGMENT_BYTES, ctypes.byref(seg_bytes)) == B.MPM_OK
+    assert seg_bytes.value > 0
+    with pytest.raises(B.MpmError):
+        sim.set_option(B.MPM_OPT_SEGMENT_BYTES, 1)
+
+    def check():
+        _, x = sim.forward(*args, **kw)
+        g_phi, g_mag, g_field = sim.backward(torch.ones(w.cfg.n_instances, device="cuda"))
+        assert rel_l2(x.cpu().numpy(), of["x"]) <= STATE_TOL
+        assert_grads(dict(g_phi=g_phi.cpu().numpy(), g_mag=g_mag.cpu().numpy(), g_field=g_field.cpu().numpy()),
+                     ob, w)
+
+    sim.forward(*args, **kw)
+    check()  # forward, forward, backward
+    sim.set_option(B.MPM_OPT_RESIDENT_SEGMENTS, 1)
+    with pytest.raises(B.MpmError):  # the count changed: the last forward is gone
+        sim.backward(torch.ones(w.cfg.n_instances, device="cuda"))
+    check()
+    sim.set_option(B.MPM_OPT_GRID_BLOCKS, 0)
+    check()
+    sim.set_option(B.MPM_OPT_GRID_BLOCKS, 1)
+    check()
+    sim.set_option(B.MPM_OPT_RESIDENT_SEGMENTS, 0)
+    assert sim.options()["resident_segments"] == 0
+    check()
+    sim.close()
+
 def test_graph_replay_with_new_inputs():
     """A replayed graph reads the new call's inputs, not the captured ones."""
     import oracle
@@ -463,3 +519,47 @@ def test_precision_report(name):
     assert all(v <= STATE_TOL for v in worst.values()), worst
     assert row["cos_min"] >= GRAD_COS
     assert max(row["g_phi"], row["g_mag"], row["g_field"]) <= GRAD_REL
+
+
+# Full-horizon parity of the two 3D workloads.  The FP64 oracle needs about
+# 25 minutes of the host's cores for both, so these run only on request:
+#   MPM_LONG_PARITY=1 python -m pytest tests/test_gpu_parity.py -k full_horizon -s
+LONG_CASES = {
+    # forward curve to the full 5,000 substeps: 50 checkpoint segments, each
+    # with its cell sort and permutation, floor contact throughout
+    "C4 walker3d 128^3, ~1,000,000 p, 5,000 steps, K = 100":
+        (lambda: W.walker_3d(seed=0), (1000, 2000, 3000, 4000, 5000), None),
+    # forward curve and gradients over the full 1,000 substeps: the checkpointed
+    # adjoint crosses 10 segments with the two-stream recomputation
+    "C3 plate3d 64^3, 3 x 200,000 p, 1,000 steps, K = 100":
+        (lambda: W.plate_3d(seed=0), (250, 500, 750, 1000), 1000),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("MPM_LONG_PARITY") != "1",
+                    reason="full-horizon 3D parity (about 25 minutes of oracle time): set MPM_LONG_PARITY=1")
+@pytest.mark.parametrize("name", list(LONG_CASES))
+def test_full_horizon_parity(name):
+    """FP32 GPU state against the FP64 oracle along the whole horizon of the
+    3D workloads, with the workloads' own checkpoint interval (and for C3 the
+    gradients over the whole horizon), at the state and gradient tolerances."""
+    import oracle
+    make, curve, t_grad = LONG_CASES[name]
+    full = make()
+    ref = oracle_states(full, curve)
+    worst = {}
+    for h in curve:
+        g = run_gpu(W.with_steps(full, h, checkpoint_every=100), backward=False)
+        errs = state_errors(g, ref[h], W.with_steps(full, h))
+        print("CURVE |", name, "| step", h, "|", " | ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+        for k, v in errs.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    assert all(v <= STATE_TOL for v in worst.values()), worst
+    if t_grad:
+        wg = W.with_steps(full, t_grad, checkpoint_every=100)
+        g = run_gpu(wg)
+        with oracle.threads():
+            ob = oracle.backward(wg, ckpt_every=25)
+        res = assert_grads(g, ob, wg)
+        print("GRADIENTS |", name, "|", " | ".join(f"{k} cos {c:.7f} rel {r:.2e}" for k, (c, r) in res.items()))
