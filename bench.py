@@ -52,6 +52,15 @@ WORKLOADS = {
 }
 
 
+# Device memory a design iteration may hold (bytes): the 3D locomotion
+# configuration's 180 GB allowance, used by every workload to keep its last
+# checkpoint segments resident (their recomputation skipped), except the 2D
+# locomotion workload, whose configuration fixes recomputation every 100
+# substeps.
+RESIDENT_BUDGET = {"walker2d_128": 0}
+DEFAULT_BUDGET = 180e9
+
+
 def workload(name="walker3d_128", seed=0, substeps=None, checkpoint_every=None):
     """A named workload; ``substeps`` shortens the horizon and
     ``checkpoint_every`` overrides the segment length (profiling runs on a
@@ -276,6 +285,12 @@ def run_ours(args):
         if tuned is not None:
             tuned = {**sim.options(), "tuning_s": tuned["tuning_s"], "overridden": args.options}
 
+    budget = (args.resident_budget_gb * 1e9 if args.resident_budget_gb is not None
+              else RESIDENT_BUDGET.get(args.workload, DEFAULT_BUDGET))
+    resident = sim.set_resident_budget(budget) if budget > 0 else 0
+    if tuned is not None:
+        tuned["resident_segments"] = resident
+
     # the timed region runs the passes as a user would: no timing events inside
     # the captured graphs (they would break the launch overlap they measure)
     sim.set_option(1, 0)
@@ -447,7 +462,11 @@ def run_ours(args):
 
     sequential = None
     if cfg.n_instances > 1 and not args.no_sequential and world == 1:
-        sequential = run_sequential(w, dev, g, ps)
+        # the single-instance runs keep as many segments resident as the batch
+        # did; the batch's sets are released meanwhile
+        sim.set_option(14, 0)
+        sequential = run_sequential(w, dev, g, ps, resident)
+        sim.set_option(14, resident)
     codesign = None
     if cfg.n_designs == 1 and not args.no_codesign and world == 1:
         codesign = run_codesign(w, sim, dev, args.steps)
@@ -472,6 +491,7 @@ def run_ours(args):
         "config": {**workload_desc(w, args.workload), "parallelism": (f"instances sharded over {world} ranks" if plan is not None else
                                    f"replicas x{world}" if world > 1 else "single GPU"),
                    "launch": tuned if tuned else sim_options,
+                   "resident_budget_gb": round(budget / 1e9, 1),
                    "l2": "256 MB buffer written between timed iterations (outside the timed events)"},
         "ms_per_design_iteration": round(ms_per_step, 3),
         "loss": loss_val,
@@ -494,7 +514,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_sequential(w, dev, batched_grads, ps):
+def run_sequential(w, dev, batched_grads, ps, resident=0):
     """The batch's instances as single-instance simulations run one after
     another on the same stream: same kernels, launch options tuned once on the
     first instance.  Returns their throughput and the gradient difference
@@ -515,8 +535,16 @@ def run_sequential(w, dev, batched_grads, ps):
     first[1].forward(*first[2], **first[3])
     tuned = first[1].autotune(sample_substeps=min(cfg.n_steps, 200))
     for _, sim, _, _ in runs[1:]:
-        for key, name in ((2, "block"), (3, "fuse_grid"), (8, "adjoint_blocks")):
+        for key, name in ((2, "block"), (3, "fuse_grid"), (8, "adjoint_blocks"), (13, "scatter_2d")):
             sim.set_option(key, tuned[name])
+    for _, sim, _, _ in runs:
+        try:
+            sim.set_option(14, resident)
+        except Exception:  # device memory short: recompute every segment
+            resident = 0
+            for _, s2, _, _ in runs:
+                s2.set_option(14, 0)
+            break
     one = torch.ones(1, device=dev)
 
     def sweep():
@@ -547,7 +575,9 @@ def run_sequential(w, dev, batched_grads, ps):
     for _, sim, _, _ in runs:
         sim.close()
     return {"value": round(ps / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 3),
-            "instances": cfg.n_instances, "launch": {k: tuned[k] for k in ("block", "fuse_grid", "adjoint_blocks")},
+            "instances": cfg.n_instances,
+            "launch": {**{k: tuned[k] for k in ("block", "fuse_grid", "adjoint_blocks", "scatter_2d")},
+                       "resident_segments": resident},
             "g_phi_rel_l2_vs_batched": float(np.sqrt(num / max(den, 1e-300))),
             "what": "each instance as its own single-instance simulation, one after another"}
 
@@ -705,6 +735,9 @@ def main(argv=None):
                          "(names as in Simulator.options())")
     ap.add_argument("--substeps", type=int, default=0,
                     help="horizon of the timed workload (0: the configuration's full horizon)")
+    ap.add_argument("--resident-budget-gb", type=float, default=None,
+                    help="device memory (GB) the handle may hold, the rest of it for resident checkpoint "
+                         "segments (default: 180, 0 for walker2d_128)")
     ap.add_argument("--checkpoint-every", type=int, default=0,
                     help="checkpoint segment length (0: the configuration's own)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end iterations (default min(steps, 3))")

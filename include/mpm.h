@@ -238,13 +238,26 @@ enum {
     MPM_OPT_SPIN_LIMIT = 12, /* polls (>= 1) a persistent kernel's barrier wait makes before it
                            gives up, sets the timeout flag and returns: the call then fails
                            with MPM_ERR_TIMEOUT and the handle stays usable (default 2^22) */
-    MPM_OPT_SCATTER_2D = 13 /* 2D P2G of the fused forward particle kernel (Eq. 14-15): 1: the
+    MPM_OPT_SCATTER_2D = 13, /* 2D P2G of the fused forward particle kernel (Eq. 14-15): 1: the
                            lanes of a warp that share a base node sum their node values in
                            shared memory and issue one atomic per node (as 3D always does);
                            0 (default): one float4 atomic per particle and node.  Without
                            solid boxes or a field gradient only; no effect in 3D. */
+    MPM_OPT_RESIDENT_SEGMENTS = 14, /* r >= 0 (capped at the number of checkpoint segments): the
+                           forward pass stores every state and grid of the last r segments, as
+                           the recomputation of the checkpointed adjoint would, and the
+                           backward pass runs their adjoint without recomputing them.  Setting
+                           it reserves r segment sets of device memory (MPM_OPT_SEGMENT_BYTES
+                           each; MPM_ERR_OOM if that fails, leaving none) and drops the last
+                           forward: call mpm_forward again before mpm_backward.  0 (default)
+                           releases them.  Not used by the persistent passes or while
+                           autotuning. */
+    MPM_OPT_SEGMENT_BYTES = 15 /* read only: device bytes of one resident segment set (K + 1
+                           states, K accumulator and K velocity grids, the segment's design
+                           and initial positions, and in 3D a node-block list) */
 };
-/* Errors: MPM_ERR_ARG for an unknown key or a value out of range. */
+/* Errors: MPM_ERR_ARG for an unknown key or a value out of range; MPM_ERR_OOM (resident
+   segments). */
 int mpm_set_option(mpm_handle* h, int key, long long value);
 /* Current value of an option.  Errors: MPM_ERR_ARG. */
 int mpm_get_option(const mpm_handle* h, int key, long long* value);

@@ -23,6 +23,8 @@ MPM_OPT_GRID_BLOCKS = 10
 MPM_OPT_PERSISTENT = 11
 MPM_OPT_SPIN_LIMIT = 12
 MPM_OPT_SCATTER_2D = 13
+MPM_OPT_RESIDENT_SEGMENTS = 14
+MPM_OPT_SEGMENT_BYTES = 15
 STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_CUDA", -3: "MPM_ERR_OOM",
                 -4: "MPM_ERR_STATE", -5: "MPM_ERR_NUMERIC", -6: "MPM_ERR_DOMAIN",
                 -7: "MPM_ERR_TIMEOUT"}

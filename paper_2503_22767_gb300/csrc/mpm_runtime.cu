@@ -133,6 +133,26 @@ struct mpm_handle {
     int4* blk_wbox = nullptr; // [4][n_wbox]
     bool seg_dirty = false;   // a backward pass ran over every node: the segment accumulators are not zero
 
+    // --- resident segments (MPM_OPT_RESIDENT_SEGMENTS) ---
+    // The forward pass stores the trajectory of the last n_res checkpoint
+    // segments into sets of their own (states, accumulators, grid velocities,
+    // current-order design and x0, 3D lists 4 .. 4 + n_res - 1), and the
+    // backward pass runs their adjoint without recomputing them.
+    int n_res = 0;
+    std::vector<void*> res_allocs;
+    long long res_bytes = 0;
+    float* res_state = nullptr;  // [n_res][K + 1][S]
+    float4* res_acc = nullptr;   // [n_res][K][G]
+    float4* res_V = nullptr;     // [n_res][K][G]
+    float* res_phi = nullptr;    // [n_res][np]
+    float* res_mag = nullptr;    // [n_res][d][np]
+    float* res_x0 = nullptr;     // [n_res][d][np]
+    int* res_flag = nullptr;     // [n_res][n_blocks]
+    int* res_list = nullptr;     // [n_res][n_blocks]
+    int* res_count = nullptr;    // [n_res]
+    int4* res_wbox = nullptr;    // [n_res][n_wbox]
+    bool res_dirty = false;      // resident accumulators set outside their lists
+
     // --- persistent passes (MPM_OPT_PERSISTENT) ---
     bool persistent = false;
     long long spin_limit = 1LL << 22;  // polls before a grid-barrier wait gives up
@@ -221,6 +241,51 @@ void drop_graphs(mpm_handle* h) {
     }
 }
 
+// Resident segment sets (MPM_OPT_RESIDENT_SEGMENTS), reserved after creation
+// and released on change or destruction.
+template <typename T>
+int ralloc(mpm_handle* h, T** p, long long count) {
+    *p = nullptr;
+    size_t bytes = sizeof(T) * (size_t)std::max(1LL, count);
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "cudaMalloc of " + std::to_string(bytes) + " bytes for resident segments failed: " +
+                 cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA;
+    }
+    h->res_allocs.push_back(ptr);
+    h->res_bytes += (long long)bytes;
+    h->device_bytes += (long long)bytes;
+    *p = (T*)ptr;
+    return MPM_OK;
+}
+
+// Device bytes of one resident segment set: K + 1 states, K accumulators and
+// K grid velocities, the current-order design and x0, and in 3D one
+// node-block list.
+long long resident_set_bytes(const mpm_handle* h) {
+    const long long S = (long long)h->ncomp * h->np, G = h->total_nodes;
+    long long b = (long long)sizeof(float) * S * (h->K + 1) + 2LL * (long long)sizeof(float4) * G * h->K +
+                  (long long)sizeof(float) * (1 + 2 * h->dim) * h->np;
+    if (h->blocks) b += (long long)sizeof(int) * (2 * h->n_blocks + 1) + (long long)sizeof(int4) * h->n_wbox;
+    return b;
+}
+
+void free_resident(mpm_handle* h) {
+    for (void* p : h->res_allocs) cudaFree(p);
+    h->res_allocs.clear();
+    h->device_bytes -= h->res_bytes;
+    h->res_bytes = 0;
+    h->n_res = 0;
+    h->res_state = h->res_phi = h->res_mag = h->res_x0 = nullptr;
+    h->res_acc = h->res_V = nullptr;
+    h->res_flag = h->res_list = h->res_count = nullptr;
+    h->res_wbox = nullptr;
+    h->res_dirty = false;
+}
+
 void free_all(mpm_handle* h) {
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -233,6 +298,7 @@ void free_all(mpm_handle* h) {
     }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
+    free_resident(h);
     for (int c = 0; c < kNumClasses; ++c) {
         for (auto& e : h->events[c]) {
             if (e.a) cudaEventDestroy(e.a);
@@ -240,6 +306,43 @@ void free_all(mpm_handle* h) {
         }
         h->events[c].clear();
     }
+}
+
+// Reserve r resident segment sets (0 releases them); r is capped at the
+// number of segments.  The forward and backward passes change shape, so the
+// captured graphs and the last forward are dropped.
+int set_resident(mpm_handle* h, int r) {
+    r = std::max(0, std::min(r, h->n_seg));
+    if (r == h->n_res) return MPM_OK;
+    drop_graphs(h);
+    h->forward_done = false;
+    free_resident(h);
+    if (r == 0) return MPM_OK;
+    const long long S = (long long)h->ncomp * h->np, G = h->total_nodes;
+    int rc;
+    if ((rc = ralloc(h, &h->res_state, r * S * (h->K + 1))) || (rc = ralloc(h, &h->res_acc, r * G * h->K)) ||
+        (rc = ralloc(h, &h->res_V, r * G * h->K)) || (rc = ralloc(h, &h->res_phi, r * h->np)) ||
+        (rc = ralloc(h, &h->res_mag, r * h->dim * h->np)) || (rc = ralloc(h, &h->res_x0, r * h->dim * h->np))) {
+        free_resident(h);
+        return rc;
+    }
+    if (h->blocks && ((rc = ralloc(h, &h->res_flag, r * h->n_blocks)) ||
+                      (rc = ralloc(h, &h->res_list, r * h->n_blocks)) || (rc = ralloc(h, &h->res_count, r)) ||
+                      (rc = ralloc(h, &h->res_wbox, r * h->n_wbox)))) {
+        free_resident(h);
+        return rc;
+    }
+    // the sets start as the lists expect them: accumulators, flags and counts zero
+    cudaError_t e = cudaMemset(h->res_acc, 0, sizeof(float4) * r * G * h->K);
+    if (e == cudaSuccess && h->blocks) e = cudaMemset(h->res_flag, 0, sizeof(int) * r * h->n_blocks);
+    if (e == cudaSuccess && h->blocks) e = cudaMemset(h->res_count, 0, sizeof(int) * r);
+    if (e == cudaSuccess && h->blocks) e = cudaMemset(h->res_wbox, 0, sizeof(int4) * r * h->n_wbox);
+    if (e != cudaSuccess) {
+        free_resident(h);
+        return fail(h, MPM_ERR_CUDA, std::string("resident segments: ") + cudaGetErrorString(e));
+    }
+    h->n_res = r;
+    return MPM_OK;
 }
 
 // algorithmic bytes of one launch (what the method itself must move; see the
@@ -594,6 +697,14 @@ int persist(mpm_handle* h, mpm::PersistKind kind, int cls, double bytes, mpm::Pe
 mpm::ActiveBlocks block_list(const mpm_handle* h, int i) {
     mpm::ActiveBlocks b;
     if (!h->blocks) return b;
+    if (i >= 4) {  // a resident set's list
+        const int r = i - 4;
+        b.flag = h->res_flag + (long long)r * h->n_blocks;
+        b.list = h->res_list + (long long)r * h->n_blocks;
+        b.count = h->res_count + r;
+        b.wbox = h->res_wbox + (long long)r * h->n_wbox;
+        return b;
+    }
     b.flag = h->blk_flag + (long long)i * h->n_blocks;
     b.list = h->blk_list + (long long)i * h->n_blocks;
     b.count = h->blk_count + i;
@@ -619,6 +730,54 @@ int dcopy(mpm_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t 
     MPM_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
     return MPM_OK;
 }
+
+struct SegSet {
+    float* state;   // [K + 1] states
+    float4* acc;    // [K] accumulators
+    float4* V;      // [K] grid velocities
+    float* phi;     // current-order design of the segment
+    float* mag;
+    float* x0;      // current-order initial positions of the segment
+    int list_id;    // 3D: its node-block list (block_list)
+};
+
+SegSet seg_set(mpm_handle* h, int b) {
+    const long long S = (long long)h->ncomp * h->np;
+    const long long G = h->total_nodes;
+    SegSet ss;
+    ss.state = h->seg_state + (long long)b * S * (h->K + 1);
+    ss.acc = h->seg_acc + (long long)b * G * h->K;
+    ss.V = h->seg_V + (long long)b * G * h->K;
+    ss.phi = h->phi_cur + (long long)b * h->np;
+    ss.mag = h->mag_cur + (long long)b * h->dim * h->np;
+    ss.x0 = h->x0_seg + (long long)b * h->dim * h->np;
+    ss.list_id = 2 + b;
+    return ss;
+}
+
+// resident set r (MPM_OPT_RESIDENT_SEGMENTS)
+SegSet res_set(mpm_handle* h, int r) {
+    const long long S = (long long)h->ncomp * h->np;
+    const long long G = h->total_nodes;
+    SegSet ss;
+    ss.state = h->res_state + (long long)r * S * (h->K + 1);
+    ss.acc = h->res_acc + (long long)r * G * h->K;
+    ss.V = h->res_V + (long long)r * G * h->K;
+    ss.phi = h->res_phi + (long long)r * h->np;
+    ss.mag = h->res_mag + (long long)r * h->dim * h->np;
+    ss.x0 = h->res_x0 + (long long)r * h->dim * h->np;
+    ss.list_id = 4 + r;
+    return ss;
+}
+
+// Trailing segments of an n_seg-segment pass that run from resident sets:
+// none while autotuning (a truncated horizon) or in the persistent form.
+int resident_segments(const mpm_handle* h, int n_seg) {
+    if (h->tune_T > 0 || use_persist(h)) return 0;
+    return std::min(h->n_res, n_seg);
+}
+
+int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStream_t st, float* mom = nullptr);
 
 // --- the forward pass: library-owned buffers only, so it can be captured ---
 int forward_pass(mpm_handle* h, cudaStream_t st) {
@@ -653,6 +812,10 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
     int* id_nxt = h->idB;
     const int T = h->tune_T > 0 ? std::min(h->T, h->tune_T) : h->T;
     const int n_seg = (T + h->K - 1) / h->K;
+    // the last n_res segments are stored into resident sets as they run; the
+    // lean substeps end where the first of them begins
+    const int first_res = n_seg - resident_segments(h, n_seg);
+    const int lean_end = std::min(T, first_res * h->K);
     if ((rc = counted(h, 1, [&] {
              return mpm::launch_init_state(d, P, h->st_x0, h->st_v0, cur, id_cur, h->x0_fwd, st);
          })))
@@ -694,6 +857,17 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
                              return mpm::launch_instance_mass(P, h->phi_cur, h->d_inst_off, h->Minst, st);
                          })))
             return rc;
+        if (seg >= first_res) {
+            // a resident segment: every state and grid stored, as a
+            // recomputation would (with the momentum rows of the loss)
+            const SegSet ss = res_set(h, seg - first_res);
+            const int Ks = s1 - s0;
+            // lists: the set holds nothing from an earlier forward pass
+            if (h->blocks && h->grid_blocks && (rc = clear_list(h, ss.list_id, ss.acc, G, Ks, st))) return rc;
+            if ((rc = recompute_segment(h, seg, T, ss, st, h->mom))) return rc;
+            MPM_CUDA(h, cudaMemcpyAsync(cur, ss.state + S * Ks, sizeof(float) * S, cudaMemcpyDeviceToDevice, st));
+            continue;
+        }
         if (persistent) {
             // the whole segment in one cooperative launch
             mpm::PersistArgs pa;
@@ -733,7 +907,7 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
                               return mpm::launch_grid(d, P, h->acc, h->V, nullptr, true, n, st);
                           })))
                 return rc;
-            const bool p2g = n + 1 < T;
+            const bool p2g = n + 1 < lean_end;  // a resident segment runs its own first P2G
             const bool all = n + 1 == s1;
             a.s_in = cur;
             a.s_out = nxt;
@@ -774,31 +948,11 @@ int forward_pass(mpm_handle* h, cudaStream_t st) {
 // recomputation of segment s-1 does not depend on the adjoint of segment s,
 // so with two streams they overlap: the segment buffers and the
 // current-order design come in two sets, used by segment parity.
-struct SegSet {
-    float* state;   // [K + 1] states
-    float4* acc;    // [K] accumulators
-    float4* V;      // [K] grid velocities
-    float* phi;     // current-order design of the segment
-    float* mag;
-    float* x0;      // current-order initial positions of the segment
-    int list_id;    // 3D: its node-block list (block_list)
-};
 
-SegSet seg_set(mpm_handle* h, int b) {
-    const long long S = (long long)h->ncomp * h->np;
-    const long long G = h->total_nodes;
-    SegSet ss;
-    ss.state = h->seg_state + (long long)b * S * (h->K + 1);
-    ss.acc = h->seg_acc + (long long)b * G * h->K;
-    ss.V = h->seg_V + (long long)b * G * h->K;
-    ss.phi = h->phi_cur + (long long)b * h->np;
-    ss.mag = h->mag_cur + (long long)b * h->dim * h->np;
-    ss.x0 = h->x0_seg + (long long)b * h->dim * h->np;
-    ss.list_id = 2 + b;
-    return ss;
-}
-
-int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStream_t st) {
+// mom: the forward pass's momentum rows (locomotion loss), accumulated by the
+// G2P of each substep when the forward pass stores a resident segment; null
+// in the backward pass.
+int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStream_t st, float* mom) {
     const int d = h->dim;
     const Params& P = h->P;
     const long long S = (long long)h->ncomp * h->np;
@@ -865,6 +1019,7 @@ int recompute_segment(mpm_handle* h, int seg, int T, const SegSet& ss, cudaStrea
         a.phi = ss.phi;
         a.mag = ss.mag;
         a.x0 = ss.x0;
+        a.mom = mom;
         a.s_in = state(k);
         a.s_out = state(k + 1);
         a.acc = next_acc;
@@ -1049,26 +1204,36 @@ int backward_pass(mpm_handle* h, cudaStream_t st) {
     const int n_seg = (T + h->K - 1) / h->K;
     float* adj = h->adj;
     float* adj_next = h->adj2;
+    // segments first_res .. n_seg - 1 were stored by the forward pass
+    const int first_res = n_seg - resident_segments(h, n_seg);
     // (the persistent kernels each take the whole GPU: one stream)
-    if (!h->two_streams || n_seg < 2 || use_persist(h)) {
+    if (!h->two_streams || n_seg < 2 || first_res == 0 || use_persist(h)) {
         for (int seg = n_seg - 1; seg >= 0; --seg) {
-            const SegSet ss = seg_set(h, 0);
-            if ((rc = recompute_segment(h, seg, T, ss, st))) return rc;
+            const bool resident = seg >= first_res;
+            const SegSet ss = resident ? res_set(h, seg - first_res) : seg_set(h, 0);
+            if (!resident && (rc = recompute_segment(h, seg, T, ss, st))) return rc;
             if ((rc = adjoint_segment(h, seg, T, ss, adj, adj_next, st))) return rc;
             std::swap(adj, adj_next);
         }
         return MPM_OK;
     }
-    // recomputation one segment ahead on the second stream
+    // recomputation one segment ahead on the second stream; the last
+    // recomputed segment starts at once, beside the resident segments' adjoint
     cudaStream_t aux = h->aux_stream;
     MPM_CUDA(h, cudaEventRecord(h->ev_fork, st));
     MPM_CUDA(h, cudaStreamWaitEvent(aux, h->ev_fork, 0));
-    if ((rc = recompute_segment(h, n_seg - 1, T, seg_set(h, (n_seg - 1) & 1), aux))) return rc;
-    MPM_CUDA(h, cudaEventRecord(h->ev_rec[(n_seg - 1) & 1], aux));
+    const int last = first_res - 1;
+    if ((rc = recompute_segment(h, last, T, seg_set(h, last & 1), aux))) return rc;
+    MPM_CUDA(h, cudaEventRecord(h->ev_rec[last & 1], aux));
     for (int seg = n_seg - 1; seg >= 0; --seg) {
+        if (seg >= first_res) {
+            if ((rc = adjoint_segment(h, seg, T, res_set(h, seg - first_res), adj, adj_next, st))) return rc;
+            std::swap(adj, adj_next);
+            continue;
+        }
         if (seg >= 1) {
             // set (seg-1)&1 was last read by the adjoint of segment seg+1
-            if (seg + 1 <= n_seg - 1) MPM_CUDA(h, cudaStreamWaitEvent(aux, h->ev_adj[(seg + 1) & 1], 0));
+            if (seg + 1 <= last) MPM_CUDA(h, cudaStreamWaitEvent(aux, h->ev_adj[(seg + 1) & 1], 0));
             if ((rc = recompute_segment(h, seg - 1, T, seg_set(h, (seg - 1) & 1), aux))) return rc;
             MPM_CUDA(h, cudaEventRecord(h->ev_rec[(seg - 1) & 1], aux));
         }
@@ -1125,7 +1290,7 @@ int finish(mpm_handle* h, int pass, cudaStream_t st) {
     int rc = check_device_flags(h, st);
     // a pass that stopped early (a timed-out barrier) may leave the segment
     // accumulators and lists set: the next backward pass clears them in full
-    if (rc != MPM_OK && h->blocks) h->seg_dirty = true;
+    if (rc != MPM_OK && h->blocks) h->seg_dirty = h->res_dirty = true;
     if (h->ran_graph[pass]) {
         h->ran_graph[pass] = false;
         int r2 = collect_graph_timing(h, pass);
@@ -1157,7 +1322,17 @@ int forward_impl(mpm_handle* h, const float* x0, const float* v0, const float* p
     if ((rc = dcopy(h, h->mag_d, mag, sizeof(float) * d * h->Nd, st))) return rc;
     if ((rc = dcopy(h, h->field, field, sizeof(float) * h->n_inst * h->T * d, st))) return rc;
     if (target && (rc = dcopy(h, h->target, target, sizeof(float) * d * h->N, st))) return rc;
+    if (h->n_res > 0 && h->blocks && h->grid_blocks && h->res_dirty) {
+        // a pass over every node left the resident accumulators set; the lists expect them zero
+        const long long r = h->n_res;
+        MPM_CUDA(h, cudaMemsetAsync(h->res_acc, 0, sizeof(float4) * r * h->total_nodes * h->K, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->res_flag, 0, sizeof(int) * r * h->n_blocks, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->res_count, 0, sizeof(int) * r, st));
+        MPM_CUDA(h, cudaMemsetAsync(h->res_wbox, 0, sizeof(int4) * r * h->n_wbox, st));
+        h->res_dirty = false;
+    }
     if ((rc = run_pass(h, 0, st))) return rc;
+    if (h->n_res > 0 && h->blocks && !h->grid_blocks) h->res_dirty = true;
     if ((rc = dcopy(h, loss_out, h->st_loss, sizeof(float) * h->n_inst, st))) return rc;
     if (x_out) {
         h->launches++;
@@ -1186,7 +1361,7 @@ int backward_impl(mpm_handle* h, const float* dloss, float* g_phi, float* g_mag,
         h->seg_dirty = false;
     }
     if ((rc = run_pass(h, 1, st))) return rc;
-    if (h->blocks && !h->grid_blocks) h->seg_dirty = true;
+    if (h->blocks && !h->grid_blocks) h->seg_dirty = h->res_dirty = true;
     if (g_phi && (rc = dcopy(h, g_phi, h->gphi_d, sizeof(float) * h->Nd, st))) return rc;
     if (g_mag && (rc = dcopy(h, g_mag, h->gmag_d, sizeof(float) * d * h->Nd, st))) return rc;
     if (g_field && (rc = dcopy(h, g_field, h->gfield_d, sizeof(float) * h->n_inst * h->T * d, st)))
@@ -1616,6 +1791,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             if (h->P.adj_blocks != (int)value) drop_graphs(h);
             h->P.adj_blocks = (int)value;
             return MPM_OK;
+        case MPM_OPT_RESIDENT_SEGMENTS:
+            if (value < 0) return fail(h, MPM_ERR_ARG, "resident segments must be >= 0");
+            return set_resident(h, (int)std::min<long long>(value, h->n_seg));
+        case MPM_OPT_SEGMENT_BYTES:
+            return fail(h, MPM_ERR_ARG, "segment bytes is read-only");
         case MPM_OPT_SCATTER_2D:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "scatter_2d must be 0 or 1");
             if (h->P.agg2 != (int)value) drop_graphs(h);
@@ -1666,6 +1846,8 @@ int mpm_get_option(const mpm_handle* h, int key, long long* value) {
         case MPM_OPT_PERSISTENT: *value = h->persistent ? 1 : 0; return MPM_OK;
         case MPM_OPT_SPIN_LIMIT: *value = h->spin_limit; return MPM_OK;
         case MPM_OPT_SCATTER_2D: *value = h->P.agg2; return MPM_OK;
+        case MPM_OPT_RESIDENT_SEGMENTS: *value = h->n_res; return MPM_OK;
+        case MPM_OPT_SEGMENT_BYTES: *value = resident_set_bytes(h); return MPM_OK;
         default: return MPM_ERR_ARG;
     }
 }

@@ -230,11 +230,35 @@ class Simulator:
                           ("graphs", B.MPM_OPT_GRAPHS),
                           ("streams", B.MPM_OPT_STREAMS), ("pdl", B.MPM_OPT_PDL),
                           ("adjoint_blocks", B.MPM_OPT_ADJOINT_BLOCKS), ("grid_blocks", B.MPM_OPT_GRID_BLOCKS),
-                          ("persistent", B.MPM_OPT_PERSISTENT), ("scatter_2d", B.MPM_OPT_SCATTER_2D)):
+                          ("persistent", B.MPM_OPT_PERSISTENT), ("scatter_2d", B.MPM_OPT_SCATTER_2D),
+                          ("resident_segments", B.MPM_OPT_RESIDENT_SEGMENTS)):
             v = ctypes.c_longlong()
             self._check(self.lib.mpm_get_option(self.handle, key, ctypes.byref(v)), "mpm_get_option")
             out[name] = v.value
         return out
+
+    def get_option(self, key):
+        v = ctypes.c_longlong()
+        self._check(self.lib.mpm_get_option(self.handle, int(key), ctypes.byref(v)), "mpm_get_option")
+        return v.value
+
+    def set_resident_budget(self, budget_bytes):
+        """Keep as many trailing checkpoint segments resident
+        (MPM_OPT_RESIDENT_SEGMENTS) as fit in budget_bytes of device memory
+        for the whole handle; returns the count."""
+        self.set_option(B.MPM_OPT_RESIDENT_SEGMENTS, 0)
+        base = self.stats()["device_bytes"]
+        seg = self.get_option(B.MPM_OPT_SEGMENT_BYTES)
+        want = int(max(0, (int(budget_bytes) - base) // max(1, seg)))
+        while want > 0:
+            try:
+                self.set_option(B.MPM_OPT_RESIDENT_SEGMENTS, want)
+                break
+            except B.MpmError as e:  # device memory short of the budget: fewer
+                if e.status != B.MPM_ERR_OOM:
+                    raise
+                want //= 2
+        return self.get_option(B.MPM_OPT_RESIDENT_SEGMENTS)
 
     def set_option(self, key, value):
         self._check(self.lib.mpm_set_option(self.handle, int(key), int(value)), "mpm_set_option")
