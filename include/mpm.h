@@ -82,7 +82,10 @@ typedef enum {
  *                     target (Eq. 38), 1 = -sum_{n=1..N} vbar_x(n) dt with the
  *                     mass-averaged velocity (Eq. 40).
  *   checkpoint_every  K: the backward pass recomputes K-substep segments from
- *                     checkpoints; 0 = keep every substep (one segment).
+ *                     checkpoints, keeping every substep of the segment it
+ *                     works on; 0 = one segment over the whole horizon.  With
+ *                     MPM_OPT_RESIDENT_SEGMENTS the forward pass keeps the
+ *                     last segments instead.
  */
 typedef struct {
     int dim;
@@ -108,7 +111,9 @@ typedef struct {
 /*
  * Create a handle and allocate, on the current device, every buffer the
  * forward and backward passes need (grid, sort scratch, checkpoints, segment
- * store, saved inputs).  No later call allocates device memory.
+ * store, saved inputs).  No later call allocates device memory, except
+ * mpm_set_option(MPM_OPT_RESIDENT_SEGMENTS), which reserves the resident
+ * segment sets.
  * Errors: MPM_ERR_ARG (bad config), MPM_ERR_OOM, MPM_ERR_CUDA.  On error
  * *out is set to NULL and nothing stays allocated.
  */
