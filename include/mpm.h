@@ -256,7 +256,8 @@ enum {
                            each; MPM_ERR_OOM if that fails, leaving none) and drops the last
                            forward: call mpm_forward again before mpm_backward.  0 (default)
                            releases them.  Not used by the persistent passes or while
-                           autotuning. */
+                           autotuning; while any are reserved, changing MPM_OPT_PERSISTENT or
+                           MPM_OPT_GRID_BLOCKS also drops the last forward. */
     MPM_OPT_SEGMENT_BYTES = 15 /* read only: device bytes of one resident segment set (K + 1
                            states, K accumulator and K velocity grids, the segment's design
                            and initial positions, and in 3D a node-block list) */

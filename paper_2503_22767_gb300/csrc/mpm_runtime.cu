@@ -1773,7 +1773,11 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             return MPM_OK;
         case MPM_OPT_PERSISTENT:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "persistent must be 0 or 1");
-            if (h->persistent != (value == 1)) drop_graphs(h);
+            if (h->persistent != (value == 1)) {
+                drop_graphs(h);
+                // whether the forward pass filled the resident sets may change
+                if (h->n_res > 0) h->forward_done = false;
+            }
             h->persistent = value == 1;
             return MPM_OK;
         case MPM_OPT_SPIN_LIMIT:
@@ -1783,7 +1787,10 @@ int mpm_set_option(mpm_handle* h, int key, long long value) {
             return MPM_OK;
         case MPM_OPT_GRID_BLOCKS:
             if (value != 0 && value != 1) return fail(h, MPM_ERR_ARG, "grid blocks must be 0 or 1");
-            if (h->grid_blocks != (value == 1)) drop_graphs(h);
+            if (h->grid_blocks != (value == 1)) {
+                drop_graphs(h);
+                if (h->n_res > 0) h->forward_done = false;
+            }
             h->grid_blocks = value == 1;
             return MPM_OK;
         case MPM_OPT_ADJOINT_BLOCKS:

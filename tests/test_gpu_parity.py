@@ -366,9 +366,9 @@ def test_resident_segments_match_oracle(key, resident, streams, gb):
 
 def test_resident_segments_forward_twice_and_option_changes():
     """Two forward passes before one backward, a resident count above the
-    number of segments (capped), a change of the count (which drops the last
-    forward), and a switch between listed blocks and every node: the handle
-    keeps giving the oracle's results."""
+    number of segments (capped), changes of the count, of the list mode and
+    of the persistent form (each drops the last forward): the handle keeps
+    giving the oracle's results."""
     w, of, ob = _oracle("walker3d_48_s0.25_60")
     args = (_t(w.x0), _t(w.phi), _t(w.mag), _t(w.field))
     kw = dict(target=_t(w.target), v0=_t(w.v0), want_x=True)
@@ -393,10 +393,14 @@ def test_resident_segments_forward_twice_and_option_changes():
     with pytest.raises(B.MpmError):  # the count changed: the last forward is gone
         sim.backward(torch.ones(w.cfg.n_instances, device="cuda"))
     check()
-    sim.set_option(B.MPM_OPT_GRID_BLOCKS, 0)
-    check()
-    sim.set_option(B.MPM_OPT_GRID_BLOCKS, 1)
-    check()
+    one = torch.ones(w.cfg.n_instances, device="cuda")
+    # modes that decide whether the forward pass fills the resident sets drop the last forward
+    for key, value in ((B.MPM_OPT_GRID_BLOCKS, 0), (B.MPM_OPT_GRID_BLOCKS, 1), (B.MPM_OPT_PERSISTENT, 1),
+                       (B.MPM_OPT_PERSISTENT, 0)):
+        sim.set_option(key, value)
+        with pytest.raises(B.MpmError):
+            sim.backward(one)
+        check()
     sim.set_option(B.MPM_OPT_RESIDENT_SEGMENTS, 0)
     assert sim.options()["resident_segments"] == 0
     check()
