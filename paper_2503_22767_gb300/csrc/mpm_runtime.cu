@@ -337,6 +337,9 @@ int set_resident(mpm_handle* h, int r) {
     if (e == cudaSuccess && h->blocks) e = cudaMemset(h->res_flag, 0, sizeof(int) * r * h->n_blocks);
     if (e == cudaSuccess && h->blocks) e = cudaMemset(h->res_count, 0, sizeof(int) * r);
     if (e == cudaSuccess && h->blocks) e = cudaMemset(h->res_wbox, 0, sizeof(int4) * r * h->n_wbox);
+    // the memsets run on the default stream: finish them before any pass on
+    // the caller's stream (which may not synchronise with it) uses the sets
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_resident(h);
         return fail(h, MPM_ERR_CUDA, std::string("resident segments: ") + cudaGetErrorString(e));
