@@ -660,6 +660,9 @@ int create_impl(const mpm_config* c, mpm_handle* h) {
     MPM_CUDA(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
     for (cudaEvent_t* e : {&h->ev_fork, &h->ev_rec[0], &h->ev_rec[1], &h->ev_adj[0], &h->ev_adj[1]})
         MPM_CUDA(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    // the initial memsets ran on the default stream; a caller's non-blocking
+    // stream does not wait for it
+    MPM_CUDA(h, cudaDeviceSynchronize());
     return MPM_OK;
 }
 
