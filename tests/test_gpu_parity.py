@@ -10,6 +10,7 @@ bit-exact.  The long horizons run the oracle on every host core (its threaded
 passes equal the serial ones bit for bit).
 """
 import ctypes
+import dataclasses
 import functools
 import os
 
@@ -113,6 +114,11 @@ def _oracle(key):
     return w, oracle.forward(w), oracle.backward(w, ckpt_every=50)
 
 
+def _damped(w, c):
+    cfg = dataclasses.replace(w.cfg, damping=c)
+    return W.Workload(w.name, cfg, w.x0, w.v0, w.phi, w.mag, w.field, w.target, dict(w.meta))
+
+
 # workloads sized so the oracle finishes in seconds but spanning many CTAs,
 # ragged tails and both dimensions
 CASES = {
@@ -129,6 +135,14 @@ CASES = {
     "tiny3d_free": lambda: W.tiny_3d(seed=9, n_steps=30, res=12, per_axis=2, loss_kind=0,
                                      phi_lo=0.3, v_scale=0.05, bound=1, gravity=-9.81,
                                      field_scale=0.2, mag_scale=1.0),
+    # the damping of Eq. 17 as a rate (1/s), at the paper's value of 200
+    "walker2d_s0.5_damped_200": lambda: _damped(W.walker_2d(seed=5, n_steps=200, scale=0.5,
+                                                            checkpoint_every=100), 200.0),
+    # (the position loss: under the locomotion loss this small body's dL/dB~_r
+    # and dL/dB_a vanish to 1e-20)
+    "tiny3d_damped_200": lambda: _damped(W.tiny_3d(seed=10, n_steps=30, res=12, per_axis=2, loss_kind=0,
+                                                   wall_mode=1, phi_lo=0.3, v_scale=0.1, bound=1,
+                                                   gravity=-9.81, field_scale=0.2, mag_scale=1.0), 200.0),
 }
 
 
