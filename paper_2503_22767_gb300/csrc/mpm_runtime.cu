@@ -126,7 +126,7 @@ struct mpm_handle {
     long long n_wbox = 0;     // warps of 32 particles
     // lists (flags, list, count, per-warp boxes), each covering one checkpoint
     // segment: 0 and 1 for the forward pass by segment parity, 2 and 3 for the
-    // two recomputation sets
+    // two recomputation sets (4 and up: the resident sets, in res_* below)
     int* blk_flag = nullptr;  // [4][n_blocks]
     int* blk_list = nullptr;  // [4][n_blocks]
     int* blk_count = nullptr; // [4]
