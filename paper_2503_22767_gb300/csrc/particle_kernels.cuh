@@ -365,8 +365,17 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
     auto load_state_n = [&]() {
         load_position<D>(a.s_in, a.x0, np, p, x_n);  // the position x0 + u
         load_vec<D>(a.s_in, L::V, np, p, v_n);
-        load_mat<D>(a.s_in, L::C, np, p, Cn);
-        load_mat<D>(a.s_in, L::F, np, p, F_n);
+        // C and E are read again after the P2G^T node loop under RELIEF:
+        // plain loads, so that the second read finds them cached
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                Cn[i][j] = RELIEF ? __ldg(a.s_in + (long long)(L::C + i * D + j) * np + p)
+                                  : __ldcs(a.s_in + (long long)(L::C + i * D + j) * np + p);
+                F_n[i][j] = RELIEF ? __ldg(a.s_in + (long long)(L::F + i * D + j) * np + p)
+                                   : __ldcs(a.s_in + (long long)(L::F + i * D + j) * np + p);
+            }
         load_vec<D>(a.adj, L::X, np, p, xb);
         phi_n = a.phi[p];
     };
