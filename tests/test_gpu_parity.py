@@ -378,6 +378,22 @@ def test_resident_segments_match_oracle(key, resident, streams, gb):
         assert_grads(g, ob, w)
 
 
+@pytest.mark.parametrize("key", ["plate3d_3tasks_k25", "batch2d_5_k50"])
+def test_resident_segments_batches(key):
+    """Resident segments in batches: three tasks sharing a design (3D, their
+    gradients summed, Eq. 35) and five independent 2D walkers of uneven
+    size, each over three checkpoint segments with the last two resident."""
+    import oracle
+    w = {"plate3d_3tasks_k25": lambda: W.with_steps(W.plate_3d(seed=3, n_steps=60, res=32, cells=(20, 5, 20)), 60,
+                                                        checkpoint_every=25),
+         "batch2d_5_k50": lambda: W.walker_batch_2d(seed=7, n_instances=5, n_steps=120, n_lo=1500, n_hi=6000,
+                                                    checkpoint_every=50)}[key]()
+    of, ob = oracle.forward(w), oracle.backward(w, ckpt_every=25)
+    g = run_gpu(w, options={B.MPM_OPT_RESIDENT_SEGMENTS: 2})
+    assert_state(g, of, w)
+    assert_grads(g, ob, w)
+
+
 def test_resident_segments_forward_twice_and_option_changes():
     """Two forward passes before one backward, a resident count above the
     number of segments (capped), changes of the count, of the list mode and
