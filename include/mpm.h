@@ -214,7 +214,8 @@ enum {
                               (Eq. 16-18) per stencil node (one kernel per substep);
                               bit 1: the adjoint particle kernels apply its reverse per
                               stencil node; a clear bit keeps the separate grid kernel.
-                              Default 1 (forward fused, adjoint separate) */
+                              Default 0 (both separate, as the autotuner picks on every
+                              workload measured) */
     MPM_OPT_GRAPHS = 4, /* 1 (default): each pass is captured once as a CUDA graph on an
                            internal stream and replayed on cuda_stream; 0: direct launches */
     MPM_OPT_STREAMS = 6, /* 2 (default): the backward pass recomputes checkpoint segment s-1

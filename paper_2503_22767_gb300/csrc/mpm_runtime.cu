@@ -159,7 +159,9 @@ struct mpm_handle {
     unsigned* bar = nullptr;           // grid barrier of the persistent kernels
 
     // --- options ---
-    bool fuse_fwd = true;   // grid operation folded into the forward particle kernels
+    // grid operation folded into the forward particle kernels (off by default:
+    // the autotuner keeps the separate grid kernel on all five workloads)
+    bool fuse_fwd = false;
     bool fuse_adj = false;  // grid adjoint folded into the adjoint particle kernels
     bool graphs = true;   // replay the forward / backward passes as CUDA graphs
     bool v0_given = false;
