@@ -354,6 +354,12 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
     // fusion follows the grid adjoint kernel, which writes none of the
     // particle arrays of state n, the partial adjoint or the design.
     constexpr bool kEarly = CHAIN && P2GT && G2PT && !FUSE;
+    // The late P2G^T epilogue (kLate): under the 80-register budget of the 3D
+    // kernel it cuts the spills from 188 to 88 bytes per thread (3D
+    // locomotion, 1M particles: 198.1 -> 196.0 us per launch, 3 x 200,000
+    // particles: 119.3 -> 117.4 us).  The 2D budgets spill nothing in the
+    // plain order and lose with this one (2D batch: 108.3 -> 112.3 us).
+    constexpr bool kLate = RELIEF && D == 3;
     const bool active = p < P.n_total;
     const int inst = active ? find_instance(a.inst_off, P.n_inst, p) : -1;
     const long long np = P.np;
@@ -569,12 +575,12 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
             // (RELIEF) they are read again, and the stress recomputed, here, so
             // their registers are free during the loop (the recomputation is
             // cheaper than the spills); with registers to spare they stay live.
-            if (RELIEF) {
-                reload_mat<D>(a.s_in, L::C, np, p, Cn);
-                reload_mat<D>(a.s_in, L::F, np, p, F);
-            }
-            load_mat<D>(a.adj, L::F, np, p, Fb);
-            if (RELIEF) {
+            // kLate: E, the stress and Fbar are formed only where first used,
+            // and P element by element.
+            if (RELIEF) reload_mat<D>(a.s_in, L::C, np, p, Cn);
+            if (RELIEF && !kLate) reload_mat<D>(a.s_in, L::F, np, p, F);
+            if (!kLate) load_mat<D>(a.adj, L::F, np, p, Fb);
+            if (RELIEF && !kLate) {
                 stress_parts<D>(F, phi, P, S);
                 piola<D>(S, Br, Ba, Pk);
             }
@@ -598,12 +604,15 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
                     mpb += Cn[i][j] * Ab[i][j];
                 }
             }
-            // A = mp C - sc P F^T
+            // A = mp C - sc P F^T:  Pbar = -sc Abar F,  Fbar -= sc Abar^T P
             float Pb[D][D];
+            if (!kLate) {
 #pragma unroll
-            for (int i = 0; i < D; ++i)
+                for (int i = 0; i < D; ++i)
 #pragma unroll
-                for (int j = 0; j < D; ++j) Cb[i][j] = mp * Ab[i][j];
+                    for (int j = 0; j < D; ++j) Cb[i][j] = mp * Ab[i][j];
+            }
+            if (kLate) reload_mat<D>(a.s_in, L::F, np, p, F);
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -612,15 +621,35 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
 #pragma unroll
                     for (int k = 0; k < D; ++k) {
                         pb += Ab[i][k] * F[k][j];
-                        fb += Ab[k][i] * Pk[k][j];   // (Abar^T P)_ij
+                        if (!kLate) fb += Ab[k][i] * Pk[k][j];  // (Abar^T P)_ij
                     }
                     Pb[i][j] = -sc * pb;
-                    Fb[i][j] -= sc * fb;
+                    if (!kLate) Fb[i][j] -= sc * fb;
                 }
+            if (kLate) {
+                stress_parts<D>(F, phi, P, S);
+                load_mat<D>(a.adj, L::F, np, p, Fb);
+                // P_kj as piola() forms it, used by its three products at once
+                const float smu = S.s * (1.0f / kMu0);
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const float pk = S.sE * (S.a * S.dev[k][j] + S.b * S.H[k][j]) - smu * Ba[k] * Br[j];
+#pragma unroll
+                        for (int i = 0; i < D; ++i) Fb[i][j] -= sc * (Ab[k][i] * pk);
+                    }
+            }
             float phib = 0.0f, brb[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) brb[i] = 0.0f;
             piola_adjoint<D>(F, phi, S, Br, Ba, Pb, P, Fb, phib, brb, bab);
+            if (kLate) {
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int j = 0; j < D; ++j) Cb[i][j] = mp * Ab[i][j];
+            }
             float gph = phib + mpb * P.rho0 * P.p_vol;
             if (Gn) {
                 // B at the particle = B_a + G (x - x_c): dL/dB_a stays in bab,
@@ -706,6 +735,7 @@ __device__ __forceinline__ void adjoint_particle(const Params& P, const StepArgs
             if (!make_stencil<D>(x, P, s)) flags |= kErrDomain;
             // x' = x + dt v',  F' = (I + dt C') F  (Eq. 21-22)
             float vt[D], Ct[D][D], Fo[D][D];
+            if (kLate && P2GT) reload_mat<D>(a.s_in, L::C, np, p, Cn);  // C of state n, for (I + dt C')^T
 #pragma unroll
             for (int i = 0; i < D; ++i) vt[i] = vb[i] + P.dt * xb[i];
 #pragma unroll
